@@ -1,0 +1,663 @@
+// SEDEF seeding-filter oracle: TEST INFRASTRUCTURE, not product code.
+//
+// A plain, slow, single-threaded CPU restatement of what the seeding filter
+// computes, written from the paper (Numanagic et al., "Fast Characterization
+// of Segmental Duplications in Genome Assemblies").  Only the tests, the
+// smoke check and the benchmark's CPU-baseline leg may call it.  It shares no
+// code, header, table or constant generator with the CUDA library: every
+// definition below is written out again from the paper's text.
+//
+// Steps (each function cites the passage it restates):
+//   pack      Section 2 (alphabet {A,C,G,T}), Section 3.2 (soft-masked bases)
+//   hash      Section 2.2 (MinHash needs a random permutation of k-mers)
+//   sketch    Section 2.2 (winnowing, rightmost k-mer on ties), Section 3.2
+//             (seeding uses only k-mers with at least one unmasked base)
+//   index     Section 3.1 (I_G: sorted unique (i, x); reverse index x -> [i])
+//   filter    Section 2.2 (|W(X_i) ∩ W(X_j)| >= s*tau), Section 3.1 (rolling
+//             over the candidate list C sorted by position), Section 2
+//             (overlap of the two mates at most delta*n)
+//   refine    Section 2.2 (winnowed MinHash estimate), Section 3.1 (keep the j
+//             whose estimate is maximal and above tau)
+//   chain     Section 3.3 (local chaining by sparse DP, gaps limited by l*delta_G)
+//   merge     Section 3 (seeds grown into larger regions while similar),
+//             restated at chain granularity
+//   tau       Section 3.1 closed form tau >= (1-dG)/(1+dG) / (2 e^{k dM} - 1)
+//
+// Readings where the paper is silent are listed in the design notes; the code
+// below states each one where it is used.
+//
+// Results are returned as flat int64 row tables (opaque handle + length +
+// copy + free) so that the Python test harness can read them with ctypes.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <set>
+#include <tuple>
+#include <vector>
+
+namespace {
+
+const uint64_t kInf = ~0ull;  // hash of an ineligible k-mer (never selected)
+
+// Parameters, passed from Python as a flat int64 array (doubles bit-cast).
+struct Par {
+  int64_t k, w, n, step, max_occ, self_mode, gap_max, diag_max, min_unmasked;
+  double delta_m, delta_g;
+};
+
+Par read_par(const int64_t* p) {
+  Par r;
+  r.k = p[0];
+  r.w = p[1];
+  r.n = p[2];
+  r.step = p[3];
+  r.max_occ = p[4];
+  r.self_mode = p[5];
+  r.gap_max = p[6];
+  r.diag_max = p[7];
+  r.min_unmasked = p[8];
+  std::memcpy(&r.delta_m, &p[9], 8);
+  std::memcpy(&r.delta_g, &p[10], 8);
+  return r;
+}
+
+struct Table {
+  int64_t ncols = 0;
+  std::vector<int64_t> v;
+  void row(std::initializer_list<int64_t> xs) { v.insert(v.end(), xs); }
+};
+
+// One sketch record: the minimizer's hash, its start position (global
+// coordinate in the concatenated input) and its strand (1 when the reverse
+// complement is the canonical form).
+struct Rec {
+  uint64_t h;
+  int64_t pos;
+  int sigma;
+};
+
+// ---- Section 2: alphabet; Section 3.2: soft-masking ------------------------
+// A/a=0, C/c=1, G/g=2, T/t=3; any other byte is N.  A base is masked when it
+// is a lowercase letter.
+bool decode(uint8_t b, int* code, bool* masked) {
+  *masked = (b >= 'a' && b <= 'z');
+  switch (b) {
+    case 'A': case 'a': *code = 0; return true;
+    case 'C': case 'c': *code = 1; return true;
+    case 'G': case 'g': *code = 2; return true;
+    case 'T': case 't': *code = 3; return true;
+    default: *code = 0; return false;
+  }
+}
+
+// ---- Section 2.2: a collision-free hash, i.e. a permutation of the 4^k codes.
+// Reading: a composition of invertible steps on 2k-bit integers -- xor with a
+// right shift (shift >= 1) and multiplication by an odd constant, both taken
+// modulo 2^(2k).  Each step is a bijection, so the composition is one.
+uint64_t hash_code(uint64_t x, int k) {
+  const uint64_t M = (k >= 32) ? ~0ull : ((1ull << (2 * k)) - 1);
+  x &= M;
+  x ^= x >> k;
+  x = (x * 0x9E3779B97F4A7C15ull) & M;
+  x ^= x >> (k - 1);
+  x = (x * 0xD6E8FEB86659FD93ull) & M;
+  x ^= x >> k;
+  return x;
+}
+
+// Seq boundaries as a list of [start, end) in the concatenated coordinates.
+std::vector<std::pair<int64_t, int64_t>> seq_ranges(const int64_t* off, int nseq) {
+  std::vector<std::pair<int64_t, int64_t>> r;
+  for (int s = 0; s < nseq; ++s) r.push_back({off[s], off[s + 1]});
+  return r;
+}
+
+int seq_of(const std::vector<std::pair<int64_t, int64_t>>& rs, int64_t pos) {
+  for (size_t s = 0; s < rs.size(); ++s)
+    if (pos >= rs[s].first && pos < rs[s].second) return (int)s;
+  return -1;
+}
+
+// ---- Section 3.1: threshold tau from the SD error model --------------------
+double tau_of(int64_t k, double dm, double dg) {
+  return (1.0 - dg) / (1.0 + dg) * (1.0 / (2.0 * std::exp((double)k * dm) - 1.0));
+}
+
+// m[s]: the least integer m with m >= tau*s - 1e-9 (shared minimizers needed
+// for a sketch of s distinct hashes; Section 2.2, |W ∩ W'| >= s*tau).
+int64_t min_shared(double tau, int64_t s) {
+  int64_t m = 0;
+  while ((double)m < tau * (double)s - 1e-9) ++m;
+  return m;
+}
+
+// Records are sorted by position; [first, last) indexes those with pos in [lo, hi].
+std::pair<size_t, size_t> pos_range(const std::vector<Rec>& recs, int64_t lo, int64_t hi) {
+  auto cmp = [](const Rec& r, int64_t p) { return r.pos < p; };
+  size_t a = std::lower_bound(recs.begin(), recs.end(), lo, cmp) - recs.begin();
+  size_t b = std::lower_bound(recs.begin(), recs.end(), hi + 1, cmp) - recs.begin();
+  return {a, std::max(a, b)};
+}
+
+// Window k-mer content: distinct hashes of the minimizers with start in
+// [lo, hi], each with the set of strands it occurs with (bit sigma).
+std::map<uint64_t, int> window_hashes(const std::vector<Rec>& recs, int64_t lo, int64_t hi) {
+  std::map<uint64_t, int> w;
+  auto r = pos_range(recs, lo, hi);
+  for (size_t a = r.first; a < r.second; ++a) w[recs[a].h] |= 1 << recs[a].sigma;
+  return w;
+}
+
+// Valid target window starts j for query window i (Section 2 overlap rule in
+// self mode; windows lie inside one sequence).  In self mode only pairs with
+// the target after the query are searched (each unordered pair once), and
+// the mates may overlap by at most floor(delta*n) bases.
+std::vector<std::pair<int64_t, int64_t>> valid_targets(
+    const std::vector<std::pair<int64_t, int64_t>>& tr, int qseq, int64_t i, const Par& P) {
+  std::vector<std::pair<int64_t, int64_t>> v;
+  const int64_t overlap = (int64_t)std::floor((P.delta_m + P.delta_g) * (double)P.n);
+  for (size_t u = 0; u < tr.size(); ++u) {
+    int64_t lo = tr[u].first, hi = tr[u].second - P.n;
+    if (hi < lo) continue;
+    if (P.self_mode) {
+      if ((int)u < qseq) continue;
+      if ((int)u == qseq) lo = std::max(lo, i + P.n - overlap);
+    }
+    if (lo <= hi) v.push_back({lo, hi});
+  }
+  return v;
+}
+
+std::vector<Rec> rows_to_recs(const int64_t* rows, int64_t nrec) {
+  std::vector<Rec> v(nrec);
+  for (int64_t a = 0; a < nrec; ++a) v[a] = {(uint64_t)rows[3 * a], rows[3 * a + 1], (int)rows[3 * a + 2]};
+  return v;
+}
+
+// Target postings: hash -> positions with strands (the reverse index).
+std::map<uint64_t, std::vector<std::pair<int64_t, int>>> postings_of(const std::vector<Rec>& t) {
+  std::map<uint64_t, std::vector<std::pair<int64_t, int>>> m;
+  for (const Rec& r : t) m[r.h].push_back({r.pos, r.sigma});
+  for (auto& kv : m) std::sort(kv.second.begin(), kv.second.end());
+  return m;
+}
+
+// Winnowed MinHash estimate for query window content wq (s distinct hashes)
+// against the target window [j, j+n-k] with relative strand o (Section 2.2):
+// U = the s smallest hashes of W_Q ∪ W_T; est = |{h in U : h shared with o}|.
+// In self mode a target occurrence inside the query window's own k-mer span
+// [i, i+n-k] is the same genome position, not a copy: it enters W_T (and so
+// the union) but never counts as shared.
+void estimate(const std::map<uint64_t, int>& wq, const std::vector<Rec>& trecs, int64_t i,
+              int64_t j, const Par& P, int o, int64_t* est, int64_t* den) {
+  std::map<uint64_t, int> wt;
+  auto rg = pos_range(trecs, j, j + P.n - P.k);
+  for (size_t a = rg.first; a < rg.second; ++a) {
+    const Rec& r = trecs[a];
+    const bool self_pos = P.self_mode && r.pos >= i && r.pos <= i + P.n - P.k;
+    wt[r.h] |= self_pos ? 0 : (1 << r.sigma);
+  }
+  std::set<uint64_t> uni;
+  for (auto& kv : wq) uni.insert(kv.first);
+  for (auto& kv : wt) uni.insert(kv.first);
+  const int64_t s = (int64_t)wq.size();
+  int64_t taken = 0, e = 0;
+  for (uint64_t h : uni) {
+    if (taken == s) break;
+    ++taken;
+    auto a = wq.find(h);
+    auto b = wt.find(h);
+    if (a == wq.end() || b == wt.end()) continue;
+    bool shared = false;
+    for (int sq = 0; sq < 2; ++sq)
+      for (int st = 0; st < 2; ++st)
+        if ((a->second >> sq & 1) && (b->second >> st & 1) && ((sq ^ st) == o)) shared = true;
+    if (shared) ++e;
+  }
+  *est = e;
+  *den = taken;
+}
+
+}  // namespace
+
+extern "C" {
+
+void* orc_table_new() { return new Table(); }
+int64_t orc_table_rows(void* t) {
+  Table* T = (Table*)t;
+  return T->ncols ? (int64_t)T->v.size() / T->ncols : 0;
+}
+int64_t orc_table_cols(void* t) { return ((Table*)t)->ncols; }
+void orc_table_copy(void* t, int64_t* dst) {
+  Table* T = (Table*)t;
+  if (!T->v.empty()) std::memcpy(dst, T->v.data(), T->v.size() * 8);
+}
+void orc_table_free(void* t) { delete (Table*)t; }
+
+// ---- a1 pack (Section 2 alphabet, Section 3.2 masking) ---------------------
+// Base p goes to bits 2*(p%16) of packed[p/16]; mask bit p%32 of mask[p/32]
+// is set for a lowercase base; nbits likewise for a non-ACGT byte.
+void orc_pack(const uint8_t* seq, int64_t n, uint32_t* packed, uint32_t* mask, uint32_t* nbits) {
+  for (int64_t w = 0; w < (n + 15) / 16; ++w) packed[w] = 0;
+  for (int64_t w = 0; w < (n + 31) / 32; ++w) mask[w] = nbits[w] = 0;
+  for (int64_t p = 0; p < n; ++p) {
+    int code;
+    bool masked;
+    bool ok = decode(seq[p], &code, &masked);
+    packed[p / 16] |= (uint32_t)code << (2 * (p % 16));
+    if (masked) mask[p / 32] |= 1u << (p % 32);
+    if (!ok) nbits[p / 32] |= 1u << (p % 32);
+  }
+}
+
+uint64_t orc_hash(uint64_t code, int k) { return hash_code(code, k); }
+
+void orc_hash_all(int k, uint64_t* out) {
+  const uint64_t N = 1ull << (2 * k);
+  for (uint64_t x = 0; x < N; ++x) out[x] = hash_code(x, k);
+}
+
+double orc_tau(int64_t k, double dm, double dg) { return tau_of(k, dm, dg); }
+
+void orc_mtable(int64_t k, double dm, double dg, int64_t smax, int64_t* out) {
+  double tau = tau_of(k, dm, dg);
+  for (int64_t s = 0; s <= smax; ++s) out[s] = min_shared(tau, s);
+}
+
+// ---- a2 sketch: canonical k-mers + winnowing (Section 2.2, Section 3.2) -----
+// Output rows (hash, pos, strand) sorted by pos.
+void* orc_sketch(const uint8_t* seq, const int64_t* off, int nseq, const int64_t* par) {
+  Par P = read_par(par);
+  Table* T = new Table();
+  T->ncols = 3;
+  for (int s = 0; s < nseq; ++s) {
+    const int64_t st = off[s], en = off[s + 1];
+    const int64_t nk = en - st - P.k + 1;  // k-mer starts inside the sequence
+    if (nk <= 0) continue;
+    std::vector<uint64_t> h(nk);
+    std::vector<int> sig(nk);
+    for (int64_t a = 0; a < nk; ++a) {
+      uint64_t f = 0, r = 0;
+      bool ok = true;
+      int64_t unmasked = 0;
+      for (int64_t x = 0; x < P.k; ++x) {
+        int code;
+        bool masked;
+        if (!decode(seq[st + a + x], &code, &masked)) ok = false;
+        if (!masked) ++unmasked;
+        f = f * 4 + (uint64_t)code;                       // first base most significant
+        r = r + ((uint64_t)(3 - code) << (2 * x));        // complement, reversed order
+      }
+      // eligible: no N, at least min_unmasked unmasked bases, strand defined
+      if (!ok || unmasked < P.min_unmasked || f == r) {
+        h[a] = kInf;
+        sig[a] = 0;
+      } else {
+        h[a] = hash_code(std::min(f, r), (int)P.k);
+        sig[a] = (r < f) ? 1 : 0;
+      }
+    }
+    std::set<int64_t> chosen;
+    for (int64_t q = 0; q + P.w <= nk; ++q) {  // every full window of w k-mer starts
+      uint64_t best = kInf;
+      int64_t arg = -1;
+      for (int64_t x = q; x < q + P.w; ++x)
+        if (h[x] != kInf && h[x] <= best) {  // '<=' keeps the rightmost minimum
+          best = h[x];
+          arg = x;
+        }
+      if (arg >= 0) chosen.insert(arg);
+    }
+    for (int64_t a : chosen) T->row({(int64_t)h[a], st + a, sig[a]});
+  }
+  return T;
+}
+
+// ---- a3 index: I_G sorted by (hash, position) plus offsets (Section 3.1) ----
+// off_out has 4^k + 1 entries: off[x] = number of records with hash < x.
+void* orc_index(const int64_t* rows, int64_t nrec, int k, uint32_t* off_out) {
+  std::vector<Rec> v = rows_to_recs(rows, nrec);
+  std::sort(v.begin(), v.end(), [](const Rec& a, const Rec& b) {
+    return std::tie(a.h, a.pos) < std::tie(b.h, b.pos);
+  });
+  const uint64_t N = 1ull << (2 * k);
+  std::vector<int64_t> cnt(N + 1, 0);
+  for (const Rec& r : v) cnt[r.h + 1]++;
+  for (uint64_t x = 0; x < N; ++x) cnt[x + 1] += cnt[x];
+  for (uint64_t x = 0; x <= N; ++x) off_out[x] = (uint32_t)cnt[x];
+  Table* T = new Table();
+  T->ncols = 3;
+  for (const Rec& r : v) T->row({(int64_t)r.h, r.pos, r.sigma});
+  return T;
+}
+
+// ---- a4/a5/a6 filter + refine (Section 2.2, Section 3.1, Section 2) ---------
+// For every query window i (start of each sequence, then every `step` bases,
+// while i + n <= sequence end) and each relative strand o:
+//   shared_o(j) = number of distinct hashes h of W(G_i) that occur in the
+//   target window [j, j+n-k] with relative strand o;
+//   j passes when it is a valid target window and shared_o(j) >= m[s];
+//   each maximal run of passing j is one output row, with its refined seed.
+// The rolling follows Section 3.1: the candidates C are sorted by position and
+// the window slides right; every hit at position t enters at j = t-(n-k) and
+// leaves at j = t+1, and the shared count is constant between such events.
+//
+// Rows: i, o, j_a, j_b, max_shared, j_at_max, s, m, est, j_star, den, keep.
+// `windows` (optional, nwin >= 0) restricts the query windows to that list of
+// starts; nwin < 0 means all windows.  dense != 0 evaluates the refine
+// estimate at every j of the run instead of at its breakpoints.
+void* orc_filter(const int64_t* qrows, int64_t nq, const int64_t* qoff, int nqseq,
+                 const int64_t* trows, int64_t nt, const int64_t* toff, int ntseq,
+                 const int64_t* par, const int64_t* windows, int64_t nwin, int dense) {
+  Par P = read_par(par);
+  std::vector<Rec> qrecs = rows_to_recs(qrows, nq);
+  std::vector<Rec> trecs = rows_to_recs(trows, nt);
+  auto post = postings_of(trecs);
+  auto qr = seq_ranges(qoff, nqseq);
+  auto tr = seq_ranges(toff, ntseq);
+  const double tau = tau_of(P.k, P.delta_m, P.delta_g);
+  const int64_t span = P.n - P.k;  // a window's k-mer starts are [j, j+span]
+
+  std::vector<int64_t> starts;
+  if (nwin >= 0) {
+    starts.assign(windows, windows + nwin);
+  } else {
+    for (auto& r : qr)
+      for (int64_t i = r.first; i + P.n <= r.second; i += P.step) starts.push_back(i);
+  }
+
+  Table* T = new Table();
+  T->ncols = 12;
+  for (int64_t i : starts) {
+    const int qseq = seq_of(qr, i);
+    std::map<uint64_t, int> wq = window_hashes(qrecs, i, i + span);
+    if (P.max_occ > 0) {  // optional occurrence cap (off by default)
+      for (auto it = wq.begin(); it != wq.end();) {
+        auto p = post.find(it->first);
+        int64_t occ = (p == post.end()) ? 0 : (int64_t)p->second.size();
+        if (occ > P.max_occ) it = wq.erase(it); else ++it;
+      }
+    }
+    const int64_t s = (int64_t)wq.size();
+    if (s == 0) continue;
+    const int64_t m = min_shared(tau, s);
+    auto valid = valid_targets(tr, qseq, i, P);
+
+    for (int o = 0; o < 2; ++o) {
+      // candidate list C for this strand: (j, +1/-1, hash) events
+      std::vector<std::tuple<int64_t, int, uint64_t>> ev;
+      for (auto& kv : wq) {
+        auto p = post.find(kv.first);
+        if (p == post.end()) continue;
+        for (auto& ts : p->second) {
+          // self mode: the query window's own positions are not copies
+          if (P.self_mode && ts.first >= i && ts.first <= i + span) continue;
+          if (kv.second >> (ts.second ^ o) & 1) {  // some query strand sq with sq^st == o
+            ev.push_back({ts.first - span, +1, kv.first});
+            ev.push_back({ts.first + 1, -1, kv.first});
+          }
+        }
+      }
+      std::sort(ev.begin(), ev.end());
+      std::map<uint64_t, int64_t> cnt;
+      int64_t shared = 0;
+      bool in_run = false;
+      int64_t ja = 0, jb = 0, mx = 0, jmx = 0;
+      auto close_run = [&]() {
+        if (!in_run) return;
+        // refine: evaluate the estimate at j_a and at every j in (j_a, j_b]
+        // where a target minimizer enters or leaves the window (the estimate
+        // only changes there), or at every j when dense.
+        std::vector<int64_t> bps;
+        if (dense) {
+          for (int64_t j = ja; j <= jb; ++j) bps.push_back(j);
+        } else {
+          std::set<int64_t> b;
+          b.insert(ja);
+          auto rg = pos_range(trecs, ja - span, jb + span);
+          for (size_t x = rg.first; x < rg.second; ++x) {
+            int64_t e1 = trecs[x].pos - span, e2 = trecs[x].pos + 1;
+            if (e1 > ja && e1 <= jb) b.insert(e1);
+            if (e2 > ja && e2 <= jb) b.insert(e2);
+          }
+          bps.assign(b.begin(), b.end());
+        }
+        int64_t best = -1, jstar = ja, dstar = 0;
+        for (int64_t j : bps) {
+          int64_t e, d;
+          estimate(wq, trecs, i, j, P, o, &e, &d);
+          if (e > best) {
+            best = e;
+            jstar = j;
+            dstar = d;
+          }
+        }
+        const int64_t keep = (best >= min_shared(tau, dstar)) ? 1 : 0;
+        T->row({i, o, ja, jb, mx, jmx, s, m, best, jstar, dstar, keep});
+        in_run = false;
+      };
+      size_t a = 0;
+      while (a < ev.size()) {
+        const int64_t j = std::get<0>(ev[a]);
+        while (a < ev.size() && std::get<0>(ev[a]) == j) {
+          auto& e = ev[a];
+          int64_t& c = cnt[std::get<2>(e)];
+          if (std::get<1>(e) > 0) {
+            if (c++ == 0) ++shared;
+          } else {
+            if (--c == 0) --shared;
+          }
+          ++a;
+        }
+        const int64_t jend = (a < ev.size()) ? std::get<0>(ev[a]) - 1 : j;  // constant on [j, jend]
+        if (a >= ev.size()) break;  // after the last event nothing is covered
+        for (auto& vr : valid) {
+          int64_t lo = std::max(j, vr.first), hi = std::min(jend, vr.second);
+          if (lo > hi) continue;
+          if (shared >= m) {
+            if (in_run && lo == jb + 1) {
+              jb = hi;
+            } else {
+              close_run();
+              in_run = true;
+              ja = lo;
+              jb = hi;
+              mx = -1;
+            }
+            if (shared > mx) {
+              mx = shared;
+              jmx = lo;
+            }
+          } else {
+            close_run();
+          }
+        }
+      }
+      close_run();
+    }
+  }
+  return T;
+}
+
+// ---- a7 chain: colinear chaining of seed anchors (Section 3.3) -------------
+// For every kept run row (i, o, j_a, j_b, ..., s) the anchors are the pairs
+// (p, t) of a query-window minimizer p in [i, i+n-k] and a target minimizer t
+// in [j_a, j_b+n-k] with equal hash and strands differing by o.  For o = 1
+// the target axis is reversed (t' = j_b+n-k - t) so that a chain is increasing
+// on both axes.  f(a) = 1 + max f(b) over predecessors b with p_b < p_a,
+// t'_b < t'_a, both gaps <= gap_max and |gap_p - gap_t| <= diag_max.
+// Ties: the predecessor with the largest f, then the largest sorted index; the
+// chain end with the largest f, then the smallest sorted index.  A chain is
+// kept when f >= m[s].
+// Rows: i, o, qseq, q0, q1, tseq, t0, t1, score, s  (q/t in global coordinates).
+void* orc_chain(const int64_t* runs, int64_t nruns, int64_t run_cols,
+                const int64_t* qrows, int64_t nq, const int64_t* qoff, int nqseq,
+                const int64_t* trows, int64_t nt, const int64_t* toff, int ntseq,
+                const int64_t* par) {
+  Par P = read_par(par);
+  std::vector<Rec> qrecs = rows_to_recs(qrows, nq);
+  std::vector<Rec> trecs = rows_to_recs(trows, nt);
+  auto post = postings_of(trecs);
+  auto qr = seq_ranges(qoff, nqseq);
+  auto tr = seq_ranges(toff, ntseq);
+  const double tau = tau_of(P.k, P.delta_m, P.delta_g);
+  const int64_t span = P.n - P.k;
+  Table* T = new Table();
+  T->ncols = 10;
+  for (int64_t r = 0; r < nruns; ++r) {
+    const int64_t* R = runs + r * run_cols;
+    const int64_t i = R[0], o = R[1], ja = R[2], jb = R[3], s = R[6], keep = R[11];
+    if (!keep) continue;
+    std::map<uint64_t, int> wq = window_hashes(qrecs, i, i + span);
+    const int64_t tref = jb + span;
+    std::vector<std::tuple<int64_t, int64_t, int64_t>> anc;  // (p, t', t)
+    auto qrg = pos_range(qrecs, i, i + span);
+    auto trg = pos_range(trecs, ja, tref);
+    for (size_t x = qrg.first; x < qrg.second; ++x) {
+      const Rec& q = qrecs[x];
+      if (P.max_occ > 0) {
+        auto p = post.find(q.h);
+        if (p != post.end() && (int64_t)p->second.size() > P.max_occ) continue;
+      }
+      for (size_t y = trg.first; y < trg.second; ++y) {
+        const Rec& t = trecs[y];
+        if (t.h != q.h || (q.sigma ^ t.sigma) != o) continue;
+        if (P.self_mode && t.pos >= i && t.pos <= i + span) continue;  // same position
+        anc.push_back({q.pos, o ? tref - t.pos : t.pos, t.pos});
+      }
+    }
+    std::sort(anc.begin(), anc.end());
+    const int64_t A = (int64_t)anc.size();
+    if (A == 0) continue;
+    std::vector<int64_t> f(A, 1), pred(A, -1);
+    for (int64_t a = 0; a < A; ++a) {
+      for (int64_t b = 0; b < a; ++b) {
+        int64_t dp = std::get<0>(anc[a]) - std::get<0>(anc[b]);
+        int64_t dt = std::get<1>(anc[a]) - std::get<1>(anc[b]);
+        if (dp <= 0 || dt <= 0 || dp > P.gap_max || dt > P.gap_max) continue;
+        if (std::llabs(dp - dt) > P.diag_max) continue;
+        if (pred[a] < 0 || f[b] + 1 > f[a] || (f[b] + 1 == f[a] && b > pred[a])) {
+          f[a] = f[b] + 1;
+          pred[a] = b;
+        }
+      }
+    }
+    int64_t end = 0;
+    for (int64_t a = 1; a < A; ++a)
+      if (f[a] > f[end]) end = a;
+    const int64_t score = f[end];
+    if (score < min_shared(tau, s)) continue;
+    int64_t q0 = INT64_MAX, q1 = -1, t0 = INT64_MAX, t1 = -1;
+    for (int64_t a = end; a >= 0; a = pred[a]) {
+      q0 = std::min(q0, std::get<0>(anc[a]));
+      q1 = std::max(q1, std::get<0>(anc[a]) + P.k);
+      t0 = std::min(t0, std::get<2>(anc[a]));
+      t1 = std::max(t1, std::get<2>(anc[a]) + P.k);
+    }
+    T->row({i, o, (int64_t)seq_of(qr, i), q0, q1, (int64_t)seq_of(tr, ja), t0, t1, score, s});
+  }
+  return T;
+}
+
+// Chaining of one explicit anchor list (for pin tests): anchors are (p, t')
+// rows; returns rows (f, pred) per anchor in sorted (p, t') order followed by
+// nothing else.  The best end is the largest f, then the smallest index.
+void* orc_chain_anchors(const int64_t* anchors, int64_t A, int64_t gap_max, int64_t diag_max) {
+  std::vector<std::pair<int64_t, int64_t>> anc(A);
+  for (int64_t a = 0; a < A; ++a) anc[a] = {anchors[2 * a], anchors[2 * a + 1]};
+  std::sort(anc.begin(), anc.end());
+  std::vector<int64_t> f(A, 1), pred(A, -1);
+  for (int64_t a = 0; a < A; ++a)
+    for (int64_t b = 0; b < a; ++b) {
+      int64_t dp = anc[a].first - anc[b].first, dt = anc[a].second - anc[b].second;
+      if (dp <= 0 || dt <= 0 || dp > gap_max || dt > gap_max) continue;
+      if (std::llabs(dp - dt) > diag_max) continue;
+      if (pred[a] < 0 || f[b] + 1 > f[a] || (f[b] + 1 == f[a] && b > pred[a])) {
+        f[a] = f[b] + 1;
+        pred[a] = b;
+      }
+    }
+  Table* T = new Table();
+  T->ncols = 4;
+  for (int64_t a = 0; a < A; ++a) T->row({anc[a].first, anc[a].second, f[a], pred[a]});
+  return T;
+}
+
+// ---- merge chains into SD candidates ---------------------------------------
+// Reading of Section 3 ("keep expanding both seed regions while similar") at
+// chain granularity: chains a and b are linked when they have the same query
+// sequence, target sequence and strand, their query intervals overlap or
+// touch, their target intervals overlap or touch, and their diagonals differ
+// by at most diag_max + ceil(delta_G * max(len_a, len_b)) (len = query span;
+// diagonal t0 - q0 for o = 0, t1 + q0 for o = 1).  Candidates are the
+// connected components: bounding boxes, summed scores and chain counts.
+// Rows (sorted by q0, t0, o, q1, t1; global coordinates):
+//   qseq, q0, q1, tseq, t0, t1, o, score, nchains
+void* orc_merge(const int64_t* chains, int64_t nc, int64_t cols, const int64_t* par) {
+  Par P = read_par(par);
+  std::vector<int64_t> parent(nc);
+  for (int64_t a = 0; a < nc; ++a) parent[a] = a;
+  auto find = [&](int64_t x) {
+    while (parent[x] != x) x = parent[x];
+    return x;
+  };
+  auto diag = [&](const int64_t* c) { return c[1] == 0 ? c[6] - c[3] : c[7] + c[3]; };
+  for (int64_t a = 0; a < nc; ++a)
+    for (int64_t b = a + 1; b < nc; ++b) {
+      const int64_t* A = chains + a * cols;
+      const int64_t* B = chains + b * cols;
+      if (A[1] != B[1] || A[2] != B[2] || A[5] != B[5]) continue;
+      if (B[3] > A[4] || A[3] > B[4]) continue;  // query intervals overlap or touch
+      if (B[6] > A[7] || A[6] > B[7]) continue;  // target intervals overlap or touch
+      const int64_t len = std::max(A[4] - A[3], B[4] - B[3]);
+      const int64_t slack = P.diag_max + (int64_t)std::ceil(P.delta_g * (double)len);
+      if (std::llabs(diag(A) - diag(B)) > slack) continue;
+      int64_t ra = find(a), rb = find(b);
+      if (ra != rb) parent[std::max(ra, rb)] = std::min(ra, rb);
+    }
+  std::map<int64_t, std::vector<int64_t>> comp;
+  for (int64_t a = 0; a < nc; ++a) {
+    const int64_t* A = chains + a * cols;
+    int64_t r = find(a);
+    auto it = comp.find(r);
+    if (it == comp.end()) {
+      comp[r] = {A[2], A[3], A[4], A[5], A[6], A[7], A[1], A[8], 1};
+    } else {
+      auto& c = it->second;
+      c[1] = std::min(c[1], A[3]);
+      c[2] = std::max(c[2], A[4]);
+      c[4] = std::min(c[4], A[6]);
+      c[5] = std::max(c[5], A[7]);
+      c[7] += A[8];
+      c[8] += 1;
+    }
+  }
+  std::vector<std::vector<int64_t>> out;
+  for (auto& kv : comp) out.push_back(kv.second);
+  std::sort(out.begin(), out.end(), [](const std::vector<int64_t>& x, const std::vector<int64_t>& y) {
+    return std::make_tuple(x[1], x[4], x[6], x[2], x[5], x[0], x[3], x[7], x[8]) <
+           std::make_tuple(y[1], y[4], y[6], y[2], y[5], y[0], y[3], y[7], y[8]);
+  });
+  Table* T = new Table();
+  T->ncols = 9;
+  for (auto& c : out) T->v.insert(T->v.end(), c.begin(), c.end());
+  return T;
+}
+
+// Exact k-mer set Jaccard of two substrings (Section 2.2 definition), used to
+// pin the closed form J = c / (2t - c) of Section 3.1.
+double orc_jaccard(const uint8_t* seq, int64_t i, int64_t j, int64_t n, int k) {
+  std::set<std::vector<uint8_t>> X, Y;
+  for (int64_t a = 0; a + k <= n; ++a) {
+    X.insert(std::vector<uint8_t>(seq + i + a, seq + i + a + k));
+    Y.insert(std::vector<uint8_t>(seq + j + a, seq + j + a + k));
+  }
+  int64_t inter = 0;
+  for (auto& x : X) inter += Y.count(x);
+  return (double)inter / (double)(X.size() + Y.size() - inter);
+}
+
+}  // extern "C"

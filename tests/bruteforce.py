@@ -1,0 +1,175 @@
+"""Brute-force restatements used to pin the oracle on tiny inputs.
+
+Everything here works on Python strings, sets and explicit loops over every
+candidate (every window, every target start j), so that it shares no logic
+with the oracle's event sweep, index or DP.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+
+_RC = str.maketrans("ACGTacgt", "TGCAtgca")
+_CODE = str.maketrans("ACGT", "0123")
+
+
+def kmer_codes(seq: bytes, st: int, en: int, k: int, min_unmasked: int = 1):
+    """Per k-mer start p in [st, en-k]: (forward code, revcomp code, eligible)."""
+    out = []
+    s = seq.decode("latin1")
+    for p in range(st, en - k + 1):
+        km = s[p:p + k]
+        up = km.upper()
+        ok = all(c in "ACGT" for c in up)
+        unmasked = sum(1 for c in km if not c.islower())
+        if ok:
+            f = int(up.translate(_CODE), 4)
+            r = int(up.translate(_RC)[::-1].translate(_CODE), 4)
+        else:
+            f = r = -1
+        out.append((f, r, ok and unmasked >= min_unmasked and f != r))
+    return out
+
+
+def sketch(seq: bytes, offsets, k: int, w: int, hash_fn, min_unmasked=1):
+    """Winnowing by explicit window scan; set of (h, pos, strand)."""
+    res = set()
+    for s in range(len(offsets) - 1):
+        st, en = int(offsets[s]), int(offsets[s + 1])
+        codes = kmer_codes(seq, st, en, k, min_unmasked)
+        hs = []
+        for f, r, ok in codes:
+            if ok:
+                c = min(f, r)
+                hs.append((hash_fn(c), 1 if r < f else 0))
+            else:
+                hs.append(None)
+        for q in range(0, len(hs) - w + 1):
+            win = [(hs[x][0], x) for x in range(q, q + w) if hs[x] is not None]
+            if not win:
+                continue
+            mn = min(h for h, _ in win)
+            x = max(x for h, x in win if h == mn)
+            res.add((hs[x][0], st + x, hs[x][1]))
+    return res
+
+
+def windows(offsets, n, step):
+    for s in range(len(offsets) - 1):
+        i = int(offsets[s])
+        while i + n <= int(offsets[s + 1]):
+            yield s, i
+            i += step
+
+
+def m_of(tau, s):
+    m = math.ceil(tau * s - 1e-9)
+    return max(m, 0)
+
+
+def filter_runs(qrecs, qoff, trecs, toff, p, tau):
+    """Every query window x every valid target start j, by explicit sets."""
+    k, n = p["k"], p["n"]
+    span = n - k
+    overlap = math.floor((p["delta_m"] + p["delta_g"]) * n)
+    post = {}
+    for h, t, sg in trecs:
+        post.setdefault(h, []).append((t, sg))
+    rows = []
+    for qs_, i in windows(qoff, n, p["step"]):
+        wq = {}
+        for h, pos, sg in qrecs:
+            if i <= pos <= i + span:
+                wq.setdefault(h, set()).add(sg)
+        if p["max_occ"] > 0:
+            wq = {h: v for h, v in wq.items() if len(post.get(h, [])) <= p["max_occ"]}
+        s = len(wq)
+        if s == 0:
+            continue
+        m = m_of(tau, s)
+        for o in (0, 1):
+            def shared(j):
+                hs = set()
+                for h, t, sg in trecs:
+                    if not (j <= t <= j + span):
+                        continue
+                    if p["self_mode"] and i <= t <= i + span:
+                        continue
+                    if h in wq and any((sq ^ sg) == o for sq in wq[h]):
+                        hs.add(h)
+                return len(hs)
+
+            for u in range(len(toff) - 1):
+                lo, hi = int(toff[u]), int(toff[u + 1]) - n
+                if p["self_mode"]:
+                    if u < qs_:
+                        continue
+                    if u == qs_:
+                        lo = max(lo, i + n - overlap)
+                run = None
+                for j in range(lo, hi + 1):
+                    c = shared(j)
+                    if c >= m:
+                        if run is None:
+                            run = [j, j, c, j]
+                        else:
+                            run[1] = j
+                            if c > run[2]:
+                                run[2], run[3] = c, j
+                    elif run is not None:
+                        rows.append((i, o, *run, s, m))
+                        run = None
+                if run is not None:
+                    rows.append((i, o, *run, s, m))
+    return rows
+
+
+def estimate(wq, trecs, i, j, p, o):
+    """Winnowed MinHash estimate by explicit set construction."""
+    span = p["n"] - p["k"]
+    wt_all = set()
+    wt_shared = set()
+    for h, t, sg in trecs:
+        if j <= t <= j + span:
+            wt_all.add(h)
+            if p["self_mode"] and i <= t <= i + span:
+                continue
+            if h in wq and any((sq ^ sg) == o for sq in wq[h]):
+                wt_shared.add(h)
+    s = len(wq)
+    union = sorted(set(wq) | wt_all)
+    U = union[:s]
+    return sum(1 for h in U if h in wt_shared), len(U)
+
+
+def best_chain_length(anchors, gap_max, diag_max):
+    """Longest valid chain as the longest path of the 'may follow' relation,
+    found by forward recursion over successors (tiny inputs only)."""
+    A = sorted(set(anchors))
+    nxt = {a: [] for a in range(len(A))}
+    for a, b in itertools.permutations(range(len(A)), 2):
+        dp = A[b][0] - A[a][0]
+        dt = A[b][1] - A[a][1]
+        if 0 < dp <= gap_max and 0 < dt <= gap_max and abs(dp - dt) <= diag_max:
+            nxt[a].append(b)
+    best = 0
+    memo = {}
+
+    def longest(a):
+        if a in memo:
+            return memo[a]
+        r = 1 + max((longest(b) for b in nxt[a]), default=0)
+        memo[a] = r
+        return r
+
+    for a in range(len(A)):
+        best = max(best, longest(a))
+    return best, A
+
+
+def chain_is_valid(chain, gap_max, diag_max):
+    for (p1, t1), (p2, t2) in zip(chain, chain[1:]):
+        dp, dt = p2 - p1, t2 - t1
+        if not (0 < dp <= gap_max and 0 < dt <= gap_max and abs(dp - dt) <= diag_max):
+            return False
+    return True

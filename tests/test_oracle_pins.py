@@ -1,0 +1,378 @@
+"""Pins for the CPU oracle: checks against what the paper and the mathematics
+fix, independent of the oracle's own code paths.
+
+- tau: the lower bound of Section 3.1 rebuilt from explicit sets that have
+  the structure the derivation assumes (not by retyping the formula);
+- hash: the 'random permutation' of Section 2.2 is a bijection on 4^k codes;
+- pack and sketch: per-base definitions and winnowing (Section 2.2: minimal
+  hash per window, rightmost on ties) by explicit string and window scans;
+- winnowing invariant and density 2/(w+1) (Section 2.2);
+- index: sorted unique (hash, position) pairs (Section 3.1) versus numpy;
+- filter and refine: every window x every target start by explicit sets;
+- chaining: longest chain by a different search on tiny anchor sets;
+- merge: connected components by networkx;
+- planted duplications are recovered (the protocol of Section 4.1.1).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1807_00205_gb300 import synth
+from tests import bruteforce as bf
+
+TINY = dict(k=5, w=4, n=40, step=3, max_occ=0, self_mode=1, gap_max=40,
+            diag_max=4, min_unmasked=1, delta_m=0.15, delta_g=0.10)
+
+
+def tiny_genome(seed, lengths=(260, 170), mask=0.15, gaps=True):
+    return synth.small_case(seed, lengths=lengths, n_sd=3, sd_lo=50, sd_hi=110,
+                            id_lo=0.9, id_hi=1.0, mask_frac=mask, n_gaps=gaps,
+                            inter_frac=0.5, repeat_lengths=(15, 30))
+
+
+# ---------------------------------------------------------------- tau ------
+
+@pytest.mark.parametrize("k,dm,dg", [(12, 0.15, 0.10), (12, 0.15, 0.15), (11, 0.10, 0.05),
+                                     (16, 0.05, 0.20)])
+def test_tau_matches_set_construction(k, dm, dg):
+    """Section 3.1 derivation rebuilt from explicit sets: t_M copied k-mers of
+    which c = t_M e^{-k dM} survive in both copies, plus gap k-mers that the
+    two sides do not share.  With t_G = t_M dG/(1-dG) gap k-mers per side (the
+    premise) the exact Jaccard is at least tau; with t_G = dG/(1-dG) times
+    |X^M_i u X^M_j| every step of the derivation is tight and the exact
+    Jaccard equals tau up to the rounding of the set sizes."""
+    t_m = 200_000
+    c = round(t_m * math.exp(-k * dm))
+
+    def jaccard_with_gaps(t_g):
+        X = set(range(t_m)) | set(range(10**7, 10**7 + t_g))
+        Y = set(range(c)) | set(range(2 * 10**7, 2 * 10**7 + t_m - c)) | \
+            set(range(3 * 10**7, 3 * 10**7 + t_g))
+        return len(X & Y) / len(X | Y)
+
+    tau = oracle.tau(k, dm, dg)
+    assert jaccard_with_gaps(round(t_m * dg / (1 - dg))) >= tau
+    assert tau == pytest.approx(jaccard_with_gaps(round((2 * t_m - c) * dg / (1 - dg))), rel=2e-4)
+
+
+def test_tau_default_value():
+    # the defaults of Sections 2.1 and 3.3 (k = 12, dM = 0.15, dG = 0.10)
+    assert oracle.tau() == pytest.approx(0.07371, abs=5e-6)
+
+
+def test_mtable_is_least_integer():
+    tau = oracle.tau()
+    m = oracle.mtable(smax=739)
+    s = np.arange(740)
+    assert np.all(m >= tau * s - 1e-9)
+    assert np.all((m - 1) < tau * s - 1e-9) or m[0] == 0
+    assert m[0] == 0 and m[1] == 1 and np.all(np.diff(m) >= 0)
+
+
+# ---------------------------------------------------------------- hash -----
+
+@pytest.mark.parametrize("k", [2, 3, 5, 8, 11, 12])
+def test_hash_is_permutation(k):
+    h = oracle.hash_all(k)
+    assert h.max() < (1 << (2 * k))
+    assert len(np.unique(h)) == (1 << (2 * k))
+
+
+# ---------------------------------------------------------------- pack -----
+
+def test_pack_every_byte():
+    rng = np.random.default_rng(7)
+    seq = np.concatenate([np.arange(256, dtype=np.uint8),
+                          rng.integers(0, 256, 1000).astype(np.uint8),
+                          np.frombuffer(b"ACGTacgtNnRY-", dtype=np.uint8)])
+    packed, mask, nbits = oracle.pack(seq)
+    table = {ord(c): v for c, v in zip("ACGTacgt", [0, 1, 2, 3, 0, 1, 2, 3])}
+    for p, b in enumerate(seq.tolist()):
+        code = (int(packed[p // 16]) >> (2 * (p % 16))) & 3
+        assert code == table.get(b, 0)
+        assert ((int(mask[p // 32]) >> (p % 32)) & 1) == int(chr(b).islower() and chr(b).isalpha()
+                                                           and b < 128)
+        assert ((int(nbits[p // 32]) >> (p % 32)) & 1) == int(b not in table)
+
+
+def test_pack_empty_and_ragged():
+    for n in [0, 1, 15, 16, 17, 31, 32, 33]:
+        seq = np.frombuffer(b"acgtN" * 10, dtype=np.uint8)[:n]
+        packed, mask, nbits = oracle.pack(seq)
+        assert len(packed) == (n + 15) // 16 and len(mask) == (n + 31) // 32
+
+
+# --------------------------------------------------------------- sketch ----
+
+def _sketch_cases():
+    yield tiny_genome(1), dict(TINY)
+    yield tiny_genome(2, lengths=(5, 9, 300)), dict(TINY, w=6)
+    # tandem repeats (equal hashes inside one window -> rightmost tie) and a
+    # palindromic 12-mer run
+    rep = (b"ACGTTA" * 30) + (b"ACGTACGTACGT" * 6) + b"GATTACA" * 20 + (b"cagtc" * 12)
+    offs = np.array([0, len(rep)], dtype=np.int64)
+    yield synth.Genome(np.frombuffer(rep, dtype=np.uint8).copy(), offs, []), dict(TINY, k=12, w=16)
+    yield tiny_genome(3, mask=0.5), dict(TINY, k=4, w=1)
+    yield tiny_genome(4, mask=0.4), dict(TINY, k=6, w=5, min_unmasked=3)
+
+
+@pytest.mark.parametrize("case", list(range(5)))
+def test_sketch_matches_window_scan(case):
+    g, p = list(_sketch_cases())[case]
+    rows = oracle.sketch(g.seq, g.offsets, p)
+    want = bf.sketch(g.seq.tobytes(), g.offsets, p["k"], p["w"],
+                     lambda c: oracle.hash_code(c, p["k"]), p["min_unmasked"])
+    assert set(map(tuple, rows.tolist())) == want
+    assert np.all(np.diff(rows[:, 1]) > 0)  # sorted, unique positions
+
+
+def test_winnow_invariant_and_density():
+    rng = np.random.default_rng(11)
+    L = 1_000_000
+    seq = synth.random_bases(rng, L)
+    offs = np.array([0, L], dtype=np.int64)
+    p = oracle.params()
+    rows = oracle.sketch(seq, offs, p)
+    pos = rows[:, 1]
+    # every full window of w k-mer starts holds a selected start (all k-mers
+    # of an ACGT-only random sequence are eligible except palindromes)
+    sel = np.zeros(L, dtype=np.int64)
+    sel[pos] = 1
+    cs = np.concatenate([[0], np.cumsum(sel)])
+    nk = L - p["k"] + 1
+    q = np.arange(nk - p["w"] + 1)
+    assert np.all(cs[q + p["w"]] - cs[q] >= 1)
+    # expected density 2/(w+1) for a random sequence (Section 2.2)
+    dens = len(pos) / nk
+    assert abs(dens - 2 / (p["w"] + 1)) < 0.003
+
+
+# ---------------------------------------------------------------- index ----
+
+def test_index_sorted_with_offsets():
+    g = tiny_genome(5, lengths=(3000, 2000))
+    p = dict(TINY, k=6, w=5)
+    recs = oracle.sketch(g.seq, g.offsets, p)
+    rows, off = oracle.index(recs, p["k"])
+    order = np.lexsort((recs[:, 1], recs[:, 0]))
+    assert np.array_equal(rows, recs[order])
+    want = np.searchsorted(recs[order, 0], np.arange((1 << 12) + 1), side="left")
+    assert np.array_equal(off.astype(np.int64), want)
+
+
+# --------------------------------------------------------------- filter ----
+
+FILTER_CASES = [
+    (11, dict(TINY)),
+    (12, dict(TINY, step=1, n=30)),
+    (13, dict(TINY, self_mode=0)),
+    (14, dict(TINY, max_occ=4)),
+    (15, dict(TINY, k=4, w=3, n=25, step=5)),
+]
+
+
+@pytest.mark.parametrize("seed,p", FILTER_CASES)
+def test_filter_and_refine_match_all_pairs(seed, p):
+    g = tiny_genome(seed)
+    recs = oracle.sketch(g.seq, g.offsets, p)
+    tau = oracle.tau(p["k"], p["delta_m"], p["delta_g"])
+    runs = oracle.filter_runs(recs, g.offsets, recs, g.offsets, p)
+    rl = [tuple(map(int, r)) for r in bf.filter_runs([tuple(r) for r in recs.tolist()], g.offsets,
+                                                    [tuple(r) for r in recs.tolist()], g.offsets,
+                                                    p, tau)]
+    assert len(rl) > 0
+    assert [tuple(r[:8]) for r in runs.tolist()] == rl
+    # refine: the estimate at every j of each run, by explicit sets
+    trecs = [tuple(r) for r in recs.tolist()]
+    for r in runs.tolist():
+        i, o, ja, jb = r[0], r[1], r[2], r[3]
+        wq = {}
+        for h, pos, sg in trecs:
+            if i <= pos <= i + p["n"] - p["k"]:
+                wq.setdefault(h, set()).add(sg)
+        if p["max_occ"] > 0:
+            cnt = {}
+            for h, _, _ in trecs:
+                cnt[h] = cnt.get(h, 0) + 1
+            wq = {h: v for h, v in wq.items() if cnt[h] <= p["max_occ"]}
+        best, jstar, den = -1, None, None
+        for j in range(ja, jb + 1):
+            e, d = bf.estimate(wq, trecs, i, j, p, o)
+            if e > best:
+                best, jstar, den = e, j, d
+        assert (r[8], r[9], r[10]) == (best, jstar, den)
+        assert r[11] == int(best >= bf.m_of(tau, den))
+
+
+def test_refine_breakpoints_equal_dense():
+    g = tiny_genome(21, lengths=(600, 400))
+    p = dict(TINY)
+    recs = oracle.sketch(g.seq, g.offsets, p)
+    a = oracle.filter_runs(recs, g.offsets, recs, g.offsets, p)
+    b = oracle.filter_runs(recs, g.offsets, recs, g.offsets, p, dense=True)
+    assert len(a) > 0 and np.array_equal(a, b)
+
+
+def test_filter_window_subset_matches_full():
+    g = tiny_genome(22, lengths=(600, 400))
+    p = dict(TINY)
+    recs = oracle.sketch(g.seq, g.offsets, p)
+    full = oracle.filter_runs(recs, g.offsets, recs, g.offsets, p)
+    wins = np.unique(full[:, 0])[::2]
+    sub = oracle.filter_runs(recs, g.offsets, recs, g.offsets, p, windows=wins)
+    assert np.array_equal(sub, full[np.isin(full[:, 0], wins)])
+
+
+# ---------------------------------------------------------------- chain ----
+
+@pytest.mark.parametrize("seed", range(30))
+def test_chain_dp_is_longest(seed):
+    rng = np.random.default_rng(seed)
+    A = int(rng.integers(1, 12))
+    base = np.sort(rng.integers(0, 200, A))
+    anc = np.stack([base, base + rng.integers(-6, 7, A) + (seed % 3) * 5], axis=1)
+    if seed % 4 == 0:
+        anc = rng.integers(0, 60, (A, 2))
+    gap_max, diag_max = 60, 5
+    rows = oracle.chain_anchors(anc, gap_max, diag_max)
+    best, srt = bf.best_chain_length([tuple(a) for a in anc.tolist()], gap_max, diag_max)
+    # duplicates of the same anchor cannot chain with each other
+    assert rows[:, 2].max() == best
+    # backtrack the oracle's chosen chain and check it is a valid chain
+    end = int(np.argmax(rows[:, 2]))
+    chain = []
+    while end >= 0:
+        chain.append((int(rows[end, 0]), int(rows[end, 1])))
+        end = int(rows[end, 3])
+    chain.reverse()
+    assert len(chain) == best and bf.chain_is_valid(chain, gap_max, diag_max)
+
+
+def test_chain_rows_are_colinear_boxes():
+    g = synth.small_case(31, lengths=(60_000,), n_sd=4, sd_lo=2000, sd_hi=5000, id_lo=0.9)
+    p = oracle.params()
+    r = oracle.selfsearch(g.seq, g.offsets, p)
+    ch = r["chains"]
+    assert len(ch) > 0
+    assert np.all(ch[:, 4] > ch[:, 3]) and np.all(ch[:, 7] > ch[:, 6])
+    m = oracle.mtable()
+    assert np.all(ch[:, 8] >= m[ch[:, 9]])
+    # in self mode the target box starts after the query window start
+    assert np.all(ch[:, 6] > ch[:, 0])
+
+
+# ---------------------------------------------------------------- merge ----
+
+def test_merge_is_connected_components():
+    nx = pytest.importorskip("networkx")
+    rng = np.random.default_rng(3)
+    p = oracle.params()
+    rows = []
+    for c in range(120):
+        o = int(rng.integers(0, 2))
+        q0 = int(rng.integers(0, 5000))
+        ln = int(rng.integers(100, 700))
+        t0 = q0 + int(rng.integers(3000, 3400))
+        rows.append([q0, o, 0, q0, q0 + ln, 0, t0, t0 + ln + int(rng.integers(-50, 50)),
+                     int(rng.integers(5, 40)), 80])
+    ch = np.array(rows, dtype=np.int64)
+    got = oracle.merge(ch, p)
+    G = nx.Graph()
+    G.add_nodes_from(range(len(ch)))
+
+    def diag(c):
+        return c[6] - c[3] if c[1] == 0 else c[7] + c[3]
+
+    for a in range(len(ch)):
+        for b in range(len(ch)):
+            A, B = ch[a], ch[b]
+            if a == b or A[1] != B[1]:
+                continue
+            if max(A[3], B[3]) <= min(A[4], B[4]) and max(A[6], B[6]) <= min(A[7], B[7]):
+                ln = max(A[4] - A[3], B[4] - B[3])
+                if abs(diag(A) - diag(B)) <= p["diag_max"] + math.ceil(p["delta_g"] * ln):
+                    G.add_edge(a, b)
+    want = []
+    for comp in nx.connected_components(G):
+        C = ch[list(comp)]
+        want.append((0, C[:, 3].min(), C[:, 4].max(), 0, C[:, 6].min(), C[:, 7].max(),
+                     C[0, 1], C[:, 8].sum(), len(C)))
+    want.sort(key=lambda x: (x[1], x[4], x[6], x[2], x[5]))
+    assert [tuple(r) for r in got.tolist()] == [tuple(map(int, w)) for w in want]
+
+
+# -------------------------------------------------------------- recall -----
+
+def test_planted_duplications_recovered():
+    """Section 4.1.1 protocol on synthetic data: a duplication counts as found
+    when candidates cover more than 95% of the bases of both mates.  Copies
+    here diverge by at most 10% through substitutions and small indels.  The
+    path ends at chaining (no extension step), so a mate's ends can be missed
+    by up to one query step; the bar is: most pairs found, every pair at
+    least 90% covered."""
+    g = synth.small_case(41, lengths=(400_000,), n_sd=8, sd_lo=2000, sd_hi=8000,
+                         id_lo=0.90, id_hi=0.995)
+    p = oracle.params()
+    r = oracle.selfsearch(g.seq, g.offsets, p)
+    cands = r["cands"]
+    assert len(g.planted) >= 6
+    found = 0
+    for sd in g.planted:
+        a, b = (sd.src, sd.src + sd.length), (sd.dst, sd.dst + sd.copy_length)
+        first, second = (a, b) if a[0] < b[0] else (b, a)
+        o = 1 if sd.reverse else 0
+        qcov = np.zeros(first[1] - first[0], dtype=bool)
+        tcov = np.zeros(second[1] - second[0], dtype=bool)
+        for c in cands.tolist():
+            if c[6] != o:
+                continue
+            if c[2] <= first[0] or c[1] >= first[1] or c[5] <= second[0] or c[4] >= second[1]:
+                continue
+            qcov[max(c[1], first[0]) - first[0]:min(c[2], first[1]) - first[0]] = True
+            tcov[max(c[4], second[0]) - second[0]:min(c[5], second[1]) - second[0]] = True
+        assert qcov.mean() > 0.90 and tcov.mean() > 0.90, (sd, qcov.mean(), tcov.mean())
+        found += int(qcov.mean() > 0.95 and tcov.mean() > 0.95)
+    assert found >= 0.75 * len(g.planted)
+
+
+def test_exact_jaccard_closed_form():
+    """Section 3.1: with no repeated k-mer, J = c / (2t - c), t = n - k + 1."""
+    rng = np.random.default_rng(5)
+    n, k = 300, 12
+    a = synth.random_bases(rng, n)
+    b = a.copy()
+    b[::37] = synth.random_bases(rng, len(b[::37]))
+    seq = np.concatenate([a, b])
+    J = oracle.jaccard(seq, 0, n, n, k)
+    A = {a[x:x + k].tobytes() for x in range(n - k + 1)}
+    B = {b[x:x + k].tobytes() for x in range(n - k + 1)}
+    t = n - k + 1
+    assert len(A) == t and len(B) == t
+    c = len(A & B)
+    assert J == pytest.approx(c / (2 * t - c), abs=1e-12)
+
+
+# --------------------------------------------------------------- golden ----
+
+def test_paper_constants_are_the_defaults():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")) as f:
+        c = json.load(f)
+    p = oracle.params()
+    assert p["k"] == c["k_seeding"]["value"]
+    assert p["delta_m"] == c["delta_m"]["value"]
+    assert p["delta_m"] + p["delta_g"] == pytest.approx(c["delta"]["value"])
+    assert p["n"] == c["seed_length_n"]["value"] == round(
+        c["min_sd_length"]["value"] * (1 - c["delta"]["value"]))
+
+
+def test_oracle_matches_stored_digests():
+    import json
+    import os
+    from tests.golden import make_golden
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_small.json")) as f:
+        want = json.load(f)
+    assert make_golden.compute() == want
