@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Throughput of the SEDEF seeding filter on one GB300 (or N replicas).
+
+A step is one pass of the whole path over a device-resident genome: pack,
+sketch, index, filter (candidate lookup, sliding count, refine), chain and
+merge, through the C ABI.  The default workload is the chromosome-scale
+self-search: 100 Mbp at 41% GC, ~40% soft-masked repeats (300 bp and 6 kbp
+families), N-gaps every ~10 Mbp and 2,000 planted duplications of 1-200 kbp
+at 75-99.5% identity in both orientations (synthetic, seeded).
+
+Prints one JSON line (rank 0).  `value` is query Mbp/s of the whole job (all
+ranks); `e2e` repeats the measurement through sedef_selfsearch_host with the
+genome in pinned host memory and the candidates copied back; `roofline`
+relates the dominant kernel's algorithmic bytes to the measured HBM peak;
+`cpu_baseline` times the CPU oracle on a bounded sample.
+
+--impl reference times the CPU oracle (the reference arm of this build) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "query Mbp/s through sketch+Jaccard filter+chain (batched/served vs plain), p99 latency, HBM %"
+WORKLOAD = "chromosome-100Mbp self-search (41% GC, 40% soft-masked repeats, N-gaps, 2000 planted SDs 1-200 kbp)"
+CPU_SAMPLE_BASES = 10_000_000
+FALLBACK_HBM_GBS = 6800.0
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        hbm = d.get("hbm_gbs") or d.get("hbm_GBs") or d.get("hbm")
+        if hbm:
+            return float(hbm), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def algorithmic_bytes(seq, offsets, rec_rows, sorted_rows, runs, k, n, step):
+    """Minimum bytes each kernel family must move per launch (see the
+    design notes).  Records are 8 bytes."""
+    N = int(offsets[-1])
+    nrec = len(rec_rows)
+    span = n - k
+    # filter: every window reads its query records, one offset pair per
+    # distinct query hash and every posting of those hashes once
+    pos, hsh = rec_rows[:, 1], rec_rows[:, 0]
+    occ = np.bincount(hsh, minlength=1 << (2 * k)).astype(np.int64)
+    w_lo = np.ceil((pos - span) / step).clip(min=0).astype(np.int64)
+    w_hi = (pos // step).astype(np.int64)
+    pairs = []
+    for d in range(0, span // step + 2):
+        w = w_lo + d
+        ok = w <= w_hi
+        pairs.append((w[ok] << 32) | hsh[ok])
+    pairs = np.unique(np.concatenate(pairs))
+    hashes = (pairs & 0xFFFFFFFF).astype(np.int64)
+    recs_per_window_total = sum(int(((w_lo + d) <= w_hi).sum()) for d in range(span // step + 2))
+    filt = 8 * recs_per_window_total + 8 * len(pairs) + 8 * int(occ[hashes].sum())
+    # refine: per run the query records of its window and the target records
+    # of its span
+    ref = 0
+    if len(runs):
+        ja = runs["j_a"].astype(np.int64)
+        jb = runs["j_b"].astype(np.int64)
+        i = runs["i"].astype(np.int64)
+        a = np.searchsorted(pos, ja)
+        b = np.searchsorted(pos, jb + span, side="right")
+        qa = np.searchsorted(pos, i)
+        qb = np.searchsorted(pos, i + span, side="right")
+        ref = int(8 * ((b - a).sum() + (qb - qa).sum()) + 32 * len(runs))
+    return {
+        "k_pack": int(1.5 * N),
+        "k_sketch_count": int(0.5 * N),
+        "k_sketch_write": int(0.5 * N + 8 * nrec),
+        "k_rs_scatter": 16 * nrec,
+        "k_rs_hist": 8 * nrec,
+        "k_offsets": 8 * nrec + 4 * ((1 << (2 * k)) + 1),
+        "k_filter_fast": filt,
+        "k_refine": ref,
+    }
+
+
+def run_cpu_oracle_sample(seq):
+    import oracle
+    X = min(CPU_SAMPLE_BASES, len(seq))
+    s = np.ascontiguousarray(seq[:X])
+    off = np.array([0, X], dtype=np.int64)
+    oracle.build()
+    t = time.perf_counter()
+    oracle.selfsearch(s, off, oracle.params())
+    dt = time.perf_counter() - t
+    return X / dt / 1e6, dt, X
+
+
+def reference_arm(args):
+    ws, rank, local = dist_info()
+    if rank != 0:
+        return
+    from paper_1807_00205_gb300 import synth
+    g = synth.chromosome_100mbp()
+    import oracle
+    oracle.build()
+    X = 2_000_000
+    s = np.ascontiguousarray(g.seq[:X])
+    off = np.array([0, X], dtype=np.int64)
+    for _ in range(args.warmup):
+        oracle.selfsearch(s, off, oracle.params())
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.selfsearch(s, off, oracle.params())
+        times.append(time.perf_counter() - t)
+    ms = 1000 * sum(times) / len(times)
+    value = X / (ms / 1000) / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mbp/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"self-search of the first {X} bases",
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "Mbp/s", "cores": 1, "kind": "oracle",
+                         "sample": f"self-search of the first {X} bases of the workload"},
+        "e2e": {"value": value, "unit": "Mbp/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="chromosome", choices=["chromosome", "plain"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--trace", action="store_true", help="print the per-kernel table to stderr")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import torch
+    from paper_1807_00205_gb300 import binding, synth
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    g = synth.chromosome_100mbp() if args.workload == "chromosome" else synth.plain_2mbp()
+    N = g.length
+    p = binding.params()
+    stream = torch.cuda.Stream(dev)
+    ctx = binding.Context(local, stream=stream)
+    with torch.cuda.stream(stream):
+        d_seq = torch.from_numpy(g.seq).to(dev)
+        flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)  # 256 MB > L2
+    stream.synchronize()
+
+    def step():
+        return ctx.selfsearch(d_seq, g.offsets, p)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            out = step()
+            flush.fill_(1)
+    stream.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # ---- timed region: device-resident input
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    ctx.sedef_trace_report(reset=True)
+    ctx.sedef_trace_enable(True)
+    launches0 = binding.Context.sedef_launch_count()
+    step_ms = []
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.fill_(1)  # L2 flush between steps, outside the step's events
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+    launches = binding.Context.sedef_launch_count() - launches0
+    trace = ctx.sedef_trace_report(reset=True)
+    ctx.sedef_trace_enable(False)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = sum(step_ms) / len(step_ms)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * N / (ms / 1000) / 1e6
+
+    # ---- end to end through the host-buffer entry point
+    host_seq = torch.from_numpy(g.seq).pin_memory().numpy()
+    e2e_times = []
+    ncand = 0
+    for it in range(args.warmup + args.steps):
+        barrier()
+        t0 = time.perf_counter()
+        cands = ctx.sedef_selfsearch_host(host_seq, g.offsets, p)
+        dt = time.perf_counter() - t0
+        ncand = len(cands)
+        if it >= args.warmup:
+            e2e_times.append(dt)
+    e2e_ms = 1000 * sum(e2e_times) / len(e2e_times)
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = ws * N / (e2e_ms / 1000) / 1e6
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel
+    runs = binding.struct_view(out["runs"], binding.RUN_DTYPE)
+    rec_rows = binding.records_to_rows(binding.to_numpy_records(out["rec"]))
+    algo = algorithmic_bytes(g.seq, g.offsets, rec_rows, None, runs, p.k, p.n, p.query_step)
+    dom = max(trace.items(), key=lambda kv: kv[1][1])
+    dname, (dcount, dms) = dom
+    peak, peak_kind = peaks()
+    per_launch_ms = dms / dcount
+    roof = {"kernel": dname, "bound": "hbm", "peak": peak, "unit": "GB/s",
+            "peak_source": peak_kind, "traffic": None}
+    if dname in algo:
+        launches_per_step = dcount / args.steps
+        bytes_per_launch = algo[dname] / max(1.0, launches_per_step) if dname.startswith("k_rs") \
+            else algo[dname]
+        achieved = bytes_per_launch / (per_launch_ms / 1000) / 1e9
+        roof.update({"achieved": achieved, "frac": achieved / peak,
+                     "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "launch_ms": per_launch_ms})
+    else:
+        roof.update({"achieved": None, "frac": None, "launch_ms": per_launch_ms})
+    kernels = {k: {"launches_per_step": c / args.steps, "ms_per_step": t / args.steps}
+               for k, (c, t) in sorted(trace.items(), key=lambda kv: -kv[1][1])}
+    for k, v in kernels.items():
+        if k in algo and v["launches_per_step"]:
+            lb = algo[k] if not k.startswith("k_rs") else algo[k]
+            v["gbs"] = (lb * v["launches_per_step"] if k.startswith("k_rs") else lb) / \
+                (v["ms_per_step"] / 1000) / 1e9 if v["ms_per_step"] else None
+    if args.trace:
+        print(json.dumps(kernels, indent=1), file=sys.stderr)
+
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        v, dt, X = run_cpu_oracle_sample(g.seq)
+        cpu = {"value": v, "unit": "Mbp/s", "cores": 1, "kind": "oracle",
+               "sample": f"self-search of the first {X} bases of the workload ({dt:.1f} s)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mbp/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "genome_bases": N, "k": p.k, "w": p.w, "n": p.n,
+                   "query_step": p.query_step, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 and a 256 MB L2 flush between steps",
+                   "runs": int(out["nruns"]), "chains": int(out["nchains"]),
+                   "candidates": int(out["ncands"])},
+        "e2e": {"value": e2e_value, "unit": "Mbp/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(N + 8 * len(g.offsets)),
+                "d2h_bytes_per_step": int(ncand * 40)},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "kernels": kernels,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,287 @@
+/*
+ * sedef.h -- C ABI of the GB300 seeding filter for segmental-duplication
+ * detection (SEDEF: Numanagic et al., "Fast Characterization of Segmental
+ * Duplications in Genome Assemblies").
+ *
+ * The library computes the seed stage of the method on one GPU:
+ *   sedef_pack    2-bit codes plus soft-mask and N bit-vectors (Section 2
+ *                 alphabet; Section 3.2 soft-masked repeats)
+ *   sedef_sketch  canonical k-mer hashes and winnowing minimizers (Section
+ *                 2.2; Section 3.2 eligibility: at least one unmasked base)
+ *   sedef_index   I_G sorted by (hash, position) and the reverse index as an
+ *                 offset table over all 4^k hashes (Section 3.1)
+ *   sedef_filter  per query window: candidate lookup, sliding count of shared
+ *                 minimizers tested against tau, and the winnowed MinHash
+ *                 estimate that picks each run's seed (Sections 2.2 and 3.1)
+ *   sedef_chain_t   colinear chaining of the seed's minimizer anchors (Section
+ *                 3.3, sparse DP with gaps bounded via delta_G)
+ *   sedef_merge   chains joined into SD candidates (Section 3: seeds grown
+ *                 while similar, at chain granularity)
+ *
+ * Conventions
+ *   - Every call returns SEDEF_OK (0) or a negative sedef_status.  On error
+ *     sedef_last_error() holds a message for the calling thread.
+ *   - Pointers named d_* are device pointers (cudaMalloc or torch); h_* are
+ *     host pointers.  The caller owns every buffer it passes; the library
+ *     owns only its context (and the scratch memory the context allocates).
+ *   - All work is enqueued on the context's stream.  Calls that return a
+ *     count synchronize that stream before returning; the others do not.
+ *   - Sequences are concatenated into one byte array; sequence s covers
+ *     [seq_off[s], seq_off[s+1]) of it.  Positions inside the library are
+ *     global coordinates in that array (uint32: total length < 2^32).
+ *     sedef_cand_t reports per-sequence coordinates.  Intervals are 0-based
+ *     and half-open unless stated.
+ *   - Outputs are deterministic and sorted, so runs compare bit for bit.
+ *   - Outputs with a data-dependent size take a capacity.  When the true
+ *     size exceeds it the call returns SEDEF_ERR_CAPACITY, stores the
+ *     needed size in the count argument and leaves the output undefined;
+ *     call again with a larger buffer.
+ */
+#ifndef SEDEF_H
+#define SEDEF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sedef_status {
+  SEDEF_OK = 0,
+  SEDEF_ERR_INVALID = -1,     /* bad argument or parameter */
+  SEDEF_ERR_OOM = -2,         /* device or pinned-host allocation failed */
+  SEDEF_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  SEDEF_ERR_TIMEOUT = -4,     /* a bounded device wait gave up */
+  SEDEF_ERR_UNSUPPORTED = -5, /* parameters outside the supported range */
+  SEDEF_ERR_CAPACITY = -6     /* output buffer too small; count holds the need */
+} sedef_status;
+
+/*
+ * Parameters.  Defaults (sedef_default_params):
+ *   k = 12          k-mer length for seeding (Section 3.3)
+ *   w = 16          winnowing window, in consecutive k-mer start positions
+ *                   (Section 2.2 leaves w open)
+ *   n = 750         seed window length, n >= 1000 * (1 - delta) (Section 3)
+ *   query_step = 250  distance between query window starts (the paper slides
+ *                   over every locus; 250 = 1000 - n keeps a whole window
+ *                   inside every SD of at least 1 kbp)
+ *   max_occ = 0     0: no cap; otherwise hashes with more than max_occ
+ *                   index entries are dropped from every query window
+ *   self_mode = 1   query and target are the same genome: only pairs with
+ *                   the target after the query are reported, the mates may
+ *                   overlap by at most floor(delta * n) bases (Section 2),
+ *                   and a target occurrence inside the query window's own
+ *                   k-mer span is not a shared k-mer
+ *   gap_max = 750   largest gap between chained anchors on either axis
+ *   diag_max = 75   largest drift |gap_q - gap_t| between chained anchors,
+ *                   ceil(n * delta_G) (Section 3.3: gaps bounded by l*delta_G)
+ *   min_unmasked = 1  unmasked bases a seeding k-mer needs (Section 3.2)
+ *   delta_m = 0.15, delta_g = 0.10  error split (Section 2.1); tau from the
+ *                   Section 3.1 bound
+ * Supported: 2 <= k <= 15, 1 <= w <= 256, k < n, n - k + 1 <= 1024,
+ * query_step >= 1.
+ */
+typedef struct sedef_params {
+  int32_t k;
+  int32_t w;
+  int32_t n;
+  int32_t query_step;
+  int32_t max_occ;
+  int32_t self_mode;
+  int32_t gap_max;
+  int32_t diag_max;
+  int32_t min_unmasked;
+  int32_t reserved;
+  double delta_m;
+  double delta_g;
+} sedef_params;
+
+/*
+ * Sketch record (sedef_sketch, sedef_index): one uint64 per minimizer,
+ *   bits 33..62  hash H(c) of the canonical code c (2k significant bits)
+ *   bits  1..32  start position p (global coordinate)
+ *   bit   0      strand: 1 when the reverse complement is the canonical form
+ */
+#define SEDEF_REC_HASH(r) ((uint64_t)(r) >> 33)
+#define SEDEF_REC_POS(r) ((uint32_t)((uint64_t)(r) >> 1))
+#define SEDEF_REC_STRAND(r) ((uint32_t)((r)&1u))
+
+/*
+ * One maximal run of passing target windows for one query window and one
+ * relative strand (Section 3.1 rolling), with its refined seed.
+ *   i         query window start (global); the window is [i, i+n)
+ *   j_a, j_b  first and last passing target window start (global, inclusive)
+ *   j_at_max  smallest j in the run where the shared count is max_shared
+ *   j_star    smallest j in the run where the winnowed MinHash estimate
+ *             (Section 2.2) is largest; the seed is (i, j_star, o)
+ *   s         distinct minimizer hashes of the query window
+ *   m         shared hashes needed, the least integer >= tau*s - 1e-9
+ *   max_shared  largest shared count in the run
+ *   est, den  estimate numerator and denominator at j_star
+ *   o         relative strand (0 same, 1 reverse complement)
+ *   keep      1 when est >= m(den) (the seed is kept)
+ */
+typedef struct sedef_run_t {
+  uint32_t i, j_a, j_b, j_at_max, j_star;
+  uint16_t s, m, max_shared, est, den;
+  uint8_t o, keep;
+} sedef_run_t;
+
+/*
+ * Best chain of one kept seed (Section 3.3), global coordinates:
+ * query [q0, q1) and target [t0, t1) bounding boxes of the chained anchors,
+ * score = number of anchors, s = the query window's sketch size.
+ */
+typedef struct sedef_chain_t {
+  uint32_t i, qseq, q0, q1, tseq, t0, t1;
+  uint16_t score, s;
+  uint32_t o;
+  uint32_t reserved;
+} sedef_chain_t;
+
+/* SD candidate: one connected group of chains, per-sequence coordinates. */
+typedef struct sedef_cand_t {
+  uint32_t qseq, q0, q1, tseq, t0, t1;
+  uint32_t o, score, nchains, reserved;
+} sedef_cand_t;
+
+typedef struct sedef_ctx sedef_ctx;
+
+/* Fills *p with the defaults listed above. */
+void sedef_default_params(sedef_params* p);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* sedef_last_error(void);
+
+/*
+ * Creates a context on `device` that enqueues work on `stream` (a
+ * cudaStream_t passed as void*; NULL = the legacy default stream).  The
+ * context owns a growable device scratch buffer and a pinned host buffer;
+ * sedef_destroy frees both.  A context is not thread-safe.
+ */
+int sedef_create(int device, void* stream, sedef_ctx** out);
+int sedef_destroy(sedef_ctx* ctx);
+int sedef_set_stream(sedef_ctx* ctx, void* stream);
+
+/*
+ * Tracing.  While enabled, every kernel the context launches is bracketed by
+ * CUDA events on the context's stream.  sedef_trace_report synchronizes the
+ * stream and writes one line per kernel name, "name launches total_ms", in
+ * first-launch order, into buf (NUL-terminated, truncated to cap bytes); it
+ * returns the full text length (or a negative status) and, with reset != 0,
+ * forgets the recorded launches.
+ */
+int sedef_trace_enable(sedef_ctx* ctx, int on);
+int sedef_trace_report(sedef_ctx* ctx, char* buf, int64_t cap, int reset);
+
+/* Kernels launched by this process through the library so far. */
+uint64_t sedef_launch_count(void);
+
+/*
+ * tau from the Section 3.1 bound, tau = (1-dG)/(1+dG) / (2 e^{k dM} - 1),
+ * and m_out[s] = the least integer m with m >= tau*s - 1e-9 for s in
+ * [0, smax].  m_out may be NULL.  Host only.
+ */
+int sedef_threshold_table(const sedef_params* p, int32_t* m_out, int32_t smax, double* tau_out);
+
+/*
+ * a1: d_seq holds n ASCII bytes.  Writes d_packed[ceil(n/16)] (base p in
+ * bits 2*(p%16) of word p/16; A/a=0 C/c=1 G/g=2 T/t=3, other bytes 0),
+ * d_mask[ceil(n/32)] (bit p%32 of word p/32 set for a lowercase letter) and
+ * d_nbits[ceil(n/32)] (bit set for a byte that is not ACGTacgt).  n may be 0.
+ */
+int sedef_pack(sedef_ctx* ctx, const uint8_t* d_seq, int64_t n, uint32_t* d_packed,
+               uint32_t* d_mask, uint32_t* d_nbits);
+
+/*
+ * a2: winnowing sketch of the packed input.  For each k-mer start p whose k
+ * bases lie in one sequence: forward code f (first base most significant),
+ * reverse-complement code r, canonical c = min(f, r), strand (r < f).  The
+ * k-mer is eligible when it has no N, at least min_unmasked unmasked bases
+ * and f != r; its hash is H(c), a bijection of [0, 4^k).  For every window
+ * of w consecutive k-mer starts inside one sequence, the eligible k-mer of
+ * least hash (the rightmost on ties) is selected.  Writes the distinct
+ * selected k-mers as records (layout above) sorted by position into
+ * d_rec[0..rec_cap) and their number to *h_nrec.  Synchronizes.
+ */
+int sedef_sketch(sedef_ctx* ctx, const uint32_t* d_packed, const uint32_t* d_mask,
+                 const uint32_t* d_nbits, const int64_t* h_seq_off, int32_t nseq,
+                 const sedef_params* p, uint64_t* d_rec, int64_t rec_cap, int64_t* h_nrec);
+
+/*
+ * a3: sorts the nrec records of d_rec by (hash, position) into d_sorted and
+ * writes d_off[0..4^k] with d_off[x] = number of records whose hash is < x,
+ * so the postings of hash x are d_sorted[d_off[x] .. d_off[x+1]).
+ * d_rec and d_sorted must not overlap.
+ */
+int sedef_index(sedef_ctx* ctx, const uint64_t* d_rec, int64_t nrec, const sedef_params* p,
+                uint64_t* d_sorted, uint32_t* d_off);
+
+/*
+ * a4-a6: for every query window i (each query sequence start, then every
+ * query_step bases while i + n <= the sequence end) with W_Q = the distinct
+ * hashes of the query minimizers starting in [i, i+n-k] (s = |W_Q|, m = m(s))
+ * and each relative strand o, shared_o(j) counts the hashes of W_Q that occur
+ * in the target window [j, j+n-k] with relative strand o.  A target start j
+ * is valid when [j, j+n) lies in one target sequence (self mode: see
+ * sedef_params).  Each maximal run of valid j with shared_o(j) >= m is one
+ * sedef_run_t, refined with the winnowed MinHash estimate at every j of the run
+ * where the target window's minimizers change.
+ *
+ * Query: d_qrec (nq records sorted by position) over sequences h_qoff.
+ * Target: d_trec (nt records sorted by position), its index d_tsorted/d_toff
+ * (sedef_index), over sequences h_toff.  In self mode query and target are
+ * the same arrays.  Runs are sorted by (i, o, j_a).  Synchronizes.
+ */
+int sedef_filter(sedef_ctx* ctx, const uint64_t* d_qrec, int64_t nq, const int64_t* h_qoff,
+                 int32_t nqseq, const uint64_t* d_trec, const uint64_t* d_tsorted,
+                 const uint32_t* d_toff, int64_t nt, const int64_t* h_toff, int32_t ntseq,
+                 const sedef_params* p, sedef_run_t* d_runs, int64_t run_cap, int64_t* h_nruns);
+
+/*
+ * a7 (chaining): for each kept run, the anchors are the pairs (p, t) of a
+ * query-window minimizer and a target minimizer starting in [j_a, j_b+n-k]
+ * with equal hash and strands differing by o (self mode: t outside the query
+ * window's span).  For o = 1 the target axis is reversed.  The best chain
+ * maximizes the number of anchors; consecutive anchors advance on both axes
+ * by at most gap_max with |gap_q - gap_t| <= diag_max.  Ties: predecessor
+ * with the larger count then the later anchor in (p, t') order; chain end
+ * with the larger count then the earlier anchor.  Chains with fewer than
+ * m(s) anchors are dropped.  Query records as in sedef_filter; the target
+ * is given by its index (d_tsorted, d_toff from sedef_index).  Writes chains
+ * in run order.  Synchronizes.
+ */
+int sedef_chain(sedef_ctx* ctx, const sedef_run_t* d_runs, int64_t nruns, const uint64_t* d_qrec,
+                int64_t nq, const int64_t* h_qoff, int32_t nqseq, const uint64_t* d_tsorted,
+                const uint32_t* d_toff, int64_t nt, const int64_t* h_toff, int32_t ntseq,
+                const sedef_params* p, sedef_chain_t* d_chains, int64_t cap, int64_t* h_nchains);
+
+/*
+ * a7 (merge): chains with the same query sequence, target sequence and
+ * strand are linked when their query intervals overlap or touch, their
+ * target intervals overlap or touch, and their diagonals (t0 - q0 for o = 0,
+ * t1 + q0 for o = 1) differ by at most diag_max + ceil(delta_g * L), L the
+ * longer query span.  Each connected component becomes one candidate: the
+ * bounding boxes, the summed scores and the chain count, in per-sequence
+ * coordinates, sorted by global (q0, t0, o, q1, t1).  Synchronizes.
+ */
+int sedef_merge(sedef_ctx* ctx, const sedef_chain_t* d_chains, int64_t nchains,
+                const int64_t* h_qoff, int32_t nqseq, const int64_t* h_toff, int32_t ntseq,
+                const sedef_params* p, sedef_cand_t* d_cands, int64_t cap, int64_t* h_ncands);
+
+/*
+ * Whole self-search through host buffers: copies h_seq (total bytes
+ * h_seq_off[nseq]) to the device, runs pack, sketch, index, filter, chain
+ * and merge on the context's stream, and copies the candidates back to
+ * h_cands.  Device memory comes from the context.  Synchronizes.
+ */
+int sedef_selfsearch_host(sedef_ctx* ctx, const uint8_t* h_seq, const int64_t* h_seq_off,
+                          int32_t nseq, const sedef_params* p, sedef_cand_t* h_cands, int64_t cap,
+                          int64_t* h_ncands);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEDEF_H */

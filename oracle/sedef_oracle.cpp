@@ -185,37 +185,28 @@ std::map<uint64_t, std::vector<std::pair<int64_t, int>>> postings_of(const std::
   return m;
 }
 
-// Winnowed MinHash estimate for query window content wq (s distinct hashes)
-// against the target window [j, j+n-k] with relative strand o (Section 2.2):
-// U = the s smallest hashes of W_Q ∪ W_T; est = |{h in U : h shared with o}|.
-// In self mode a target occurrence inside the query window's own k-mer span
-// [i, i+n-k] is the same genome position, not a copy: it enters W_T (and so
-// the union) but never counts as shared.
-void estimate(const std::map<uint64_t, int>& wq, const std::vector<Rec>& trecs, int64_t i,
-              int64_t j, const Par& P, int o, int64_t* est, int64_t* den) {
-  std::map<uint64_t, int> wt;
-  auto rg = pos_range(trecs, j, j + P.n - P.k);
-  for (size_t a = rg.first; a < rg.second; ++a) {
-    const Rec& r = trecs[a];
-    const bool self_pos = P.self_mode && r.pos >= i && r.pos <= i + P.n - P.k;
-    wt[r.h] |= self_pos ? 0 : (1 << r.sigma);
-  }
-  std::set<uint64_t> uni;
-  for (auto& kv : wq) uni.insert(kv.first);
-  for (auto& kv : wt) uni.insert(kv.first);
+// Winnowed MinHash estimate (Section 2.2) for query window content wq (s
+// distinct hashes) against the current target window content wt: hash ->
+// (records in the window, records that are shared-compatible).  U = the s
+// smallest hashes of W_Q u W_T; est = |{h in U : h in W_Q and shared}|;
+// den = |U|.
+void estimate(const std::map<uint64_t, int>& wq,
+              const std::map<uint64_t, std::pair<int64_t, int64_t>>& wt, int64_t* est,
+              int64_t* den) {
   const int64_t s = (int64_t)wq.size();
+  auto a = wq.begin();
+  auto b = wt.begin();
   int64_t taken = 0, e = 0;
-  for (uint64_t h : uni) {
-    if (taken == s) break;
-    ++taken;
-    auto a = wq.find(h);
-    auto b = wt.find(h);
-    if (a == wq.end() || b == wt.end()) continue;
-    bool shared = false;
-    for (int sq = 0; sq < 2; ++sq)
-      for (int st = 0; st < 2; ++st)
-        if ((a->second >> sq & 1) && (b->second >> st & 1) && ((sq ^ st) == o)) shared = true;
+  while (taken < s && (a != wq.end() || b != wt.end())) {
+    uint64_t h;
+    if (b == wt.end() || (a != wq.end() && a->first <= b->first)) h = a->first;
+    else h = b->first;
+    const bool in_q = (a != wq.end() && a->first == h);
+    const bool shared = in_q && b != wt.end() && b->first == h && b->second.second > 0;
     if (shared) ++e;
+    ++taken;
+    if (a != wq.end() && a->first == h) ++a;
+    if (b != wt.end() && b->first == h) ++b;
   }
   *est = e;
   *den = taken;
@@ -408,32 +399,54 @@ void* orc_filter(const int64_t* qrows, int64_t nq, const int64_t* qoff, int nqse
       int64_t ja = 0, jb = 0, mx = 0, jmx = 0;
       auto close_run = [&]() {
         if (!in_run) return;
-        // refine: evaluate the estimate at j_a and at every j in (j_a, j_b]
-        // where a target minimizer enters or leaves the window (the estimate
-        // only changes there), or at every j when dense.
-        std::vector<int64_t> bps;
-        if (dense) {
-          for (int64_t j = ja; j <= jb; ++j) bps.push_back(j);
-        } else {
-          std::set<int64_t> b;
-          b.insert(ja);
-          auto rg = pos_range(trecs, ja - span, jb + span);
-          for (size_t x = rg.first; x < rg.second; ++x) {
-            int64_t e1 = trecs[x].pos - span, e2 = trecs[x].pos + 1;
-            if (e1 > ja && e1 <= jb) b.insert(e1);
-            if (e2 > ja && e2 <= jb) b.insert(e2);
-          }
-          bps.assign(b.begin(), b.end());
-        }
+        // refine (Section 3.1): roll the target window over the run, keeping
+        // its minimizers in an ordered map (the paper's set L), and evaluate
+        // the estimate at j_a and at every j in (j_a, j_b] where a target
+        // minimizer enters or leaves the window -- the estimate only changes
+        // there -- or at every j when dense.  In self mode a target record
+        // inside the query window's own span is not shared-compatible.
+        std::map<uint64_t, std::pair<int64_t, int64_t>> wt;
+        auto rg = pos_range(trecs, ja, jb + span);
+        auto compatible = [&](const Rec& r) {
+          if (P.self_mode && r.pos >= i && r.pos <= i + span) return false;
+          auto q = wq.find(r.h);
+          return q != wq.end() && ((q->second >> (r.sigma ^ o)) & 1);
+        };
+        auto enter = [&](const Rec& r) {
+          auto& c = wt[r.h];
+          c.first += 1;
+          if (compatible(r)) c.second += 1;
+        };
+        auto leave = [&](const Rec& r) {
+          auto it = wt.find(r.h);
+          it->second.first -= 1;
+          if (compatible(r)) it->second.second -= 1;
+          if (it->second.first == 0) wt.erase(it);
+        };
+        size_t in = rg.first, out = rg.first;  // next record to enter / to leave
+        int64_t j = ja;
+        while (in < rg.second && trecs[in].pos <= j + span) enter(trecs[in++]);
         int64_t best = -1, jstar = ja, dstar = 0;
-        for (int64_t j : bps) {
+        while (true) {
           int64_t e, d;
-          estimate(wq, trecs, i, j, P, o, &e, &d);
+          estimate(wq, wt, &e, &d);
           if (e > best) {
             best = e;
             jstar = j;
             dstar = d;
           }
+          int64_t nx;
+          if (dense) {
+            nx = j + 1;
+          } else {
+            nx = INT64_MAX;
+            if (in < rg.second) nx = std::min(nx, trecs[in].pos - span);
+            if (out < in) nx = std::min(nx, trecs[out].pos + 1);
+          }
+          if (nx > jb) break;
+          j = nx;
+          while (out < in && trecs[out].pos < j) leave(trecs[out++]);
+          while (in < rg.second && trecs[in].pos <= j + span) enter(trecs[in++]);
         }
         const int64_t keep = (best >= min_shared(tau, dstar)) ? 1 : 0;
         T->row({i, o, ja, jb, mx, jmx, s, m, best, jstar, dstar, keep});

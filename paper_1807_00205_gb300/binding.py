@@ -1,0 +1,303 @@
+"""Thin ctypes binding of libsedef (include/sedef.h).
+
+Argument marshalling only: torch allocates device buffers and provides the
+stream; every step of the seeding filter runs in the library's CUDA kernels.
+There is no fallback: if the library cannot be loaded, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SEDEF_OK = 0
+SEDEF_ERR_CAPACITY = -6
+
+RUN_DTYPE = np.dtype([("i", "<u4"), ("j_a", "<u4"), ("j_b", "<u4"), ("j_at_max", "<u4"),
+                      ("j_star", "<u4"), ("s", "<u2"), ("m", "<u2"), ("max_shared", "<u2"),
+                      ("est", "<u2"), ("den", "<u2"), ("o", "u1"), ("keep", "u1")])
+CHAIN_DTYPE = np.dtype([("i", "<u4"), ("qseq", "<u4"), ("q0", "<u4"), ("q1", "<u4"),
+                        ("tseq", "<u4"), ("t0", "<u4"), ("t1", "<u4"), ("score", "<u2"),
+                        ("s", "<u2"), ("o", "<u4"), ("reserved", "<u4")])
+CAND_DTYPE = np.dtype([("qseq", "<u4"), ("q0", "<u4"), ("q1", "<u4"), ("tseq", "<u4"),
+                       ("t0", "<u4"), ("t1", "<u4"), ("o", "<u4"), ("score", "<u4"),
+                       ("nchains", "<u4"), ("reserved", "<u4")])
+assert RUN_DTYPE.itemsize == 32 and CHAIN_DTYPE.itemsize == 40 and CAND_DTYPE.itemsize == 40
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("w", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("query_step", ctypes.c_int32), ("max_occ", ctypes.c_int32),
+                ("self_mode", ctypes.c_int32), ("gap_max", ctypes.c_int32),
+                ("diag_max", ctypes.c_int32), ("min_unmasked", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("delta_m", ctypes.c_double),
+                ("delta_g", ctypes.c_double)]
+
+
+EXPORTS = ["sedef_default_params", "sedef_last_error", "sedef_create", "sedef_destroy",
+           "sedef_set_stream", "sedef_trace_enable", "sedef_trace_report", "sedef_launch_count",
+           "sedef_threshold_table", "sedef_pack", "sedef_sketch",
+           "sedef_index", "sedef_filter", "sedef_chain", "sedef_merge", "sedef_selfsearch_host"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libsedef.so (building it first when allowed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsedef not built: {path} is missing")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    P = ctypes.POINTER(Params)
+    lib.sedef_default_params.argtypes = [P]
+    lib.sedef_last_error.restype = ctypes.c_char_p
+    lib.sedef_create.argtypes = [ctypes.c_int, vp, ctypes.POINTER(vp)]
+    lib.sedef_destroy.argtypes = [vp]
+    lib.sedef_set_stream.argtypes = [vp, vp]
+    lib.sedef_threshold_table.argtypes = [P, vp, i32, ctypes.POINTER(ctypes.c_double)]
+    lib.sedef_pack.argtypes = [vp, vp, i64, vp, vp, vp]
+    lib.sedef_sketch.argtypes = [vp, vp, vp, vp, vp, i32, P, vp, i64, ctypes.POINTER(i64)]
+    lib.sedef_index.argtypes = [vp, vp, i64, P, vp, vp]
+    lib.sedef_filter.argtypes = [vp, vp, i64, vp, i32, vp, vp, vp, i64, vp, i32, P, vp, i64,
+                                 ctypes.POINTER(i64)]
+    lib.sedef_chain.argtypes = [vp, vp, i64, vp, i64, vp, i32, vp, vp, i64, vp, i32, P, vp, i64,
+                                ctypes.POINTER(i64)]
+    lib.sedef_merge.argtypes = [vp, vp, i64, vp, i32, vp, i32, P, vp, i64, ctypes.POINTER(i64)]
+    lib.sedef_selfsearch_host.argtypes = [vp, vp, vp, i32, P, vp, i64, ctypes.POINTER(i64)]
+    lib.sedef_trace_enable.argtypes = [vp, ctypes.c_int]
+    lib.sedef_trace_report.argtypes = [vp, ctypes.c_char_p, i64, ctypes.c_int]
+    lib.sedef_launch_count.restype = ctypes.c_uint64
+    lib.sedef_launch_count.argtypes = []
+    for name in EXPORTS:
+        if name not in ("sedef_default_params", "sedef_last_error", "sedef_launch_count"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class SedefError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libsedef status {status}: {msg}")
+        self.status = status
+
+
+def _check(status: int):
+    if status != SEDEF_OK:
+        raise SedefError(status, load().sedef_last_error().decode())
+
+
+def params(**kw) -> Params:
+    p = Params()
+    load().sedef_default_params(ctypes.byref(p))
+    for key, v in kw.items():
+        if key == "step":
+            key = "query_step"
+        setattr(p, key, v)
+    return p
+
+
+def params_from_dict(d: dict) -> Params:
+    keys = {"k", "w", "n", "step", "max_occ", "self_mode", "gap_max", "diag_max",
+            "min_unmasked", "delta_m", "delta_g"}
+    return params(**{k: v for k, v in d.items() if k in keys})
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _offsets(off) -> np.ndarray:
+    return np.ascontiguousarray(off, dtype=np.int64)
+
+
+class Context:
+    """A libsedef context bound to one device and one CUDA stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        _check(self.lib.sedef_create(device, ctypes.c_void_p(self.stream.cuda_stream),
+                                     ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            self.lib.sedef_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _empty(self, n, dtype):
+        return self.torch.empty(max(int(n), 1), dtype=dtype, device=self.device)
+
+    # -- tracing ----------------------------------------------------------------
+
+    def sedef_trace_enable(self, on: bool = True):
+        _check(self.lib.sedef_trace_enable(self.handle, 1 if on else 0))
+
+    def sedef_trace_report(self, reset: bool = True) -> dict:
+        """{kernel name: (launches, total ms)} since the last reset."""
+        n = self.lib.sedef_trace_report(self.handle, None, 0, 0)
+        if n < 0:
+            _check(n)
+        buf = ctypes.create_string_buffer(n + 1)
+        self.lib.sedef_trace_report(self.handle, buf, n + 1, 1 if reset else 0)
+        out = {}
+        for line in buf.value.decode().splitlines():
+            name, cnt, ms = line.split()
+            out[name] = (int(cnt), float(ms))
+        return out
+
+    @staticmethod
+    def sedef_launch_count() -> int:
+        return int(load().sedef_launch_count())
+
+    # -- stages ---------------------------------------------------------------
+
+    def sedef_pack(self, d_seq):
+        n = d_seq.numel()
+        t = self.torch
+        packed = self._empty((n + 15) // 16, t.int32)
+        mask = self._empty((n + 31) // 32, t.int32)
+        nbits = self._empty((n + 31) // 32, t.int32)
+        _check(self.lib.sedef_pack(self.handle, _ptr(d_seq), n, _ptr(packed), _ptr(mask),
+                                   _ptr(nbits)))
+        return packed, mask, nbits
+
+    def sedef_sketch(self, packed, mask, nbits, offsets, p: Params, cap=None):
+        off = _offsets(offsets)
+        n = int(off[-1])
+        cap = cap if cap is not None else n // 4 + 1024
+        count = ctypes.c_int64()
+        for _ in range(2):
+            rec = self._empty(cap, self.torch.int64)
+            st = self.lib.sedef_sketch(self.handle, _ptr(packed), _ptr(mask), _ptr(nbits),
+                                       off.ctypes.data, len(off) - 1, ctypes.byref(p), _ptr(rec),
+                                       cap, ctypes.byref(count))
+            if st == SEDEF_ERR_CAPACITY:
+                cap = count.value
+                continue
+            _check(st)
+            return rec[:count.value]
+        raise SedefError(SEDEF_ERR_CAPACITY, "sketch capacity")
+
+    def sedef_index(self, rec, p: Params):
+        t = self.torch
+        nrec = rec.numel()
+        srt = self._empty(nrec, t.int64)
+        off = self._empty((1 << (2 * p.k)) + 1, t.int32)
+        _check(self.lib.sedef_index(self.handle, _ptr(rec), nrec, ctypes.byref(p), _ptr(srt),
+                                    _ptr(off)))
+        return srt[:nrec], off
+
+    def sedef_filter(self, qrec, qoff, trec, tsorted, toff_tab, toff, p: Params, cap=None):
+        qo, to = _offsets(qoff), _offsets(toff)
+        cap = cap if cap is not None else max(4096, int(qo[-1]) // 64)
+        count = ctypes.c_int64()
+        for _ in range(2):
+            runs = self._empty(cap * RUN_DTYPE.itemsize, self.torch.uint8)
+            st = self.lib.sedef_filter(self.handle, _ptr(qrec), qrec.numel(), qo.ctypes.data,
+                                       len(qo) - 1, _ptr(trec), _ptr(tsorted), _ptr(toff_tab),
+                                       trec.numel(), to.ctypes.data, len(to) - 1, ctypes.byref(p),
+                                       _ptr(runs), cap, ctypes.byref(count))
+            if st == SEDEF_ERR_CAPACITY:
+                cap = count.value
+                continue
+            _check(st)
+            return runs[:count.value * RUN_DTYPE.itemsize], count.value
+        raise SedefError(SEDEF_ERR_CAPACITY, "filter capacity")
+
+    def sedef_chain(self, runs, nruns, qrec, qoff, tsorted, toff_tab, toff, p: Params):
+        qo, to = _offsets(qoff), _offsets(toff)
+        cap = max(int(nruns), 1)
+        count = ctypes.c_int64()
+        chains = self._empty(cap * CHAIN_DTYPE.itemsize, self.torch.uint8)
+        _check(self.lib.sedef_chain(self.handle, _ptr(runs), nruns, _ptr(qrec), qrec.numel(),
+                                    qo.ctypes.data, len(qo) - 1, _ptr(tsorted), _ptr(toff_tab),
+                                    tsorted.numel(), to.ctypes.data, len(to) - 1, ctypes.byref(p),
+                                    _ptr(chains), cap, ctypes.byref(count)))
+        return chains[:count.value * CHAIN_DTYPE.itemsize], count.value
+
+    def sedef_merge(self, chains, nchains, qoff, toff, p: Params):
+        qo, to = _offsets(qoff), _offsets(toff)
+        cap = max(int(nchains), 1)
+        count = ctypes.c_int64()
+        cands = self._empty(cap * CAND_DTYPE.itemsize, self.torch.uint8)
+        _check(self.lib.sedef_merge(self.handle, _ptr(chains), nchains, qo.ctypes.data,
+                                    len(qo) - 1, to.ctypes.data, len(to) - 1, ctypes.byref(p),
+                                    _ptr(cands), cap, ctypes.byref(count)))
+        return cands[:count.value * CAND_DTYPE.itemsize], count.value
+
+    def sedef_selfsearch_host(self, seq: np.ndarray, offsets, p: Params, cap=None):
+        seq = np.ascontiguousarray(seq, dtype=np.uint8)
+        off = _offsets(offsets)
+        cap = cap if cap is not None else max(1024, len(seq) // 1000)
+        count = ctypes.c_int64()
+        for _ in range(2):
+            out = np.zeros(cap, dtype=CAND_DTYPE)
+            st = self.lib.sedef_selfsearch_host(self.handle, seq.ctypes.data, off.ctypes.data,
+                                                len(off) - 1, ctypes.byref(p), out.ctypes.data,
+                                                cap, ctypes.byref(count))
+            if st == SEDEF_ERR_CAPACITY:
+                cap = count.value
+                continue
+            _check(st)
+            return out[:count.value]
+        raise SedefError(SEDEF_ERR_CAPACITY, "selfsearch capacity")
+
+    # -- whole path -------------------------------------------------------------
+
+    def selfsearch(self, d_seq, offsets, p: Params):
+        """All stages on a device-resident sequence; returns every output."""
+        packed, mask, nbits = self.sedef_pack(d_seq)
+        rec = self.sedef_sketch(packed, mask, nbits, offsets, p)
+        srt, off = self.sedef_index(rec, p)
+        runs, nruns = self.sedef_filter(rec, offsets, rec, srt, off, offsets, p)
+        chains, nch = self.sedef_chain(runs, nruns, rec, offsets, srt, off, offsets, p)
+        cands, nc = self.sedef_merge(chains, nch, offsets, offsets, p)
+        return dict(packed=packed, mask=mask, nbits=nbits, rec=rec, sorted=srt, off=off,
+                    runs=runs, nruns=nruns, chains=chains, nchains=nch, cands=cands, ncands=nc)
+
+
+def to_numpy_records(t) -> np.ndarray:
+    """Device int64 record tensor -> numpy uint64."""
+    return t.cpu().numpy().view(np.uint64)
+
+
+def records_to_rows(rec: np.ndarray) -> np.ndarray:
+    """uint64 records -> int64 rows (hash, pos, strand) as the oracle prints them."""
+    rec = rec.view(np.uint64)
+    out = np.zeros((len(rec), 3), dtype=np.int64)
+    out[:, 0] = (rec >> np.uint64(33)).astype(np.int64)
+    out[:, 1] = ((rec >> np.uint64(1)) & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    out[:, 2] = (rec & np.uint64(1)).astype(np.int64)
+    return out
+
+
+def struct_view(t, dtype) -> np.ndarray:
+    return t.cpu().numpy().view(dtype)

@@ -1,0 +1,529 @@
+// C ABI entry points, context, scratch pool and parameter checks.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+
+#include <atomic>
+#include <map>
+
+struct sedef_ctx {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  sedef::Pool pool;
+  void* pinned = nullptr;
+  size_t pinned_cap = 0;
+  // tracing: one (name, start, stop) per traced launch since the last report
+  bool trace = false;
+  struct Mark {
+    const char* name;
+    cudaEvent_t start, stop;
+  };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> spare;  // recycled events
+};
+
+namespace sedef {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int status, const std::string& msg) {
+  g_last_error = msg;
+  return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? SEDEF_ERR_OOM : SEDEF_ERR_CUDA;
+}
+
+void* Pool::alloc(size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255) & ~size_t(255);
+  int best = -1;
+  for (size_t b = 0; b < blocks.size(); ++b)
+    if (!blocks[b].used && blocks[b].size >= bytes &&
+        (best < 0 || blocks[b].size < blocks[best].size))
+      best = (int)b;
+  if (best >= 0) {
+    blocks[best].used = true;
+    return blocks[best].ptr;
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  blocks.push_back({p, bytes, true});
+  return p;
+}
+
+void Pool::reset() {
+  for (auto& b : blocks) b.used = false;
+}
+
+void Pool::release() {
+  for (auto& b : blocks) cudaFree(b.ptr);
+  blocks.clear();
+}
+
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static cudaEvent_t take_event(sedef_ctx* c) {
+  if (!c->spare.empty()) {
+    cudaEvent_t e = c->spare.back();
+    c->spare.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+TraceScope::TraceScope(sedef_ctx* c, const char* name) : ctx(c), slot(-1) {
+  if (!c || !c->trace) return;
+  cudaEvent_t a = take_event(c), b = take_event(c);
+  if (!a || !b) return;
+  cudaEventRecord(a, c->stream);
+  c->marks.push_back({name, a, b});
+  slot = (int)c->marks.size() - 1;
+}
+
+TraceScope::~TraceScope() {
+  if (slot >= 0) cudaEventRecord(ctx->marks[slot].stop, ctx->stream);
+}
+
+cudaStream_t ctx_stream(sedef_ctx* ctx) { return ctx->stream; }
+int ctx_device(sedef_ctx* ctx) { return ctx->device; }
+int ctx_sm_count(sedef_ctx* ctx) { return ctx->sm_count; }
+
+void* ctx_alloc(sedef_ctx* ctx, size_t bytes) {
+  void* p = ctx->pool.alloc(bytes);
+  if (!p) set_error("device scratch allocation of " + std::to_string(bytes) + " bytes failed");
+  return p;
+}
+
+// Pinned staging for small uploads and counters.  The stream is drained
+// before the buffer is handed out again, so an earlier async copy from it
+// has completed.
+void* ctx_host(sedef_ctx* ctx, size_t bytes) {
+  cudaStreamSynchronize(ctx->stream);
+  if (bytes > ctx->pinned_cap) {
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    ctx->pinned = nullptr;
+    size_t cap = bytes < 65536 ? 65536 : bytes * 2;
+    if (cudaMallocHost(&ctx->pinned, cap) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->pinned_cap = 0;
+      set_error("pinned host allocation failed");
+      return nullptr;
+    }
+    ctx->pinned_cap = cap;
+  }
+  return ctx->pinned;
+}
+
+int derive(const sedef_params* p, Derived* d) {
+  if (!p) return fail(SEDEF_ERR_INVALID, "params is NULL");
+  if (p->k < 2 || p->k > 15) return fail(SEDEF_ERR_UNSUPPORTED, "k must be in [2, 15]");
+  if (p->w < 1 || p->w > 256) return fail(SEDEF_ERR_UNSUPPORTED, "w must be in [1, 256]");
+  if (p->n <= p->k) return fail(SEDEF_ERR_UNSUPPORTED, "n must exceed k");
+  if (p->n - p->k + 1 > kMaxWindowRecs)
+    return fail(SEDEF_ERR_UNSUPPORTED, "n - k + 1 must be at most 1024");
+  if (p->query_step < 1) return fail(SEDEF_ERR_INVALID, "query_step must be >= 1");
+  if (p->max_occ < 0 || p->gap_max < 0 || p->diag_max < 0 || p->min_unmasked < 0)
+    return fail(SEDEF_ERR_INVALID, "negative limit");
+  if (!(p->delta_m >= 0 && p->delta_g >= 0 && p->delta_g < 1))
+    return fail(SEDEF_ERR_INVALID, "delta_m, delta_g out of range");
+  d->k = p->k;
+  d->w = p->w;
+  d->n = p->n;
+  d->span = p->n - p->k;
+  d->step = p->query_step;
+  d->max_occ = p->max_occ;
+  d->self_mode = p->self_mode ? 1 : 0;
+  d->gap_max = p->gap_max;
+  d->diag_max = p->diag_max;
+  d->min_unmasked = p->min_unmasked;
+  d->overlap = (int)std::floor((p->delta_m + p->delta_g) * (double)p->n);
+  d->kmask = (uint32_t)((1ull << (2 * p->k)) - 1);
+  d->delta_g = p->delta_g;
+  return SEDEF_OK;
+}
+
+// m(s) table for s in [0, smax] (Section 3.1 tau; Section 2.2 count test).
+static void mtable(const sedef_params* p, int32_t* m, int smax, double* tau_out) {
+  const double tau = (1.0 - p->delta_g) / (1.0 + p->delta_g) *
+                     (1.0 / (2.0 * std::exp((double)p->k * p->delta_m) - 1.0));
+  if (tau_out) *tau_out = tau;
+  if (!m) return;
+  for (int s = 0; s <= smax; ++s) {
+    double need = tau * (double)s - 1e-9;
+    int32_t v = (int32_t)std::ceil(need);
+    if (v < 0) v = 0;
+    // least integer >= need
+    while ((double)(v - 1) >= need && v > 0) --v;
+    while ((double)v < need) ++v;
+    m[s] = v;
+  }
+}
+
+static int check_offsets(const int64_t* off, int nseq, const char* what) {
+  if (nseq < 0 || (nseq > 0 && !off)) return fail(SEDEF_ERR_INVALID, std::string(what) + ": bad offsets");
+  if (nseq == 0) return SEDEF_OK;
+  if (off[0] != 0) return fail(SEDEF_ERR_INVALID, std::string(what) + ": offsets must start at 0");
+  for (int s = 0; s < nseq; ++s)
+    if (off[s + 1] < off[s]) return fail(SEDEF_ERR_INVALID, std::string(what) + ": offsets decrease");
+  if (off[nseq] >= (int64_t(1) << 32))
+    return fail(SEDEF_ERR_UNSUPPORTED, std::string(what) + ": total length must be < 2^32");
+  return SEDEF_OK;
+}
+
+}  // namespace sedef
+
+using namespace sedef;
+
+extern "C" {
+
+void sedef_default_params(sedef_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->k = 12;
+  p->w = 16;
+  p->n = 750;
+  p->query_step = 250;
+  p->max_occ = 0;
+  p->self_mode = 1;
+  p->gap_max = 750;
+  p->diag_max = 75;
+  p->min_unmasked = 1;
+  p->delta_m = 0.15;
+  p->delta_g = 0.10;
+}
+
+const char* sedef_last_error(void) { return g_last_error.c_str(); }
+
+int sedef_create(int device, void* stream, sedef_ctx** out) {
+  if (!out) return fail(SEDEF_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  SEDEF_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(SEDEF_ERR_INVALID, "no such device");
+  SEDEF_CUDA(cudaSetDevice(device));
+  sedef_ctx* c = new sedef_ctx();
+  c->device = device;
+  c->pool.device = device;
+  c->stream = (cudaStream_t)stream;
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  *out = c;
+  return SEDEF_OK;
+}
+
+int sedef_destroy(sedef_ctx* ctx) {
+  if (!ctx) return SEDEF_OK;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& m : ctx->marks) {
+    cudaEventDestroy(m.start);
+    cudaEventDestroy(m.stop);
+  }
+  for (auto e : ctx->spare) cudaEventDestroy(e);
+  ctx->pool.release();
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  delete ctx;
+  return SEDEF_OK;
+}
+
+int sedef_set_stream(sedef_ctx* ctx, void* stream) {
+  if (!ctx) return fail(SEDEF_ERR_INVALID, "ctx is NULL");
+  cudaStreamSynchronize(ctx->stream);
+  ctx->stream = (cudaStream_t)stream;
+  return SEDEF_OK;
+}
+
+int sedef_trace_enable(sedef_ctx* ctx, int on) {
+  if (!ctx) return fail(SEDEF_ERR_INVALID, "ctx is NULL");
+  ctx->trace = on != 0;
+  return SEDEF_OK;
+}
+
+int sedef_trace_report(sedef_ctx* ctx, char* buf, int64_t cap, int reset) {
+  if (!ctx || (cap > 0 && !buf)) return fail(SEDEF_ERR_INVALID, "bad arguments");
+  SEDEF_CUDA(cudaStreamSynchronize(ctx->stream));
+  std::map<std::string, std::pair<long, double>> agg;
+  std::vector<std::string> order;
+  for (auto& m : ctx->marks) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, m.start, m.stop);
+    auto it = agg.find(m.name);
+    if (it == agg.end()) {
+      order.push_back(m.name);
+      agg[m.name] = {1, ms};
+    } else {
+      it->second.first += 1;
+      it->second.second += ms;
+    }
+  }
+  std::string out;
+  char line[256];
+  for (auto& n : order) {
+    std::snprintf(line, sizeof(line), "%s %ld %.6f\n", n.c_str(), agg[n].first, agg[n].second);
+    out += line;
+  }
+  if (reset) {
+    for (auto& m : ctx->marks) {
+      ctx->spare.push_back(m.start);
+      ctx->spare.push_back(m.stop);
+    }
+    ctx->marks.clear();
+  }
+  if (cap > 0) {
+    const size_t n = out.size() < (size_t)(cap - 1) ? out.size() : (size_t)(cap - 1);
+    std::memcpy(buf, out.data(), n);
+    buf[n] = 0;
+  }
+  return (int)out.size();
+}
+
+uint64_t sedef_launch_count(void) { return g_launches.load(); }
+
+int sedef_threshold_table(const sedef_params* p, int32_t* m_out, int32_t smax, double* tau_out) {
+  Derived d;
+  SEDEF_TRY(derive(p, &d));
+  if (smax < 0) return fail(SEDEF_ERR_INVALID, "smax < 0");
+  mtable(p, m_out, smax, tau_out);
+  return SEDEF_OK;
+}
+
+int sedef_pack(sedef_ctx* ctx, const uint8_t* d_seq, int64_t n, uint32_t* d_packed,
+               uint32_t* d_mask, uint32_t* d_nbits) {
+  if (!ctx) return fail(SEDEF_ERR_INVALID, "ctx is NULL");
+  if (n < 0) return fail(SEDEF_ERR_INVALID, "n < 0");
+  if (n == 0) return SEDEF_OK;
+  if (!d_seq || !d_packed || !d_mask || !d_nbits) return fail(SEDEF_ERR_INVALID, "NULL buffer");
+  if (n >= (int64_t(1) << 32)) return fail(SEDEF_ERR_UNSUPPORTED, "n must be < 2^32");
+  SEDEF_CUDA(cudaSetDevice(ctx->device));
+  return launch_pack(ctx, d_seq, n, d_packed, d_mask, d_nbits);
+}
+
+int sedef_sketch(sedef_ctx* ctx, const uint32_t* d_packed, const uint32_t* d_mask,
+                 const uint32_t* d_nbits, const int64_t* h_seq_off, int32_t nseq,
+                 const sedef_params* p, uint64_t* d_rec, int64_t rec_cap, int64_t* h_nrec) {
+  if (!ctx || !h_nrec) return fail(SEDEF_ERR_INVALID, "NULL argument");
+  Derived D;
+  SEDEF_TRY(derive(p, &D));
+  SEDEF_TRY(check_offsets(h_seq_off, nseq, "sedef_sketch"));
+  *h_nrec = 0;
+  if (nseq == 0 || h_seq_off[nseq] == 0) return SEDEF_OK;
+  if (!d_packed || !d_mask || !d_nbits) return fail(SEDEF_ERR_INVALID, "NULL input buffer");
+  if (rec_cap > 0 && !d_rec) return fail(SEDEF_ERR_INVALID, "NULL output buffer");
+  SEDEF_CUDA(cudaSetDevice(ctx->device));
+  ctx->pool.reset();
+  return run_sketch(ctx, d_packed, d_mask, d_nbits, h_seq_off, nseq, D, d_rec, rec_cap, h_nrec);
+}
+
+int sedef_index(sedef_ctx* ctx, const uint64_t* d_rec, int64_t nrec, const sedef_params* p,
+                uint64_t* d_sorted, uint32_t* d_off) {
+  if (!ctx) return fail(SEDEF_ERR_INVALID, "ctx is NULL");
+  Derived D;
+  SEDEF_TRY(derive(p, &D));
+  if (nrec < 0 || nrec >= (int64_t(1) << 32)) return fail(SEDEF_ERR_INVALID, "bad nrec");
+  if (!d_off || (nrec > 0 && (!d_rec || !d_sorted))) return fail(SEDEF_ERR_INVALID, "NULL buffer");
+  if (nrec > 0 && d_rec == d_sorted) return fail(SEDEF_ERR_INVALID, "d_rec and d_sorted overlap");
+  SEDEF_CUDA(cudaSetDevice(ctx->device));
+  ctx->pool.reset();
+  if (nrec > 0)
+    SEDEF_TRY(radix_sort_u64(ctx, d_rec, nullptr, d_sorted, nullptr, nrec, 33, 33 + 2 * D.k));
+  return build_offsets(ctx, d_sorted, nrec, D.k, d_off);
+}
+
+int sedef_filter(sedef_ctx* ctx, const uint64_t* d_qrec, int64_t nq, const int64_t* h_qoff,
+                 int32_t nqseq, const uint64_t* d_trec, const uint64_t* d_tsorted,
+                 const uint32_t* d_toff, int64_t nt, const int64_t* h_toff, int32_t ntseq,
+                 const sedef_params* p, sedef_run_t* d_runs, int64_t run_cap, int64_t* h_nruns) {
+  if (!ctx || !h_nruns) return fail(SEDEF_ERR_INVALID, "NULL argument");
+  Derived D;
+  SEDEF_TRY(derive(p, &D));
+  SEDEF_TRY(check_offsets(h_qoff, nqseq, "query"));
+  SEDEF_TRY(check_offsets(h_toff, ntseq, "target"));
+  if (D.self_mode && (nqseq != ntseq || d_qrec != d_trec || nq != nt))
+    return fail(SEDEF_ERR_INVALID, "self mode needs identical query and target");
+  if (D.self_mode)
+    for (int s = 0; s <= nqseq; ++s)
+      if (h_qoff[s] != h_toff[s]) return fail(SEDEF_ERR_INVALID, "self mode offsets differ");
+  if (nq < 0 || nt < 0 || (nq > 0 && !d_qrec) || (nt > 0 && (!d_trec || !d_tsorted)) || !d_toff)
+    return fail(SEDEF_ERR_INVALID, "bad record arrays");
+  if (run_cap > 0 && !d_runs) return fail(SEDEF_ERR_INVALID, "NULL output buffer");
+  SEDEF_CUDA(cudaSetDevice(ctx->device));
+  ctx->pool.reset();
+  std::vector<int32_t> mt(kMaxWindowRecs + 1);
+  mtable(p, mt.data(), kMaxWindowRecs, nullptr);
+  *h_nruns = 0;
+  return run_filter(ctx, d_qrec, nq, h_qoff, nqseq, d_trec, d_tsorted, d_toff, nt, h_toff, ntseq,
+                    D, mt.data(), d_runs, run_cap, h_nruns);
+}
+
+int sedef_chain(sedef_ctx* ctx, const sedef_run_t* d_runs, int64_t nruns, const uint64_t* d_qrec,
+                int64_t nq, const int64_t* h_qoff, int32_t nqseq, const uint64_t* d_tsorted,
+                const uint32_t* d_toff, int64_t nt, const int64_t* h_toff, int32_t ntseq,
+                const sedef_params* p, sedef_chain_t* d_chains, int64_t cap, int64_t* h_nchains) {
+  if (!ctx || !h_nchains) return fail(SEDEF_ERR_INVALID, "NULL argument");
+  Derived D;
+  SEDEF_TRY(derive(p, &D));
+  SEDEF_TRY(check_offsets(h_qoff, nqseq, "query"));
+  SEDEF_TRY(check_offsets(h_toff, ntseq, "target"));
+  if (nruns < 0 || (nruns > 0 && !d_runs)) return fail(SEDEF_ERR_INVALID, "bad runs");
+  if (cap > 0 && !d_chains) return fail(SEDEF_ERR_INVALID, "NULL output buffer");
+  SEDEF_CUDA(cudaSetDevice(ctx->device));
+  ctx->pool.reset();
+  std::vector<int32_t> mt(kMaxWindowRecs + 1);
+  mtable(p, mt.data(), kMaxWindowRecs, nullptr);
+  *h_nchains = 0;
+  if (nruns == 0) return SEDEF_OK;
+  if ((nq > 0 && !d_qrec) || (nt > 0 && !d_tsorted) || !d_toff)
+    return fail(SEDEF_ERR_INVALID, "bad record arrays");
+  return run_chain(ctx, d_runs, nruns, d_qrec, nq, h_qoff, nqseq, d_tsorted, nt, d_toff, h_toff,
+                   ntseq, D, mt.data(), d_chains, cap, h_nchains);
+}
+
+int sedef_merge(sedef_ctx* ctx, const sedef_chain_t* d_chains, int64_t nchains,
+                const int64_t* h_qoff, int32_t nqseq, const int64_t* h_toff, int32_t ntseq,
+                const sedef_params* p, sedef_cand_t* d_cands, int64_t cap, int64_t* h_ncands) {
+  if (!ctx || !h_ncands) return fail(SEDEF_ERR_INVALID, "NULL argument");
+  Derived D;
+  SEDEF_TRY(derive(p, &D));
+  SEDEF_TRY(check_offsets(h_qoff, nqseq, "query"));
+  SEDEF_TRY(check_offsets(h_toff, ntseq, "target"));
+  if (nchains < 0 || (nchains > 0 && !d_chains)) return fail(SEDEF_ERR_INVALID, "bad chains");
+  if (cap > 0 && !d_cands) return fail(SEDEF_ERR_INVALID, "NULL output buffer");
+  SEDEF_CUDA(cudaSetDevice(ctx->device));
+  ctx->pool.reset();
+  *h_ncands = 0;
+  if (nchains == 0) return SEDEF_OK;
+  return run_merge(ctx, d_chains, nchains, h_qoff, nqseq, h_toff, ntseq, D, d_cands, cap, h_ncands);
+}
+
+int sedef_selfsearch_host(sedef_ctx* ctx, const uint8_t* h_seq, const int64_t* h_seq_off,
+                          int32_t nseq, const sedef_params* p, sedef_cand_t* h_cands, int64_t cap,
+                          int64_t* h_ncands) {
+  if (!ctx || !h_ncands) return fail(SEDEF_ERR_INVALID, "NULL argument");
+  Derived D;
+  SEDEF_TRY(derive(p, &D));
+  SEDEF_TRY(check_offsets(h_seq_off, nseq, "sedef_selfsearch_host"));
+  if (!D.self_mode) return fail(SEDEF_ERR_INVALID, "self search needs self_mode = 1");
+  *h_ncands = 0;
+  if (nseq == 0 || h_seq_off[nseq] == 0) return SEDEF_OK;
+  if (!h_seq || (cap > 0 && !h_cands)) return fail(SEDEF_ERR_INVALID, "NULL buffer");
+  SEDEF_CUDA(cudaSetDevice(ctx->device));
+  const int64_t N = h_seq_off[nseq];
+  cudaStream_t st = ctx->stream;
+  // Buffers owned by this call (freed at the end); the stage calls use the
+  // context pool for their own scratch.
+  uint8_t* seq = nullptr;
+  uint32_t *packed = nullptr, *mask = nullptr, *nbits = nullptr, *off = nullptr;
+  uint64_t *rec = nullptr, *sorted = nullptr;
+  sedef_run_t* runs = nullptr;
+  sedef_chain_t* chains = nullptr;
+  sedef_cand_t* cands = nullptr;
+  int status = SEDEF_OK;
+  int64_t nrec = 0, nruns = 0, nch = 0, nc = 0;
+  const size_t nwords16 = (size_t)((N + 15) / 16), nwords32 = (size_t)((N + 31) / 32);
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    cudaFree(seq);
+    cudaFree(packed);
+    cudaFree(mask);
+    cudaFree(nbits);
+    cudaFree(off);
+    cudaFree(rec);
+    cudaFree(sorted);
+    cudaFree(runs);
+    cudaFree(chains);
+    cudaFree(cands);
+  };
+#define STEP(x)                   \
+  do {                            \
+    status = (x);                 \
+    if (status != SEDEF_OK) {     \
+      cleanup();                  \
+      return status;              \
+    }                             \
+  } while (0)
+#define DALLOC(ptr, bytes)                                                   \
+  do {                                                                       \
+    if (cudaMalloc((void**)&ptr, (bytes) ? (bytes) : 256) != cudaSuccess) {  \
+      cudaGetLastError();                                                    \
+      cleanup();                                                             \
+      return fail(SEDEF_ERR_OOM, "selfsearch: device allocation failed");    \
+    }                                                                        \
+  } while (0)
+  DALLOC(seq, (size_t)N);
+  DALLOC(packed, nwords16 * 4);
+  DALLOC(mask, nwords32 * 4);
+  DALLOC(nbits, nwords32 * 4);
+  if (cudaMemcpyAsync(seq, h_seq, (size_t)N, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    cleanup();
+    return fail(SEDEF_ERR_CUDA, "selfsearch: H2D copy failed");
+  }
+  STEP(sedef_pack(ctx, seq, N, packed, mask, nbits));
+  // sketch: start from the expected density and grow once if needed
+  int64_t rcap = N / 4 + 1024;
+  DALLOC(rec, (size_t)rcap * 8);
+  status = sedef_sketch(ctx, packed, mask, nbits, h_seq_off, nseq, p, rec, rcap, &nrec);
+  if (status == SEDEF_ERR_CAPACITY) {
+    cudaFree(rec);
+    rec = nullptr;
+    rcap = nrec;
+    DALLOC(rec, (size_t)rcap * 8);
+    status = sedef_sketch(ctx, packed, mask, nbits, h_seq_off, nseq, p, rec, rcap, &nrec);
+  }
+  STEP(status);
+  DALLOC(sorted, (size_t)(nrec ? nrec : 1) * 8);
+  DALLOC(off, ((size_t(1) << (2 * D.k)) + 1) * 4);
+  STEP(sedef_index(ctx, rec, nrec, p, sorted, off));
+  int64_t fcap = N / 64 + 4096;
+  DALLOC(runs, (size_t)fcap * sizeof(sedef_run_t));
+  status = sedef_filter(ctx, rec, nrec, h_seq_off, nseq, rec, sorted, off, nrec, h_seq_off, nseq, p,
+                        runs, fcap, &nruns);
+  if (status == SEDEF_ERR_CAPACITY) {
+    cudaFree(runs);
+    runs = nullptr;
+    fcap = nruns;
+    DALLOC(runs, (size_t)fcap * sizeof(sedef_run_t));
+    status = sedef_filter(ctx, rec, nrec, h_seq_off, nseq, rec, sorted, off, nrec, h_seq_off, nseq,
+                          p, runs, fcap, &nruns);
+  }
+  STEP(status);
+  DALLOC(chains, (size_t)(nruns ? nruns : 1) * sizeof(sedef_chain_t));
+  STEP(sedef_chain(ctx, runs, nruns, rec, nrec, h_seq_off, nseq, sorted, off, nrec, h_seq_off, nseq,
+                   p, chains, nruns, &nch));
+  DALLOC(cands, (size_t)(nch ? nch : 1) * sizeof(sedef_cand_t));
+  STEP(sedef_merge(ctx, chains, nch, h_seq_off, nseq, h_seq_off, nseq, p, cands, nch, &nc));
+  *h_ncands = nc;
+  if (nc > cap) {
+    cleanup();
+    return fail(SEDEF_ERR_CAPACITY, "selfsearch: candidate buffer too small");
+  }
+  if (nc > 0 &&
+      cudaMemcpyAsync(h_cands, cands, (size_t)nc * sizeof(sedef_cand_t), cudaMemcpyDeviceToHost,
+                      st) != cudaSuccess) {
+    cleanup();
+    return fail(SEDEF_ERR_CUDA, "selfsearch: D2H copy failed");
+  }
+  cleanup();
+#undef STEP
+#undef DALLOC
+  return SEDEF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,195 @@
+// Shared device/host helpers of the GB300 seeding-filter library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sedef.h"
+
+namespace sedef {
+
+constexpr uint32_t kInfHash = 0xFFFFFFFFu;  // ineligible k-mer: never selected
+constexpr int kMaxWindowRecs = 1024;        // n - k + 1 bound (records per window)
+
+// Host-side error reporting (thread-local message, negative status).
+void set_error(const std::string& msg);
+int fail(int status, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define SEDEF_CUDA(call)                                   \
+  do {                                                     \
+    cudaError_t _e = (call);                               \
+    if (_e != cudaSuccess) return ::sedef::cuda_fail(_e, #call); \
+  } while (0)
+
+#define SEDEF_LAUNCHED(name)                               \
+  do {                                                     \
+    cudaError_t _e = cudaGetLastError();                   \
+    if (_e != cudaSuccess) return ::sedef::cuda_fail(_e, name); \
+  } while (0)
+
+// Every kernel launch goes through SEDEF_KERNEL: it counts the launch,
+// brackets it with CUDA events when the context traces, and turns a launch
+// error into a status.
+#define SEDEF_KERNEL(ctx, name, ...)                                        \
+  do {                                                                      \
+    ::sedef::TraceScope _ts((ctx), (name));                                 \
+    __VA_ARGS__;                                                            \
+    ::sedef::count_launch();                                                \
+    cudaError_t _e = cudaGetLastError();                                    \
+    if (_e != cudaSuccess) return ::sedef::cuda_fail(_e, name);             \
+  } while (0)
+
+#define SEDEF_TRY(call)            \
+  do {                             \
+    int _s = (call);               \
+    if (_s != SEDEF_OK) return _s; \
+  } while (0)
+
+// Device scratch pool owned by a context.  Blocks are cudaMalloc'ed on
+// demand and reused; reset() releases every block for the next call (the
+// stream orders the next call's kernels after the previous ones).
+struct Pool {
+  struct Block {
+    void* ptr;
+    size_t size;
+    bool used;
+  };
+  std::vector<Block> blocks;
+  int device = 0;
+  void* alloc(size_t bytes);
+  void reset();
+  void release();
+};
+
+// Launch-time derived parameters shared by the kernels (computed on the host
+// from sedef_params).
+struct Derived {
+  int k, w, n, span;        // span = n - k: a window's k-mer starts are [j, j+span]
+  int step, max_occ, self_mode, gap_max, diag_max, min_unmasked;
+  int overlap;              // floor((delta_m + delta_g) * n)
+  uint32_t kmask;           // 4^k - 1
+  double delta_g;
+};
+
+int derive(const sedef_params* p, Derived* d);
+
+// ---------------------------------------------------------------- device ---
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Inclusive warp scan (add).
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_sum(T v) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T o = __shfl_up_sync(0xffffffffu, v, d);
+    if ((int)lane_id() >= d) v += o;
+  }
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+  return v;
+}
+
+// Block-wide exclusive scan of one value per thread (blockDim.x multiple of
+// 32, at most 1024).  `tmp` holds 33 ints of shared memory.  Returns the
+// exclusive prefix; *total receives the block sum.
+__device__ __forceinline__ int block_exclusive_sum(int v, int* tmp, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int inc = warp_inclusive_sum(v);
+  if (lane == 31) tmp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int x = lane < nw ? tmp[lane] : 0;
+    int xi = warp_inclusive_sum(x);
+    if (lane < nw) tmp[lane] = xi - x;
+    if (lane == 31) tmp[32] = xi;
+  }
+  __syncthreads();
+  int r = tmp[warp] + inc - v;
+  *total = tmp[32];
+  __syncthreads();
+  return r;
+}
+
+// First index in [lo, hi) of a sorted uint64 array whose value is >= key
+// under the projection proj.
+template <typename F>
+__device__ __forceinline__ int64_t lower_bound_by(const uint64_t* a, int64_t lo, int64_t hi,
+                                                  uint64_t key, F proj) {
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (proj(a[mid]) < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Record field access (layout in sedef.h).
+__device__ __forceinline__ uint32_t rec_hash(uint64_t r) { return (uint32_t)(r >> 33); }
+__device__ __forceinline__ uint32_t rec_pos(uint64_t r) { return (uint32_t)(r >> 1); }
+__device__ __forceinline__ uint32_t rec_strand(uint64_t r) { return (uint32_t)(r & 1u); }
+
+// Index of the sequence containing global position pos (offsets has nseq+1
+// entries, offsets[0] = 0).
+__device__ __forceinline__ int seq_of(const int64_t* off, int nseq, int64_t pos) {
+  int lo = 0, hi = nseq;  // answer in [0, nseq)
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (off[mid] <= pos) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+}  // namespace sedef
+
+// Launchers implemented in the kernel translation units.
+namespace sedef {
+struct Ctx;
+int launch_pack(sedef_ctx* ctx, const uint8_t* seq, int64_t n, uint32_t* packed, uint32_t* mask,
+                uint32_t* nbits);
+int run_sketch(sedef_ctx* ctx, const uint32_t* packed, const uint32_t* mask, const uint32_t* nbits,
+               const int64_t* h_off, int nseq, const Derived& D, uint64_t* rec, int64_t cap,
+               int64_t* nrec);
+int radix_sort_u64(sedef_ctx* ctx, const uint64_t* keys_in, const uint32_t* vals_in,
+                   uint64_t* keys_out, uint32_t* vals_out, int64_t n, int bit_lo, int bit_hi);
+int build_offsets(sedef_ctx* ctx, const uint64_t* sorted, int64_t n, int k, uint32_t* off);
+int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* h_qoff, int nqseq,
+               const uint64_t* trec, const uint64_t* tsorted, const uint32_t* toff, int64_t nt,
+               const int64_t* h_toff, int ntseq, const Derived& D, const int32_t* h_mtab,
+               sedef_run_t* runs, int64_t cap, int64_t* nruns);
+int run_chain(sedef_ctx* ctx, const sedef_run_t* runs, int64_t nruns, const uint64_t* qrec, int64_t nq,
+              const int64_t* h_qoff, int nqseq, const uint64_t* tsorted, int64_t nt,
+              const uint32_t* toff, const int64_t* h_toff, int ntseq, const Derived& D,
+              const int32_t* h_mtab, sedef_chain_t* chains, int64_t cap, int64_t* nchains);
+int run_merge(sedef_ctx* ctx, const sedef_chain_t* chains, int64_t nchains, const int64_t* h_qoff,
+              int nqseq, const int64_t* h_toff, int ntseq, const Derived& D, sedef_cand_t* cands,
+              int64_t cap, int64_t* ncands);
+// Tracing (per-kernel CUDA events on the context's stream) and launch count.
+void count_launch();
+struct TraceScope {
+  sedef_ctx* ctx;
+  int slot;
+  TraceScope(sedef_ctx* c, const char* name);
+  ~TraceScope();
+};
+// Context accessors for the kernel translation units.
+cudaStream_t ctx_stream(sedef_ctx* ctx);
+void* ctx_alloc(sedef_ctx* ctx, size_t bytes);
+void* ctx_host(sedef_ctx* ctx, size_t bytes);  // pinned host scratch
+int ctx_device(sedef_ctx* ctx);
+int ctx_sm_count(sedef_ctx* ctx);
+}  // namespace sedef

@@ -1,0 +1,327 @@
+// a1 pack and a2 sketch kernels.
+//
+// pack: 16 input bytes per thread (one 128-bit load), one packed word per
+// thread and one mask/N word per lane pair (warp shuffle), so every global
+// access is coalesced.  HBM-bound: 1 B read + 0.5 B written per base.
+//
+// sketch: one CTA per tile of 2048 consecutive windows.  The packed words,
+// mask and N bits of the tile (plus halo) are staged in shared memory; every
+// thread computes the canonical k-mer hashes of 8-9 positions from two 32-bit
+// words (forward code by bit reversal, reverse complement by complementing),
+// then the rightmost minimum of its 9 windows with a van Herk / Gil-Werman
+// split (suffix minima, a shared middle, prefix minima), and keeps a window's
+// argmin when it differs from the previous window's (winnowing argmins are
+// non-decreasing, so this emits each selected position once, in order).  A
+// count pass and a write pass bracket a device scan of the per-tile counts.
+#include "common.cuh"
+
+namespace sedef {
+
+namespace {
+
+__device__ __forceinline__ void classify(uint32_t b, uint32_t& code, uint32_t& masked,
+                                         uint32_t& isn) {
+  const uint32_t l = b | 0x20u;
+  const bool acgt = (l == 'a') | (l == 'c') | (l == 'g') | (l == 't');
+  code = acgt ? (((l >> 1) ^ (l >> 2)) & 3u) : 0u;  // a=0 c=1 g=2 t=3
+  masked = (b >= 'a' && b <= 'z') ? 1u : 0u;
+  isn = acgt ? 0u : 1u;
+}
+
+template <bool kAligned>
+__global__ void __launch_bounds__(256) k_pack(const uint8_t* __restrict__ seq, int64_t n,
+                                              uint32_t* __restrict__ packed,
+                                              uint32_t* __restrict__ mask,
+                                              uint32_t* __restrict__ nbits) {
+  const int64_t nchunk = (n + 15) >> 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nchunk; base += stride) {
+    const int64_t c = base + threadIdx.x;
+    uint32_t word = 0, m16 = 0, n16 = 0;
+    if (c < nchunk) {
+      const int64_t p0 = c << 4;
+      uint32_t v[4];
+      if (kAligned && p0 + 16 <= n) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(seq + p0));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+#pragma unroll
+        for (int x = 0; x < 16; ++x) {
+          uint32_t code, ms, isn;
+          classify((v[x >> 2] >> (8 * (x & 3))) & 0xFFu, code, ms, isn);
+          word |= code << (2 * x);
+          m16 |= ms << x;
+          n16 |= isn << x;
+        }
+      } else {
+        for (int x = 0; x < 16; ++x) {
+          if (p0 + x >= n) break;
+          uint32_t code, ms, isn;
+          classify(seq[p0 + x], code, ms, isn);
+          word |= code << (2 * x);
+          m16 |= ms << x;
+          n16 |= isn << x;
+        }
+      }
+    }
+    const uint32_t om = __shfl_down_sync(0xffffffffu, m16, 1);
+    const uint32_t on = __shfl_down_sync(0xffffffffu, n16, 1);
+    if (c < nchunk) {
+      packed[c] = word;
+      if ((c & 1) == 0) {
+        mask[c >> 1] = m16 | (om << 16);
+        nbits[c >> 1] = n16 | (on << 16);
+      }
+    }
+  }
+}
+
+constexpr int kSkThreads = 256;
+constexpr int kSkWPT = 8;                          // windows per thread
+constexpr int kSkTile = kSkThreads * kSkWPT;       // windows per CTA
+constexpr int kSkMaxW = 256;
+constexpr int kSkHashes = kSkTile + kSkMaxW;       // hash slots (tile + halo)
+constexpr int kSkWords16 = (kSkHashes + 16) / 16 + 4;
+constexpr int kSkWords32 = (kSkHashes + 16) / 32 + 4;
+
+// Canonical hash of the k-mer whose first base is bit-offset `sh` into the
+// 64-bit pair (lo, hi) of packed words.  Returns kInfHash for an ineligible
+// k-mer (N inside, too few unmasked bases, palindrome).
+__device__ __forceinline__ uint32_t bijective_hash(uint32_t x, int k, uint32_t M) {
+  // A permutation of [0, 4^k): xor-shift-right and odd multipliers, all
+  // modulo 2^(2k) (2k <= 30 bits, so 32-bit arithmetic is exact mod 2^(2k)).
+  x &= M;
+  x ^= x >> k;
+  x = (x * 0x7F4A7C15u) & M;
+  x ^= x >> (k - 1);
+  x = (x * 0x6659FD93u) & M;
+  x ^= x >> k;
+  return x;
+}
+
+struct SketchArgs {
+  const uint32_t* packed;
+  const uint32_t* mask;
+  const uint32_t* nbits;
+  const int64_t* off;  // nseq + 1 sequence offsets (device)
+  int nseq;
+  int64_t N;
+  int k, w, min_unmasked;
+  uint32_t kmask;
+  int64_t ntiles;
+};
+
+template <bool kWrite>
+__global__ void __launch_bounds__(kSkThreads) k_sketch(SketchArgs a, uint32_t* __restrict__ tile_count,
+                                                       const uint32_t* __restrict__ tile_offset,
+                                                       uint64_t* __restrict__ out, int64_t cap) {
+  __shared__ uint32_t s_pk[kSkWords16];
+  __shared__ uint32_t s_mk[kSkWords32];
+  __shared__ uint32_t s_nb[kSkWords32];
+  __shared__ uint32_t s_h[kSkHashes];
+  __shared__ uint8_t s_sg[kSkHashes];
+  __shared__ int s_tmp[33];
+
+  const int k = a.k, w = a.w;
+  const int tid = threadIdx.x;
+  for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const int64_t Q0 = tile * kSkTile;
+    const int64_t HB = Q0 - 1;                    // first hash position of the tile
+    const int nh = kSkTile + w;                   // hash positions [HB, HB + nh)
+    const int64_t b_lo = HB < 0 ? 0 : HB;
+    const int64_t wb16 = b_lo >> 4, wb32 = b_lo >> 5;
+    const int64_t nw16 = (a.N + 15) >> 4, nw32 = (a.N + 31) >> 5;
+    const int64_t last = HB + nh + k;             // one past the last base read
+    const int n16 = (int)(((last + 15) >> 4) - wb16 + 1);
+    const int n32 = (int)(((last + 31) >> 5) - wb32 + 1);
+    __syncthreads();
+    for (int x = tid; x < n16; x += kSkThreads) {
+      const int64_t g = wb16 + x;
+      s_pk[x] = g < nw16 ? __ldg(a.packed + g) : 0u;
+    }
+    for (int x = tid; x < n32; x += kSkThreads) {
+      const int64_t g = wb32 + x;
+      s_mk[x] = g < nw32 ? __ldg(a.mask + g) : 0xFFFFFFFFu;
+      s_nb[x] = g < nw32 ? __ldg(a.nbits + g) : 0xFFFFFFFFu;
+    }
+    __syncthreads();
+
+    // ---- hashes of positions HB + x, x in [0, nh)
+    {
+      const int per = (nh + kSkThreads - 1) / kSkThreads;
+      const int x0 = tid * per;
+      int64_t segend = -1, segstart = 0;
+      for (int r = 0; r < per; ++r) {
+        const int x = x0 + r;
+        if (x >= nh) break;
+        const int64_t p = HB + x;
+        uint32_t h = kInfHash, sg = 0;
+        if (p >= 0 && p + k <= a.N) {
+          if (p >= segend || p < segstart) {
+            const int s = seq_of(a.off, a.nseq, p);
+            segstart = a.off[s];
+            segend = a.off[s + 1];
+          }
+          if (p + k <= segend) {
+            const int64_t lp = p - (wb16 << 4);
+            const int wi = (int)(lp >> 4), sh = (int)(lp & 15) * 2;
+            const uint64_t pair = (uint64_t)s_pk[wi] | ((uint64_t)s_pk[wi + 1] << 32);
+            const uint32_t g = (uint32_t)(pair >> sh) & a.kmask;   // first base in the low bits
+            const int64_t lb = p - (wb32 << 5);
+            const int bi = (int)(lb >> 5), bs = (int)(lb & 31);
+            const uint64_t kb = (1ull << k) - 1;
+            const uint64_t nb = (((uint64_t)s_nb[bi] | ((uint64_t)s_nb[bi + 1] << 32)) >> bs) & kb;
+            const uint64_t mk = (((uint64_t)s_mk[bi] | ((uint64_t)s_mk[bi + 1] << 32)) >> bs) & kb;
+            // forward code: reverse the order of the k 2-bit groups
+            uint32_t f = __brev(g);
+            f = ((f >> 1) & 0x55555555u) | ((f & 0x55555555u) << 1);
+            f >>= (32 - 2 * k);
+            const uint32_t rc = g ^ a.kmask;  // complement each base, order reversed
+            const int unmasked = k - __popcll(mk);
+            if (nb == 0 && unmasked >= a.min_unmasked && f != rc) {
+              h = bijective_hash(f < rc ? f : rc, k, a.kmask);
+              sg = rc < f ? 1u : 0u;
+            }
+          }
+        }
+        s_h[x] = h;
+        s_sg[x] = (uint8_t)sg;
+      }
+    }
+    __syncthreads();
+
+    // ---- windows q = HB + B + t, t in [0, 9): local hash range [B + t, B + t + w)
+    const int B = tid * kSkWPT;
+    uint64_t key[kSkWPT + 1];
+    auto kx = [&](int x) -> uint64_t {
+      return ((uint64_t)s_h[x] << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)x);
+    };
+    if (w <= kSkWPT) {
+#pragma unroll
+      for (int t = 0; t <= kSkWPT; ++t) {
+        uint64_t m = ~0ull;
+        for (int x = B + t; x < B + t + w; ++x) m = min(m, kx(x));
+        key[t] = m;
+      }
+    } else {
+      // suffix minima over [B+t, B+7], middle over [B+8, B+w-1], prefix
+      // minima over [B+w, B+w+t-1]
+      uint64_t suf[kSkWPT + 1];
+      suf[kSkWPT] = ~0ull;
+#pragma unroll
+      for (int t = kSkWPT - 1; t >= 0; --t) suf[t] = min(suf[t + 1], kx(B + t));
+      uint64_t mid = ~0ull;
+      for (int x = B + kSkWPT; x < B + w; ++x) mid = min(mid, kx(x));
+      uint64_t pre = ~0ull;
+#pragma unroll
+      for (int t = 0; t <= kSkWPT; ++t) {
+        if (t > 0) pre = min(pre, kx(B + w + t - 1));
+        key[t] = min(min(suf[t], mid), pre);
+      }
+    }
+    // validity and selection flags for windows t = 1..8
+    uint32_t flags = 0;
+    {
+      int64_t segend = -1, segstart = 0;
+      bool prev_ok = false;
+      uint32_t prev_arg = 0;
+#pragma unroll
+      for (int t = 0; t <= kSkWPT; ++t) {
+        const int64_t q = HB + B + t;
+        bool ok = false;
+        if (q >= 0 && q + w + k - 1 <= a.N) {
+          if (q >= segend || q < segstart) {
+            const int s = seq_of(a.off, a.nseq, q);
+            segstart = a.off[s];
+            segend = a.off[s + 1];
+          }
+          ok = (q + w + k - 1 <= segend) && ((uint32_t)(key[t] >> 32) != kInfHash);
+        }
+        const uint32_t arg = 0xFFFFFFFFu - (uint32_t)key[t];
+        if (t > 0 && ok && !(prev_ok && prev_arg == arg)) flags |= 1u << t;
+        prev_ok = ok;
+        prev_arg = arg;
+      }
+    }
+    const int cnt = __popc(flags);
+    int total;
+    const int excl = block_exclusive_sum(cnt, s_tmp, &total);
+    if (!kWrite) {
+      if (tid == 0) tile_count[tile] = (uint32_t)total;
+    } else {
+      int64_t o = (int64_t)tile_offset[tile] + excl;
+#pragma unroll
+      for (int t = 1; t <= kSkWPT; ++t) {
+        if (flags >> t & 1u) {
+          const uint32_t x = 0xFFFFFFFFu - (uint32_t)key[t];
+          const uint64_t pos = (uint64_t)(HB + x);
+          if (o < cap)
+            out[o] = ((uint64_t)s_h[x] << 33) | (pos << 1) | (uint64_t)s_sg[x];
+          ++o;
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int launch_pack(sedef_ctx* ctx, const uint8_t* seq, int64_t n, uint32_t* packed, uint32_t* mask,
+                uint32_t* nbits) {
+  cudaStream_t st = ctx_stream(ctx);
+  const int64_t nchunk = (n + 15) / 16;
+  int64_t blocks = (nchunk + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  if (((uintptr_t)seq & 15) == 0)
+    SEDEF_KERNEL(ctx, "k_pack", k_pack<true><<<(int)blocks, 256, 0, st>>>(seq, n, packed, mask, nbits));
+  else
+    SEDEF_KERNEL(ctx, "k_pack", k_pack<false><<<(int)blocks, 256, 0, st>>>(seq, n, packed, mask, nbits));
+  return SEDEF_OK;
+}
+
+int scan_exclusive_u32(sedef_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n,
+                       uint32_t* d_total);
+
+int run_sketch(sedef_ctx* ctx, const uint32_t* packed, const uint32_t* mask, const uint32_t* nbits,
+               const int64_t* h_off, int nseq, const Derived& D, uint64_t* rec, int64_t cap,
+               int64_t* nrec) {
+  cudaStream_t st = ctx_stream(ctx);
+  const int64_t N = h_off[nseq];
+  SketchArgs a;
+  a.packed = packed;
+  a.mask = mask;
+  a.nbits = nbits;
+  a.nseq = nseq;
+  a.N = N;
+  a.k = D.k;
+  a.w = D.w;
+  a.min_unmasked = D.min_unmasked;
+  a.kmask = D.kmask;
+  const int64_t nwin = N;  // window starts q in [0, N)
+  a.ntiles = (nwin + kSkTile - 1) / kSkTile;
+  int64_t* d_off = (int64_t*)ctx_alloc(ctx, (size_t)(nseq + 1) * 8);
+  uint32_t* cnt = (uint32_t*)ctx_alloc(ctx, (size_t)(a.ntiles + 1) * 4);
+  uint32_t* toff = (uint32_t*)ctx_alloc(ctx, (size_t)(a.ntiles + 1) * 4);
+  if (!d_off || !cnt || !toff) return SEDEF_ERR_OOM;
+  SEDEF_CUDA(cudaMemcpyAsync(d_off, h_off, (size_t)(nseq + 1) * 8, cudaMemcpyHostToDevice, st));
+  SEDEF_CUDA(cudaStreamSynchronize(st));  // h_off is caller memory: copy before returning
+  a.off = d_off;
+  int64_t grid = a.ntiles;
+  const int64_t maxgrid = (int64_t)ctx_sm_count(ctx) * 8;
+  if (grid > maxgrid) grid = maxgrid;
+  SEDEF_KERNEL(ctx, "k_sketch_count",
+               k_sketch<false><<<(int)grid, kSkThreads, 0, st>>>(a, cnt, nullptr, nullptr, 0));
+  SEDEF_TRY(scan_exclusive_u32(ctx, cnt, toff, a.ntiles, toff + a.ntiles));
+  uint32_t* h_total = (uint32_t*)ctx_host(ctx, 8);
+  if (!h_total) return SEDEF_ERR_OOM;
+  SEDEF_CUDA(cudaMemcpyAsync(h_total, toff + a.ntiles, 4, cudaMemcpyDeviceToHost, st));
+  SEDEF_CUDA(cudaStreamSynchronize(st));
+  *nrec = *h_total;
+  if (*nrec > cap) return fail(SEDEF_ERR_CAPACITY, "sedef_sketch: record buffer too small");
+  SEDEF_KERNEL(ctx, "k_sketch_write",
+               k_sketch<true><<<(int)grid, kSkThreads, 0, st>>>(a, nullptr, toff, rec, cap));
+  SEDEF_CUDA(cudaStreamSynchronize(st));
+  return SEDEF_OK;
+}
+
+}  // namespace sedef
