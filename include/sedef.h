@@ -179,6 +179,14 @@ int sedef_trace_report(sedef_ctx* ctx, char* buf, int64_t cap, int reset);
 uint64_t sedef_launch_count(void);
 
 /*
+ * Counters of the context's last sedef_filter call, out[0..n): query
+ * windows, windows sent to the global-memory path, hits enumerated and hits
+ * collected by the shared-memory path, runs, runs refined by the large
+ * refine kernel (at most 8 values).
+ */
+int sedef_filter_stats(sedef_ctx* ctx, int64_t* out, int32_t n);
+
+/*
  * tau from the Section 3.1 bound, tau = (1-dG)/(1+dG) / (2 e^{k dM} - 1),
  * and m_out[s] = the least integer m with m >= tau*s - 1e-9 for s in
  * [0, smax].  m_out may be NULL.  Host only.

@@ -38,7 +38,7 @@ class Params(ctypes.Structure):
 
 
 EXPORTS = ["sedef_default_params", "sedef_last_error", "sedef_create", "sedef_destroy",
-           "sedef_set_stream", "sedef_trace_enable", "sedef_trace_report", "sedef_launch_count",
+           "sedef_set_stream", "sedef_trace_enable", "sedef_trace_report", "sedef_launch_count", "sedef_filter_stats",
            "sedef_threshold_table", "sedef_pack", "sedef_sketch",
            "sedef_index", "sedef_filter", "sedef_chain", "sedef_merge", "sedef_selfsearch_host"]
 
@@ -81,6 +81,7 @@ def load(build_if_missing: bool = True):
     lib.sedef_trace_report.argtypes = [vp, ctypes.c_char_p, i64, ctypes.c_int]
     lib.sedef_launch_count.restype = ctypes.c_uint64
     lib.sedef_launch_count.argtypes = []
+    lib.sedef_filter_stats.argtypes = [vp, vp, i32]
     for name in EXPORTS:
         if name not in ("sedef_default_params", "sedef_last_error", "sedef_launch_count"):
             getattr(lib, name).restype = ctypes.c_int
@@ -172,6 +173,12 @@ class Context:
             name, cnt, ms = line.split()
             out[name] = (int(cnt), float(ms))
         return out
+
+    def sedef_filter_stats(self) -> dict:
+        v = np.zeros(8, dtype=np.int64)
+        _check(self.lib.sedef_filter_stats(self.handle, v.ctypes.data, 8))
+        keys = ["windows", "overflow_windows", "hits", "collected", "runs", "big_refine"]
+        return {k: int(x) for k, x in zip(keys, v)}
 
     @staticmethod
     def sedef_launch_count() -> int:

@@ -24,6 +24,7 @@ struct sedef_ctx {
   };
   std::vector<Mark> marks;
   std::vector<cudaEvent_t> spare;  // recycled events
+  int64_t filter_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace sedef {
@@ -104,6 +105,10 @@ TraceScope::~TraceScope() {
 }
 
 cudaStream_t ctx_stream(sedef_ctx* ctx) { return ctx->stream; }
+
+void ctx_set_stats(sedef_ctx* ctx, const int64_t* v, int n) {
+  for (int x = 0; x < 8; ++x) ctx->filter_stats[x] = x < n ? v[x] : 0;
+}
 int ctx_device(sedef_ctx* ctx) { return ctx->device; }
 int ctx_sm_count(sedef_ctx* ctx) { return ctx->sm_count; }
 
@@ -296,6 +301,12 @@ int sedef_trace_report(sedef_ctx* ctx, char* buf, int64_t cap, int reset) {
 }
 
 uint64_t sedef_launch_count(void) { return g_launches.load(); }
+
+int sedef_filter_stats(sedef_ctx* ctx, int64_t* out, int32_t n) {
+  if (!ctx || (n > 0 && !out)) return fail(SEDEF_ERR_INVALID, "bad arguments");
+  for (int x = 0; x < n && x < 8; ++x) out[x] = ctx->filter_stats[x];
+  return SEDEF_OK;
+}
 
 int sedef_threshold_table(const sedef_params* p, int32_t* m_out, int32_t smax, double* tau_out) {
   Derived d;

@@ -192,4 +192,5 @@ void* ctx_alloc(sedef_ctx* ctx, size_t bytes);
 void* ctx_host(sedef_ctx* ctx, size_t bytes);  // pinned host scratch
 int ctx_device(sedef_ctx* ctx);
 int ctx_sm_count(sedef_ctx* ctx);
+void ctx_set_stats(sedef_ctx* ctx, const int64_t* v, int n);  // last sedef_filter call
 }  // namespace sedef

@@ -34,8 +34,9 @@ constexpr int kFThreads = 128;
 constexpr int kQCap = 256;        // query records per window (fast path)
 constexpr int kBinShift = 10;     // 1024-base bins (>= n - k + 1)
 constexpr int kSlots = 2048;      // (bin, o) counters (16-bit)
-constexpr int kLCap = 1024;       // collected hits (fast path)
+constexpr int kLCap = 2048;       // collected hits (fast path)
 constexpr int kHMax = 65535;      // hits per window (fast path; 16-bit counters)
+constexpr int kGCap = 512;        // dense groups per window (fast path)
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 
 struct FArgs {
@@ -60,6 +61,7 @@ struct FArgs {
   uint32_t* ov_list;
   unsigned int* nov;
   unsigned int* next_window;
+  unsigned long long* stats;  // [0] hits enumerated, [1] hits collected (fast path)
 };
 
 // ----------------------------------------------------------- run emission --
@@ -68,6 +70,9 @@ struct RunState {
   bool open;
   int64_t ja, jb, jmx;
   int mx;
+  // the target sequence that held the last position looked up
+  int64_t seq_lo = 0, seq_hi = -1;
+  int seq = 0;
 };
 
 struct WinInfo {
@@ -108,8 +113,13 @@ __device__ void segment(const FArgs& a, const WinInfo& w, RunState& r, int64_t j
   }
   int64_t x = j0 < 0 ? 0 : j0;
   while (x <= j1 && x < a.ttotal) {
-    const int u = seq_of(a.tseq, a.ntseq, x);
-    const int64_t st = a.tseq[u], en = a.tseq[u + 1];
+    if (x < r.seq_lo || x >= r.seq_hi) {
+      r.seq = seq_of(a.tseq, a.ntseq, x);
+      r.seq_lo = a.tseq[r.seq];
+      r.seq_hi = a.tseq[r.seq + 1];
+    }
+    const int u = r.seq;
+    const int64_t st = r.seq_lo, en = r.seq_hi;
     int64_t lo = st, hi = en - a.n;
     bool ok = true;
     if (a.self_mode) {
@@ -137,67 +147,107 @@ __device__ void segment(const FArgs& a, const WinInfo& w, RunState& r, int64_t j
   }
 }
 
-// Exact sweep over one strand's hits, sorted by t.  get(x) returns the hit's
-// (t, hid).  cnt[] holds one zeroed counter per hash id and is zero again on
-// return.
+// Exact sweep of one dense group [Jlo, Jhi] over one strand's hits (sorted
+// by t; get(x) returns (t, hid)).  cnt[] holds one zeroed counter per hash
+// id and is zero again on return.  A group never shares a run with another
+// (they are separated by target starts that cannot pass), so the run state
+// starts empty and every run is emitted before returning.  Single thread.
 template <typename Get>
-__device__ void sweep(const FArgs& a, WinInfo w, Get get, int64_t L, uint16_t* cnt) {
-  const int m = w.m, span = a.span;
+__device__ void sweep_group(const FArgs& a, const WinInfo& w, Get get, int64_t L, uint16_t* cnt,
+                            int64_t Jlo, int64_t Jhi) {
+  const int span = a.span;
   RunState r;
   r.open = false;
-  int64_t gl = 0, gh = -1;
-  bool have = false;
-  auto process = [&](int64_t Jlo, int64_t Jhi) {
-    // first hit with t >= Jlo
-    int64_t lo = 0, hi = L;
-    while (lo < hi) {
-      int64_t mid = (lo + hi) >> 1;
-      if ((int64_t)get(mid).x < Jlo) lo = mid + 1; else hi = mid;
+  int64_t lo = 0, hi = L;  // first hit with t >= Jlo
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)get(mid).x < Jlo) lo = mid + 1; else hi = mid;
+  }
+  int64_t e = lo, l = lo;
+  int shared = 0;
+  int64_t j = Jlo;
+  while (e < L && (int64_t)get(e).x <= j + span) {
+    if (cnt[get(e).y]++ == 0) ++shared;
+    ++e;
+  }
+  while (true) {
+    const int64_t ne = e < L ? (int64_t)get(e).x - span : INT64_MAX;
+    const int64_t nl = l < e ? (int64_t)get(l).x + 1 : INT64_MAX;
+    int64_t nx = min(ne, nl);
+    if (nx > Jhi + 1) nx = Jhi + 1;
+    segment(a, w, r, j, nx - 1, shared);
+    if (nx > Jhi) break;
+    j = nx;
+    while (l < e && (int64_t)get(l).x + 1 <= j) {
+      if (--cnt[get(l).y] == 0) --shared;
+      ++l;
     }
-    int64_t e = lo, l = lo;
-    int shared = 0;
-    int64_t j = Jlo;
-    while (e < L && (int64_t)get(e).x <= j + span) {
+    while (e < L && (int64_t)get(e).x - span <= j) {
       if (cnt[get(e).y]++ == 0) ++shared;
       ++e;
     }
-    while (true) {
-      const int64_t ne = e < L ? (int64_t)get(e).x - span : INT64_MAX;
-      const int64_t nl = l < e ? (int64_t)get(l).x + 1 : INT64_MAX;
-      int64_t nx = min(ne, nl);
-      if (nx > Jhi + 1) nx = Jhi + 1;
-      segment(a, w, r, j, nx - 1, shared);
-      if (nx > Jhi) break;
-      j = nx;
-      while (l < e && (int64_t)get(l).x + 1 <= j) {
-        if (--cnt[get(l).y] == 0) --shared;
-        ++l;
-      }
-      while (e < L && (int64_t)get(e).x - span <= j) {
-        if (cnt[get(e).y]++ == 0) ++shared;
-        ++e;
-      }
-    }
-    for (int64_t x = l; x < e; ++x) cnt[get(x).y] = 0;
-    // a count below m ends any run at the group's end (the next group is
-    // separated by j values that cannot pass)
-    segment(a, w, r, Jhi + 1, Jhi + 1, 0);
-  };
-  for (int64_t x = 0; x + m - 1 < L; ++x) {
-    const int64_t ta = get(x).x, tb = get(x + m - 1).x;
-    if (tb - ta > span) continue;
-    const int64_t jlo = tb - span, jhi = ta;
-    if (have && jlo <= gh + 1) {
-      if (jhi > gh) gh = jhi;
-    } else {
-      if (have) process(gl, gh);
-      have = true;
-      gl = jlo;
-      gh = jhi;
-    }
   }
-  if (have) process(gl, gh);
+  for (int64_t x = l; x < e; ++x) cnt[get(x).y] = 0;
   emit_run(a, w, r);
+}
+
+__device__ __forceinline__ int64_t warp_excl_max(int64_t v) {
+  const int lane = lane_id();
+  int64_t inc = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int64_t o = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d && o > inc) inc = o;
+  }
+  const int64_t ex = __shfl_up_sync(0xffffffffu, inc, 1);
+  return lane == 0 ? INT64_MIN : ex;
+}
+
+// Dense groups of one strand's t-sorted hits (warp-cooperative; every lane
+// calls).  Hit x is dense when the m hits from x on fit in n-k bases; every
+// j whose count reaches m lies in [t(x+m-1) - (n-k), t(x)] for some dense x.
+// Overlapping or touching such ranges form a group; emit(Jlo, Jhi) is called
+// by every lane, once per group, in increasing order.
+template <typename Get, typename Emit>
+__device__ void find_groups(Get get, int64_t L, int m, int span, Emit emit) {
+  const int lane = lane_id();
+  int64_t carry_hi = INT64_MIN;  // largest jhi of the dense hits seen so far
+  int64_t cur_lo = 0;
+  bool open = false;
+  for (int64_t base = 0; base + m - 1 < L; base += 32) {
+    const int64_t x = base + lane;
+    bool dense = false;
+    int64_t jlo = 0, jhi = INT64_MIN;
+    if (x + m - 1 < L) {
+      const int64_t ta = get(x).x, tb = get(x + m - 1).x;
+      if (tb - ta <= span) {
+        dense = true;
+        jlo = tb - span;
+        jhi = ta;
+      }
+    }
+    int64_t before = warp_excl_max(dense ? jhi : INT64_MIN);
+    if (carry_hi > before) before = carry_hi;
+    const bool start = dense && (before == INT64_MIN || jlo > before + 1);
+    unsigned starts = __ballot_sync(0xffffffffu, start);
+    while (starts) {
+      const int ls = __ffs(starts) - 1;
+      starts &= starts - 1;
+      const int64_t b_ls = __shfl_sync(0xffffffffu, before, ls);
+      const int64_t lo_ls = __shfl_sync(0xffffffffu, jlo, ls);
+      if (open) emit(cur_lo, b_ls);
+      cur_lo = lo_ls;
+      open = true;
+    }
+    int64_t mx = dense ? jhi : INT64_MIN;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      const int64_t o = __shfl_xor_sync(0xffffffffu, mx, d);
+      if (o > mx) mx = o;
+    }
+    if (mx > carry_hi) carry_hi = mx;
+  }
+  if (open) emit(cur_lo, carry_hi);
 }
 
 // ------------------------------------------------------ block bitonic sort --
@@ -207,7 +257,8 @@ __device__ void block_sort(T* v, int n) {  // n a power of two
   for (int size = 2; size <= n; size <<= 1)
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       for (int t = threadIdx.x; t < (n >> 1); t += blockDim.x) {
-        const int lo = 2 * stride * (t / stride) + (t % stride);
+        // pair t of this stage: stride is a power of two
+        const int lo = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));
         const int hi = lo + stride;
         const bool asc = (lo & size) == 0;
         const T x = v[lo], y = v[hi];
@@ -289,10 +340,12 @@ struct FastSmem {
   uint8_t dm[kQCap];
   uint32_t slots[kSlots / 2];  // two 16-bit counters per word
   unsigned long long hits[kLCap];
-  uint16_t cnt[kQCap];
+  uint32_t glo[kGCap];     // dense groups: Jlo (clamped to >= 0), Jhi
+  uint32_t ghi[kGCap];
+  uint16_t cnt[kFThreads / 32][kQCap];  // one counter array per warp
   int tmp[33];
   int64_t win;
-  int nhit, s, ovf;
+  int nhit, s, ovf, ng0, ng;
 };
 
 __device__ __forceinline__ uint32_t slot_of(uint32_t t, uint32_t o) {
@@ -325,7 +378,7 @@ __device__ __forceinline__ void for_hits(const FArgs& a, const FastSmem& S, int6
 __global__ void __launch_bounds__(kFThreads) k_filter_fast(FArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FastSmem& S = *reinterpret_cast<FastSmem*>(smem_raw);
-  for (int x = threadIdx.x; x < kQCap; x += blockDim.x) S.cnt[x] = 0;
+  for (int x = threadIdx.x; x < kQCap * (kFThreads / 32); x += blockDim.x) (&S.cnt[0][0])[x] = 0;
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) S.win = atomicAdd(a.next_window, 1u);
@@ -380,6 +433,7 @@ __global__ void __launch_bounds__(kFThreads) k_filter_fast(FArgs a) {
       continue;
     }
     const int m = a.mtab[s];
+    if (threadIdx.x == 0) atomicAdd(a.stats + 0, (unsigned long long)H);
     // pass 1: (bin, o) counts
     for_hits(a, S, i, (int)H, [&](uint32_t t, uint32_t, uint32_t o) {
       const uint32_t sl = slot_of(t, o);
@@ -404,6 +458,7 @@ __global__ void __launch_bounds__(kFThreads) k_filter_fast(FArgs a) {
     });
     __syncthreads();
     const int L = S.nhit;
+    if (threadIdx.x == 0) atomicAdd(a.stats + 1, (unsigned long long)L);
     if (L > kLCap) {
       if (threadIdx.x == 0) a.ov_list[atomicAdd(a.nov, 1u)] = (uint32_t)wdx;
       continue;
@@ -413,24 +468,63 @@ __global__ void __launch_bounds__(kFThreads) k_filter_fast(FArgs a) {
     for (int x = L + threadIdx.x; x < np; x += blockDim.x) S.hits[x] = ~0ull;
     __syncthreads();
     block_sort(S.hits, np);
-    if (threadIdx.x == 0) {
-      WinInfo w;
-      w.i = i;
-      w.qseq = a.win_seq[wdx];
-      w.s = s;
-      w.m = m;
-      int split = 0;
-      while (split < L && (S.hits[split] >> 63) == 0) ++split;
+    // dense groups of both strands (warp 0), then one warp per group
+    int split = 0;
+    {
+      // first hit with o = 1
+      int lo2 = 0, hi2 = L;
+      while (lo2 < hi2) {
+        const int mid = (lo2 + hi2) >> 1;
+        if ((S.hits[mid] >> 63) == 0) lo2 = mid + 1; else hi2 = mid;
+      }
+      split = lo2;
+    }
+    if (threadIdx.x < 32) {
+      int ng = 0;
       for (int o = 0; o < 2; ++o) {
-        w.o = o;
         const unsigned long long* base = S.hits + (o ? split : 0);
         const int64_t cnt = o ? L - split : split;
-        sweep(a, w,
-              [&](int64_t x) {
-                const unsigned long long h = base[x];
-                return make_uint2((uint32_t)(h >> 20), (uint32_t)(h & 0xFFFFFu));
-              },
-              cnt, S.cnt);
+        find_groups(
+            [&](int64_t x) {
+              const unsigned long long h = base[x];
+              return make_uint2((uint32_t)(h >> 20), (uint32_t)(h & 0xFFFFFu));
+            },
+            cnt, m, a.span, [&](int64_t lo, int64_t hi) {
+              if (threadIdx.x == 0 && ng < kGCap) {
+                S.glo[ng] = (uint32_t)(lo < 0 ? 0 : lo);
+                S.ghi[ng] = (uint32_t)hi;
+              }
+              ++ng;
+            });
+        if (o == 0 && threadIdx.x == 0) S.ng0 = ng;
+      }
+      if (threadIdx.x == 0) S.ng = ng;
+    }
+    __syncthreads();
+    const int ng = S.ng, ng0 = S.ng0;
+    if (ng > kGCap) {
+      if (threadIdx.x == 0) a.ov_list[atomicAdd(a.nov, 1u)] = (uint32_t)wdx;
+      continue;
+    }
+    {
+      const int warp = threadIdx.x >> 5;
+      if ((threadIdx.x & 31) == 0) {
+        WinInfo w;
+        w.i = i;
+        w.qseq = a.win_seq[wdx];
+        w.s = s;
+        w.m = m;
+        for (int g = warp; g < ng; g += kFThreads / 32) {
+          w.o = g < ng0 ? 0 : 1;
+          const unsigned long long* base = S.hits + (w.o ? split : 0);
+          const int64_t cnt = w.o ? L - split : split;
+          sweep_group(a, w,
+                      [&](int64_t x) {
+                        const unsigned long long h = base[x];
+                        return make_uint2((uint32_t)(h >> 20), (uint32_t)(h & 0xFFFFFu));
+                      },
+                      cnt, S.cnt[warp], (int64_t)S.glo[g], (int64_t)S.ghi[g]);
+        }
       }
     }
   }
@@ -527,40 +621,87 @@ __global__ void __launch_bounds__(kSThreads) k_slow_emit(FArgs a, int64_t v0, in
   }
 }
 
-__global__ void __launch_bounds__(32) k_slow_sweep(FArgs a, int64_t v0, int64_t v1,
-                                                   const unsigned long long* base,
-                                                   const int32_t* s_of, const uint64_t* keys,
-                                                   const uint32_t* vals) {
-  __shared__ uint16_t cnt[kMaxWindowRecs];
-  for (int x = threadIdx.x; x < kMaxWindowRecs; x += blockDim.x) cnt[x] = 0;
-  __syncwarp();
-  if (threadIdx.x != 0) return;
-  for (int64_t v = v0 + blockIdx.x; v < v1; v += gridDim.x) {
-    const int64_t wdx = a.ov_list[v];
+// Dense groups of the overflow windows [v0, v1): one warp per window and
+// strand writes one task (window, strand, Jlo, Jhi) per group.
+struct SlowTask {
+  uint32_t v;   // overflow-list index
+  uint32_t o;
+  int64_t jlo, jhi;
+};
+
+__device__ __forceinline__ void slow_segment(const uint64_t* keys, int64_t lo, int64_t hi,
+                                             int64_t* split) {
+  int64_t l = lo, h = hi;  // first key with o = 1
+  while (l < h) {
+    const int64_t mid = (l + h) >> 1;
+    if (((keys[mid] >> 32) & 1u) == 0) l = mid + 1; else h = mid;
+  }
+  *split = l;
+}
+
+__global__ void k_slow_groups(FArgs a, int64_t v0, int64_t v1, const unsigned long long* base,
+                              const int32_t* s_of, const uint64_t* keys, SlowTask* tasks,
+                              unsigned long long* ntask, int64_t task_cap) {
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = v0 + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < v1;
+       v += nw) {
     const int s = s_of[v];
     if (s == 0) continue;
+    const int m = a.mtab[s];
+    const int64_t lo = (int64_t)(base[v] - base[v0]), hi = (int64_t)(base[v + 1] - base[v0]);
+    int64_t split;
+    slow_segment(keys, lo, hi, &split);
+    for (int o = 0; o < 2; ++o) {
+      const int64_t b = o ? split : lo, e = o ? hi : split;
+      find_groups([&](int64_t x) { return make_uint2((uint32_t)keys[b + x], 0u); }, e - b, m,
+                  a.span, [&](int64_t jlo, int64_t jhi) {
+                    if (lane_id() == 0) {
+                      const unsigned long long at = atomicAdd(ntask, 1ull);
+                      if ((int64_t)at < task_cap) {
+                        SlowTask t;
+                        t.v = (uint32_t)v;
+                        t.o = (uint32_t)o;
+                        t.jlo = jlo < 0 ? 0 : jlo;
+                        t.jhi = jhi;
+                        tasks[at] = t;
+                      }
+                    }
+                  });
+    }
+  }
+}
+
+// One warp per task; lane 0 sweeps the group with the warp's counters.
+constexpr int kTaskWarps = 8;
+
+__global__ void __launch_bounds__(32 * kTaskWarps) k_slow_tasks(
+    FArgs a, int64_t v0, const unsigned long long* base, const int32_t* s_of,
+    const uint64_t* keys, const uint32_t* vals, const SlowTask* tasks,
+    const unsigned long long* ntask) {
+  __shared__ uint16_t cnt[kTaskWarps][kMaxWindowRecs];
+  const int warp = threadIdx.x >> 5;
+  for (int x = threadIdx.x & 31; x < kMaxWindowRecs; x += 32) cnt[warp][x] = 0;
+  __syncwarp();
+  if ((threadIdx.x & 31) != 0) return;
+  const int64_t nt = (int64_t)*ntask;
+  for (int64_t t = (int64_t)blockIdx.x * kTaskWarps + warp; t < nt;
+       t += (int64_t)gridDim.x * kTaskWarps) {
+    const SlowTask task = tasks[t];
+    const int64_t v = task.v;
+    const int64_t wdx = a.ov_list[v];
+    const int s = s_of[v];
     WinInfo w;
     w.i = a.win_i[wdx];
     w.qseq = a.win_seq[wdx];
     w.s = s;
     w.m = a.mtab[s];
+    w.o = (int)task.o;
     const int64_t lo = (int64_t)(base[v] - base[v0]), hi = (int64_t)(base[v + 1] - base[v0]);
-    int64_t split = lo;
-    {
-      int64_t l = lo, h = hi;
-      while (l < h) {
-        const int64_t mid = (l + h) >> 1;
-        if (((keys[mid] >> 32) & 1u) == 0) l = mid + 1; else h = mid;
-      }
-      split = l;
-    }
-    for (int o = 0; o < 2; ++o) {
-      w.o = o;
-      const int64_t b = o ? split : lo, e = o ? hi : split;
-      sweep(a, w,
-            [&](int64_t x) { return make_uint2((uint32_t)keys[b + x], vals[b + x]); },
-            e - b, cnt);
-    }
+    int64_t split;
+    slow_segment(keys, lo, hi, &split);
+    const int64_t b = task.o ? split : lo, e = task.o ? hi : split;
+    sweep_group(a, w, [&](int64_t x) { return make_uint2((uint32_t)keys[b + x], vals[b + x]); },
+                e - b, cnt[warp], task.jlo, task.jhi);
   }
 }
 
@@ -587,9 +728,30 @@ __global__ void k_windows(const uint64_t* __restrict__ qrec, int64_t nq,
   wseq[w] = lo;
 }
 
-__global__ void k_run_keys(const sedef_run_t* runs, int64_t n, uint64_t* keys) {
+// Sort keys of the runs: (window index, o, j_a).  part 0: the whole key
+// when it fits 64 bits; part 1: j_a alone and part 2: (window, o), for a
+// two-pass stable sort otherwise.
+__global__ void k_run_keys(const sedef_run_t* runs, int64_t n, const int64_t* qseq, int nqseq,
+                           const int64_t* wbase, int step, int part, uint64_t* keys) {
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x < n) keys[x] = ((uint64_t)runs[x].i << 1) | runs[x].o;
+  if (x >= n) return;
+  const sedef_run_t r = runs[x];
+  const int sq = seq_of(qseq, nqseq, r.i);
+  const uint64_t widx = (uint64_t)(wbase[sq] + ((int64_t)r.i - qseq[sq]) / step);
+  if (part == 0) keys[x] = (widx << 33) | ((uint64_t)r.o << 32) | r.j_a;
+  else if (part == 1) keys[x] = r.j_a;
+  else keys[x] = (widx << 1) | r.o;
+}
+
+__global__ void k_permute_u64(const uint64_t* in, const uint32_t* perm, int64_t n, uint64_t* out) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < n) out[x] = in[perm[x]];
+}
+
+__global__ void k_compose_perm(const uint32_t* first, const uint32_t* second, int64_t n,
+                               uint32_t* out) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < n) out[x] = first[second[x]];
 }
 
 __global__ void k_gather_runs(const sedef_run_t* in, const uint32_t* perm, int64_t n, sedef_run_t* out) {
@@ -598,28 +760,42 @@ __global__ void k_gather_runs(const sedef_run_t* in, const uint32_t* perm, int64
 }
 
 // ----------------------------------------------------------------- refine --
+//
+// Two instantiations of one kernel: a lean one (at most 256 query records
+// and 512 span records per run, one piece, ~12 KB of shared memory per warp
+// so that 16 warps per SM hide the latency of the sequential roll) and a
+// large one (any run, in pieces of at most 1024 span records) for the runs
+// the lean one hands over.
+//
+// The estimate at j never exceeds the number of W_Q hashes shared with the
+// window (the filter's shared_o(j)), so it is evaluated only where that
+// count exceeds the best estimate so far, and the run is finished as soon
+// as the best estimate reaches the run's max_shared.
 
-constexpr int kRWarps = 4;
-constexpr int kDCap = 2048;   // domain: |W_Q| + span records of one piece
-constexpr int kRCap = 1024;   // span records per piece
+constexpr int kRWarps = 8;     // lean kernel: warps per CTA
+constexpr int kRWarpsBig = 4;  // large kernel
 
-struct RefineWarp {
-  uint32_t dom[kDCap];       // sorted distinct hashes (W_Q u span)
-  uint16_t cntT[kDCap];      // records of this hash in the target window
-  uint16_t cntS[kDCap];      // shared-compatible records of this hash in the window
-  uint32_t pb[kDCap / 32];   // present: in W_Q or cntT > 0
-  uint32_t sb[kDCap / 32];   // shared: cntS > 0
-  uint32_t tpos[kRCap];      // span record positions (sorted)
-  uint16_t tdx[kRCap];       // domain index of each span record
-  uint8_t tsh[kRCap];        // record is shared-compatible
-  uint8_t qm[kDCap];         // strand mask for W_Q members (0 = not in W_Q)
+template <int QC, int RC>
+struct RefineWarpT {
+  static constexpr int DC = QC + RC;  // domain: W_Q u span hashes
+  uint32_t dom[DC];      // sorted distinct hashes
+  uint16_t cntT[DC];     // records of this hash in the target window
+  uint16_t cntS[DC];     // shared-compatible records of this hash in the window
+  uint8_t qm[DC];        // strand mask for W_Q members (0 = not in W_Q)
+  uint32_t pb[DC / 32];  // present: in W_Q or cntT > 0
+  uint32_t sb[DC / 32];  // shared: cntS > 0
+  uint32_t tpos[RC];     // span record positions (sorted)
+  uint16_t tdx[RC];      // domain index of each span record
+  uint8_t tsh[RC];       // record is shared-compatible
+  uint32_t wq_h[QC];     // W_Q hashes (sorted)
+  uint8_t wq_m[QC];      // W_Q strand masks
 };
 
 __device__ __forceinline__ void warp_sort_u32(uint32_t* v, int n) {  // n power of two
   for (int size = 2; size <= n; size <<= 1)
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       for (int t = lane_id(); t < (n >> 1); t += 32) {
-        const int lo = 2 * stride * (t / stride) + (t % stride);
+        const int lo = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));
         const int hi = lo + stride;
         const bool asc = (lo & size) == 0;
         const uint32_t x = v[lo], y = v[hi];
@@ -641,42 +817,44 @@ __device__ __forceinline__ int dom_find(const uint32_t* dom, int D, uint32_t h) 
   return lo;
 }
 
-// Estimate from the bitsets: shared bits among the first s present bits.
-__device__ __forceinline__ int estimate(const RefineWarp& R, int nwords, int s) {
+// theta = domain index of the s-th present bit, est = shared bits at or
+// below it (warp-wide; same word layout as estimate()).
+__device__ __forceinline__ void theta_est(const uint32_t* pb, const uint32_t* sb, int nwords,
+                                          int s, int* theta, int* est) {
   const int lane = lane_id();
-  const uint32_t p0 = (2 * lane < nwords) ? R.pb[2 * lane] : 0u;
-  const uint32_t p1 = (2 * lane + 1 < nwords) ? R.pb[2 * lane + 1] : 0u;
-  const uint32_t s0 = (2 * lane < nwords) ? R.sb[2 * lane] : 0u;
-  const uint32_t s1 = (2 * lane + 1 < nwords) ? R.sb[2 * lane + 1] : 0u;
+  const uint32_t p0 = (2 * lane < nwords) ? pb[2 * lane] : 0u;
+  const uint32_t p1 = (2 * lane + 1 < nwords) ? pb[2 * lane + 1] : 0u;
+  const uint32_t s0 = (2 * lane < nwords) ? sb[2 * lane] : 0u;
+  const uint32_t s1 = (2 * lane + 1 < nwords) ? sb[2 * lane + 1] : 0u;
   const int pc = __popc(p0) + __popc(p1);
   const int inc = warp_inclusive_sum(pc);
   const int before = inc - pc;
-  // lane holding the s-th present bit
   const unsigned owner = __ballot_sync(0xffffffffu, before < s && inc >= s);
   const int ol = __ffs(owner) - 1;
-  int est_full = (inc <= s) ? (__popc(s0) + __popc(s1)) : 0;  // lanes entirely inside
-  int part = 0;
+  int cnt = (inc < s) ? (__popc(s0) + __popc(s1)) : 0;  // lanes wholly below theta
+  int th = 0;
   if (lane == ol) {
-    int need = s - before;  // present bits to take from this lane's 64
-    uint32_t words_p[2] = {p0, p1}, words_s[2] = {s0, s1};
-    for (int x = 0; x < 2 && need > 0; ++x) {
-      const int c = __popc(words_p[x]);
-      if (c <= need) {
-        part += __popc(words_s[x]);
+    int need = s - before;
+    const uint32_t wp[2] = {p0, p1}, ws[2] = {s0, s1};
+    cnt = 0;
+    for (int x = 0; x < 2; ++x) {
+      const int c = __popc(wp[x]);
+      if (c < need) {
+        cnt += __popc(ws[x]);
         need -= c;
-      } else {
-        // position of the need-th set bit (1-based) of words_p[x]
-        uint32_t wv = words_p[x];
-        for (int y = 1; y < need; ++y) wv &= wv - 1u;
-        const int b = __ffs(wv) - 1;
-        const uint32_t below = (b >= 31) ? 0xFFFFFFFFu : ((2u << b) - 1u);
-        part += __popc(words_s[x] & below);
-        need = 0;
+        continue;
       }
+      uint32_t v = wp[x];
+      for (int y = 1; y < need; ++y) v &= v - 1u;
+      const int b = __ffs(v) - 1;
+      const uint32_t below = (b >= 31) ? 0xFFFFFFFFu : ((2u << b) - 1u);
+      cnt += __popc(ws[x] & below);
+      th = (2 * lane + x) * 32 + b;
+      break;
     }
-    est_full = 0;
   }
-  return warp_sum(est_full + part);
+  *est = warp_sum(cnt);
+  *theta = __shfl_sync(0xffffffffu, th, ol);
 }
 
 struct RefineArgs {
@@ -689,27 +867,44 @@ struct RefineArgs {
   const uint32_t* toff;
   const int32_t* mtab;
   int span, max_occ, self_mode;
+  uint32_t* big;        // runs handed to the large kernel
+  unsigned int* nbig;
 };
 
-__global__ void __launch_bounds__(32 * kRWarps) k_refine(RefineArgs a) {
+template <int QC, int RC, bool kLean>
+__global__ void __launch_bounds__(32 * (kLean ? kRWarps : kRWarpsBig)) k_refine(RefineArgs a) {
+  using RW = RefineWarpT<QC, RC>;
+  constexpr int DC = RW::DC;
+  constexpr int NW = kLean ? kRWarps : kRWarpsBig;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = lane_id();
-  RefineWarp& R = reinterpret_cast<RefineWarp*>(smem_raw)[warp];
+  RW& R = reinterpret_cast<RW*>(smem_raw)[warp];
   auto pos_of = [](uint64_t r) { return (uint64_t)((r >> 1) & 0xFFFFFFFFull); };
-  for (int64_t ri = (int64_t)blockIdx.x * kRWarps + warp; ri < a.nruns;
-       ri += (int64_t)gridDim.x * kRWarps) {
-    sedef_run_t run = a.runs[ri];
+  const int64_t count = kLean ? a.nruns : (int64_t)*a.nbig;
+  for (int64_t t = (int64_t)blockIdx.x * NW + warp; t < count; t += (int64_t)gridDim.x * NW) {
+    const int64_t ri = kLean ? t : (int64_t)a.big[t];
+    const sedef_run_t run = a.runs[ri];
     const int64_t i = run.i, ja = run.j_a, jb = run.j_b;
     const int o = run.o;
-    // ---- W_Q: sorted hashes with strand masks (capped hashes dropped)
-    int64_t qa = 0, qb = 0;
+    int64_t qa = 0, qb = 0, rlo = 0, rend = 0;
     if (lane == 0) {
       qa = lower_bound_by(a.qrec, 0, a.nq, (uint64_t)i, pos_of);
       qb = lower_bound_by(a.qrec, qa, a.nq, (uint64_t)(i + a.span + 1), pos_of);
+      rlo = lower_bound_by(a.trec, 0, a.nt, (uint64_t)ja, pos_of);
+      if (kLean) rend = lower_bound_by(a.trec, rlo, a.nt, (uint64_t)(jb + a.span + 1), pos_of);
     }
     qa = __shfl_sync(0xffffffffu, qa, 0);
     qb = __shfl_sync(0xffffffffu, qb, 0);
+    rlo = __shfl_sync(0xffffffffu, rlo, 0);
     const int c = (int)(qb - qa);
+    if (kLean) {
+      rend = __shfl_sync(0xffffffffu, rend, 0);
+      if (c > QC || rend - rlo > RC) {
+        if (lane == 0) a.big[atomicAdd(a.nbig, 1u)] = (uint32_t)ri;
+        continue;
+      }
+    }
+    // ---- W_Q: sorted hashes with strand masks (capped hashes dropped)
     const int npq = next_pow2(c < 2 ? 2 : c);
     for (int x = lane; x < npq; x += 32) {
       uint32_t key = kNone;
@@ -717,11 +912,10 @@ __global__ void __launch_bounds__(32 * kRWarps) k_refine(RefineArgs a) {
         const uint64_t r = a.qrec[qa + x];
         key = (rec_hash(r) << 1) | rec_strand(r);
       }
-      R.dom[x] = key;  // temporary use of dom as the sort buffer
+      R.dom[x] = key;  // the domain array doubles as the sort buffer
     }
     __syncwarp();
     warp_sort_u32(R.dom, npq);
-    // compact to distinct kept hashes in tpos (temporary) with masks in tsh
     int s = 0;
     for (int base = 0; base < c; base += 32) {
       const int x = base + lane;
@@ -738,58 +932,72 @@ __global__ void __launch_bounds__(32 * kRWarps) k_refine(RefineArgs a) {
       const unsigned bal = __ballot_sync(0xffffffffu, first);
       if (first) {
         const int d = s + __popc(bal & lanemask_lt());
-        R.tpos[d] = h;
-        R.tsh[d] = (uint8_t)mask;
+        R.wq_h[d] = h;
+        R.wq_m[d] = (uint8_t)mask;
       }
       s += __popc(bal);
     }
     __syncwarp();
-    // ---- pieces of the run: span records [P_lo, P_hi + span] <= kRCap
-    int best = -1, den = 0;
+    const int mx = run.max_shared;
+    int best = -1;
     int64_t jstar = ja;
-    // keep W_Q (hash, mask) in registers-by-stride: copy to the tail of dom later
-    // (W_Q has s <= 1024 entries, stored in tpos/tsh until the domain is built)
-    __shared__ uint32_t wq_h[kRWarps][kMaxWindowRecs];
-    __shared__ uint8_t wq_m[kRWarps][kMaxWindowRecs];
-    for (int x = lane; x < s; x += 32) {
-      wq_h[warp][x] = R.tpos[x];
-      wq_m[warp][x] = R.tsh[x];
-    }
-    __syncwarp();
     int64_t plo = ja;
-    int64_t rlo = 0;
-    if (lane == 0) rlo = lower_bound_by(a.trec, 0, a.nt, (uint64_t)ja, pos_of);
-    rlo = __shfl_sync(0xffffffffu, rlo, 0);
-    while (plo <= jb) {
-      // records of the piece: [rlo, rhi) with pos <= P_hi + span, at most kRCap
-      int64_t rcap_end = rlo + kRCap < a.nt ? rlo + kRCap : a.nt;
-      int64_t phi = jb;
-      int64_t rhi = 0;
+    bool finished = false;
+    while (plo <= jb && !finished) {
+      // ---- the piece [plo, phi]: span records [rlo, rhi), at most RC
+      int64_t phi = jb, rhi = 0;
       if (lane == 0) {
+        const int64_t rcap_end = rlo + RC < a.nt ? rlo + RC : a.nt;
         rhi = lower_bound_by(a.trec, rlo, a.nt, (uint64_t)(jb + a.span + 1), pos_of);
         if (rhi > rcap_end) {
-          // shrink the piece so that its records fit: P_hi + span < pos of
-          // the first record that does not fit
-          const int64_t lim = (int64_t)pos_of(a.trec[rcap_end]);
+          const int64_t lim = (int64_t)pos_of(a.trec[rcap_end]);  // first record that does not fit
           phi = lim - a.span - 1;
-          rhi = lower_bound_by(a.trec, rlo, a.nt, (uint64_t)(phi + a.span + 1), pos_of);
+          rhi = rcap_end;
         }
       }
       phi = __shfl_sync(0xffffffffu, phi, 0);
       rhi = __shfl_sync(0xffffffffu, rhi, 0);
       const int nr = (int)(rhi - rlo);
-      // ---- domain: sort W_Q hashes u record hashes
-      const int nd0 = s + nr;
+      // ---- relevant span records: a hash above max(W_Q) can never be in U
+      // (W_Q alone supplies s hashes at or below it) nor shared, so such
+      // records never change the estimate and are left out.  cntT/cntS
+      // double as a scratch array of the kept records' hashes until the
+      // domain is built.
+      const uint32_t qmax = s > 0 ? R.wq_h[s - 1] : 0u;
+      uint32_t* tmp_h = reinterpret_cast<uint32_t*>(R.cntT);  // DC u32 (cntT then cntS)
+      int nrel = 0;
+      for (int base = 0; base < nr; base += 32) {
+        const int x = base + lane;
+        bool keep = false;
+        uint32_t h = 0, t = 0, st = 0;
+        if (x < nr) {
+          const uint64_t r = a.trec[rlo + x];
+          h = rec_hash(r);
+          t = rec_pos(r);
+          st = rec_strand(r);
+          keep = h <= qmax;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+          const int y = nrel + __popc(bal & lanemask_lt());
+          R.tpos[y] = t;
+          tmp_h[y] = h;
+          R.tsh[y] = (uint8_t)st;  // strand for now
+        }
+        nrel += __popc(bal);
+      }
+      __syncwarp();
+      // ---- domain: sorted distinct hashes of W_Q u kept records
+      const int nd0 = s + nrel;
       const int npd = next_pow2(nd0 < 2 ? 2 : nd0);
       for (int x = lane; x < npd; x += 32) {
         uint32_t v = kNone;
-        if (x < s) v = wq_h[warp][x];
-        else if (x < nd0) v = rec_hash(a.trec[rlo + (x - s)]);
+        if (x < s) v = R.wq_h[x];
+        else if (x < nd0) v = tmp_h[x - s];
         R.dom[x] = v;
       }
       __syncwarp();
       warp_sort_u32(R.dom, npd);
-      // dedup in place (warp compaction in order)
       int D = 0;
       for (int base = 0; base < nd0; base += 32) {
         const int x = base + lane;
@@ -801,86 +1009,131 @@ __global__ void __launch_bounds__(32 * kRWarps) k_refine(RefineArgs a) {
         __syncwarp();
         D += __popc(bal);
       }
+      for (int x = lane; x < nrel; x += 32) R.tdx[x] = (uint16_t)dom_find(R.dom, D, tmp_h[x]);
+      __syncwarp();
       const int nwords = (D + 31) >> 5;
       for (int x = lane; x < D; x += 32) {
         R.cntT[x] = 0;
         R.cntS[x] = 0;
         R.qm[x] = 0;
       }
-      for (int x = lane; x < kDCap / 32; x += 32) {
+      for (int x = lane; x < DC / 32; x += 32) {
         R.pb[x] = 0;
         R.sb[x] = 0;
       }
       __syncwarp();
       for (int x = lane; x < s; x += 32) {
-        const int d = dom_find(R.dom, D, wq_h[warp][x]);
-        R.qm[d] = wq_m[warp][x];
+        const int d = dom_find(R.dom, D, R.wq_h[x]);
+        R.qm[d] = R.wq_m[x];
         atomicOr(&R.pb[d >> 5], 1u << (d & 31));
       }
       __syncwarp();
-      for (int x = lane; x < nr; x += 32) {
-        const uint64_t r = a.trec[rlo + x];
-        const uint32_t t = rec_pos(r), st = rec_strand(r);
-        const int d = dom_find(R.dom, D, rec_hash(r));
-        R.tpos[x] = t;
-        R.tdx[x] = (uint16_t)d;
+      for (int x = lane; x < nrel; x += 32) {
+        const uint32_t t = R.tpos[x], st = R.tsh[x];
+        const int d = R.tdx[x];
         const bool self = a.self_mode && (int64_t)t >= i && (int64_t)t <= i + a.span;
         R.tsh[x] = (!self && ((R.qm[d] >> (st ^ (uint32_t)o)) & 1u)) ? 1 : 0;
       }
       __syncwarp();
-      // ---- roll the target window over [plo, phi]
+      // ---- roll the target window over [plo, phi].  theta is the domain
+      // index of the s-th present hash (the largest member of U) and est the
+      // number of shared hashes at or below it.  After the first breakpoint
+      // lane 0 keeps both exact through every enter and leave, one record at
+      // a time: a hash joining below theta pushes theta down to its
+      // predecessor, one leaving at or below theta pulls theta up to its
+      // successor, and a W_Q hash at or below theta changes est when it
+      // becomes or stops being shared.
       int e = 0, l = 0;
       int64_t j = plo;
-      auto enter = [&](int x) {
-        const int d = R.tdx[x];
-        if (R.cntT[d]++ == 0) atomicOr(&R.pb[d >> 5], 1u << (d & 31));
-        if (R.tsh[x] && R.cntS[d]++ == 0) atomicOr(&R.sb[d >> 5], 1u << (d & 31));
-      };
-      auto leave = [&](int x) {
-        const int d = R.tdx[x];
-        if (--R.cntT[d] == 0 && R.qm[d] == 0) atomicAnd(&R.pb[d >> 5], ~(1u << (d & 31)));
-        if (R.tsh[x] && --R.cntS[d] == 0) atomicAnd(&R.sb[d >> 5], ~(1u << (d & 31)));
-      };
       if (lane == 0) {
-        while (l < nr && (int64_t)R.tpos[l] < j) ++l;
-        e = l;
-        while (e < nr && (int64_t)R.tpos[e] <= j + a.span) enter(e++);
+        while (e < nrel && (int64_t)R.tpos[e] <= j + a.span) {
+          const int d = R.tdx[e];
+          if (R.cntT[d]++ == 0) R.pb[d >> 5] |= 1u << (d & 31);
+          if (R.tsh[e] && R.cntS[d]++ == 0) R.sb[d >> 5] |= 1u << (d & 31);
+          ++e;
+        }
       }
       __syncwarp();
-      while (true) {
-        const int est = estimate(R, nwords, s);
-        if (est > best) {
-          best = est;
-          jstar = j;
-          den = s;
-        }
-        int64_t nx = 0;
-        if (lane == 0) {
-          const int64_t ne = e < nr ? (int64_t)R.tpos[e] - a.span : INT64_MAX;
-          const int64_t nl = l < e ? (int64_t)R.tpos[l] + 1 : INT64_MAX;
-          nx = min(ne, nl);
-          if (nx <= phi) {
-            while (l < e && (int64_t)R.tpos[l] + 1 <= nx) leave(l++);
-            while (e < nr && (int64_t)R.tpos[e] - a.span <= nx) enter(e++);
+      int theta = 0, est = 0;
+      theta_est(R.pb, R.sb, nwords, s, &theta, &est);
+      int fin = 0;
+      if (lane == 0) {
+        auto bit = [&](const uint32_t* bs, int d) { return (int)((bs[d >> 5] >> (d & 31)) & 1u); };
+        auto pred = [&](int d) {  // largest present index below d
+          int w = d >> 5;
+          uint32_t bits = R.pb[w] & ((1u << (d & 31)) - 1u);
+          while (bits == 0 && w > 0) bits = R.pb[--w];
+          return bits ? w * 32 + 31 - __clz(bits) : 0;
+        };
+        auto succ = [&](int d) {  // smallest present index above d
+          int w = d >> 5;
+          uint32_t bits = ((d & 31) == 31) ? 0u : (R.pb[w] & ~((2u << (d & 31)) - 1u));
+          while (bits == 0 && w + 1 < nwords) bits = R.pb[++w];
+          return bits ? w * 32 + __ffs(bits) - 1 : d;
+        };
+        auto enter = [&](int x) {
+          const int d = R.tdx[x];
+          if (R.cntT[d]++ == 0 && R.qm[d] == 0) {
+            R.pb[d >> 5] |= 1u << (d & 31);
+            if (d < theta) {
+              const int old = theta;
+              theta = pred(theta);
+              est -= bit(R.sb, old);
+            }
           }
+          if (R.tsh[x] && R.cntS[d]++ == 0) {
+            R.sb[d >> 5] |= 1u << (d & 31);
+            if (d <= theta) ++est;
+          }
+        };
+        auto leave = [&](int x) {
+          const int d = R.tdx[x];
+          if (--R.cntT[d] == 0 && R.qm[d] == 0) {
+            R.pb[d >> 5] &= ~(1u << (d & 31));
+            if (d <= theta) {
+              theta = succ(theta);
+              est += bit(R.sb, theta);
+            }
+          }
+          if (R.tsh[x] && --R.cntS[d] == 0) {
+            R.sb[d >> 5] &= ~(1u << (d & 31));
+            if (d <= theta) --est;
+          }
+        };
+        while (true) {
+          if (est > best) {
+            best = est;
+            jstar = j;
+            if (best >= mx) {
+              fin = 1;
+              break;
+            }
+          }
+          const int64_t ne = e < nrel ? (int64_t)R.tpos[e] - a.span : INT64_MAX;
+          const int64_t nl = l < e ? (int64_t)R.tpos[l] + 1 : INT64_MAX;
+          const int64_t nx = min(ne, nl);
+          if (nx > phi) break;
+          j = nx;
+          while (l < e && (int64_t)R.tpos[l] + 1 <= j) leave(l++);
+          while (e < nrel && (int64_t)R.tpos[e] - a.span <= j) enter(e++);
         }
-        nx = __shfl_sync(0xffffffffu, nx, 0);
-        __syncwarp();
-        if (nx > phi) break;
-        j = nx;
       }
+      jstar = __shfl_sync(0xffffffffu, jstar, 0);
+      finished = __shfl_sync(0xffffffffu, fin, 0) != 0;
+      best = __shfl_sync(0xffffffffu, best, 0);
       plo = phi + 1;
-      if (plo <= jb) {
+      if (plo <= jb && !finished) {
         if (lane == 0) rlo = lower_bound_by(a.trec, rlo, a.nt, (uint64_t)plo, pos_of);
         rlo = __shfl_sync(0xffffffffu, rlo, 0);
       }
+      __syncwarp();
     }
     if (lane == 0) {
       sedef_run_t& out = a.runs[ri];
-      out.est = (uint16_t)best;
-      out.den = (uint16_t)den;
+      out.est = (uint16_t)(best < 0 ? 0 : best);
+      out.den = (uint16_t)s;
       out.j_star = (uint32_t)jstar;
-      out.keep = (best >= a.mtab[den]) ? 1 : 0;
+      out.keep = (best >= a.mtab[s]) ? 1 : 0;
     }
     __syncwarp();
   }
@@ -965,6 +1218,7 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   a.ov_list = ovl;
   a.nov = (unsigned int*)(counters + 1);
   a.next_window = (unsigned int*)(counters + 2);
+  a.stats = counters + 4;
 
   SEDEF_KERNEL(ctx, "k_windows",
                k_windows<<<(int)((nwin + 255) / 256), 256, 0, st>>>(
@@ -975,8 +1229,12 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   if (!attr) {
     SEDEF_CUDA(cudaFuncSetAttribute(k_filter_fast, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)fsm));
-    SEDEF_CUDA(cudaFuncSetAttribute(k_refine, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(sizeof(RefineWarp) * kRWarps)));
+    SEDEF_CUDA(cudaFuncSetAttribute(k_refine<256, 512, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(sizeof(RefineWarpT<256, 512>) * kRWarps)));
+    SEDEF_CUDA(cudaFuncSetAttribute(k_refine<kMaxWindowRecs, 1024, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(sizeof(RefineWarpT<kMaxWindowRecs, 1024>) * kRWarpsBig)));
     attr = true;
   }
   int per_sm = 0;
@@ -1026,9 +1284,17 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
         int wbits = 0;
         while ((int64_t(1) << wbits) < nb) ++wbits;
         SEDEF_TRY(radix_sort_u64(ctx, keys, vals, skeys, svals, (int64_t)nh, 0, 33 + wbits));
-        int g2 = (int)(nb < (int64_t)ctx_sm_count(ctx) * 16 ? nb : (int64_t)ctx_sm_count(ctx) * 16);
-        SEDEF_KERNEL(ctx, "k_slow_sweep",
-                     k_slow_sweep<<<g2, 32, 0, st>>>(a, v0, v1, d_base, os, skeys, svals));
+        SlowTask* tasks = (SlowTask*)ctx_alloc(ctx, (size_t)nh * sizeof(SlowTask));
+        if (!tasks) return SEDEF_ERR_OOM;
+        SEDEF_CUDA(cudaMemsetAsync(counters + 6, 0, 8, st));
+        const int64_t gw = (nb + 7) / 8;
+        int g2 = (int)(gw < (int64_t)ctx_sm_count(ctx) * 8 ? gw : (int64_t)ctx_sm_count(ctx) * 8);
+        SEDEF_KERNEL(ctx, "k_slow_groups",
+                     k_slow_groups<<<g2, 256, 0, st>>>(a, v0, v1, d_base, os, skeys, tasks,
+                                                       counters + 6, (int64_t)nh));
+        SEDEF_KERNEL(ctx, "k_slow_tasks",
+                     k_slow_tasks<<<ctx_sm_count(ctx) * 8, 32 * kTaskWarps, 0, st>>>(
+                         a, v0, d_base, os, skeys, svals, tasks, counters + 6));
         SEDEF_CUDA(cudaStreamSynchronize(st));
       }
       v0 = v1;
@@ -1046,12 +1312,34 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   uint32_t* perm = (uint32_t*)ctx_alloc(ctx, (size_t)total * 4);
   if (!keys || !skeys || !perm) return SEDEF_ERR_OOM;
   const int tb = (int)((total + 255) / 256);
-  SEDEF_KERNEL(ctx, "k_run_keys", k_run_keys<<<tb, 256, 0, st>>>(raw, total, keys));
-  int hb = 1;
-  while ((int64_t(1) << hb) <= (a.ttotal > h_qoff[nqseq] ? a.ttotal : h_qoff[nqseq])) ++hb;
-  SEDEF_TRY(radix_sort_u64(ctx, keys, nullptr, skeys, perm, total, 0, hb + 1));
+  int wb = 1;
+  while ((int64_t(1) << wb) < nwin) ++wb;
+  const int64_t* d_wbase = (const int64_t*)(d_up + ow);
+  if (33 + wb <= 64) {
+    SEDEF_KERNEL(ctx, "k_run_keys",
+                 k_run_keys<<<tb, 256, 0, st>>>(raw, total, a.qseq, nqseq, d_wbase, D.step, 0, keys));
+    SEDEF_TRY(radix_sort_u64(ctx, keys, nullptr, skeys, perm, total, 0, 33 + wb));
+  } else {
+    // stable two-pass order: by j_a, then by (window, o)
+    uint32_t* perm1 = (uint32_t*)ctx_alloc(ctx, (size_t)total * 4);
+    uint32_t* perm2 = (uint32_t*)ctx_alloc(ctx, (size_t)total * 4);
+    uint64_t* k2 = (uint64_t*)ctx_alloc(ctx, (size_t)total * 8);
+    if (!perm1 || !perm2 || !k2) return SEDEF_ERR_OOM;
+    SEDEF_KERNEL(ctx, "k_run_keys",
+                 k_run_keys<<<tb, 256, 0, st>>>(raw, total, a.qseq, nqseq, d_wbase, D.step, 1, keys));
+    SEDEF_TRY(radix_sort_u64(ctx, keys, nullptr, skeys, perm1, total, 0, 32));
+    SEDEF_KERNEL(ctx, "k_run_keys",
+                 k_run_keys<<<tb, 256, 0, st>>>(raw, total, a.qseq, nqseq, d_wbase, D.step, 2, keys));
+    SEDEF_KERNEL(ctx, "k_permute_u64", k_permute_u64<<<tb, 256, 0, st>>>(keys, perm1, total, k2));
+    SEDEF_TRY(radix_sort_u64(ctx, k2, nullptr, skeys, perm2, total, 0, wb + 1));
+    SEDEF_KERNEL(ctx, "k_compose_perm",
+                 k_compose_perm<<<tb, 256, 0, st>>>(perm1, perm2, total, perm));
+  }
   SEDEF_KERNEL(ctx, "k_gather_runs", k_gather_runs<<<tb, 256, 0, st>>>(raw, perm, total, runs));
-  // refine
+  // refine: lean kernel over all runs, then the large kernel over the runs
+  // it handed over (their count stays on the device)
+  uint32_t* big = (uint32_t*)ctx_alloc(ctx, (size_t)total * 4);
+  if (!big) return SEDEF_ERR_OOM;
   RefineArgs ra;
   ra.runs = runs;
   ra.nruns = total;
@@ -1064,14 +1352,29 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   ra.span = D.span;
   ra.max_occ = D.max_occ;
   ra.self_mode = D.self_mode;
+  ra.big = big;
+  ra.nbig = (unsigned int*)(counters + 3);
+  using Lean = RefineWarpT<256, 512>;
+  using Big = RefineWarpT<kMaxWindowRecs, 1024>;
+  const size_t lean_sm = sizeof(Lean) * kRWarps, big_sm = sizeof(Big) * kRWarpsBig;
   int rper = 0;
-  SEDEF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rper, k_refine, 32 * kRWarps,
-                                                           sizeof(RefineWarp) * kRWarps));
+  SEDEF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rper, k_refine<256, 512, true>,
+                                                           32 * kRWarps, lean_sm));
   if (rper < 1) rper = 1;
   int64_t rgrid = (total + kRWarps - 1) / kRWarps;
   if (rgrid > (int64_t)ctx_sm_count(ctx) * rper) rgrid = (int64_t)ctx_sm_count(ctx) * rper;
   SEDEF_KERNEL(ctx, "k_refine",
-               k_refine<<<(int)rgrid, 32 * kRWarps, sizeof(RefineWarp) * kRWarps, st>>>(ra));
+               k_refine<256, 512, true><<<(int)rgrid, 32 * kRWarps, lean_sm, st>>>(ra));
+  SEDEF_KERNEL(ctx, "k_refine_big",
+               k_refine<kMaxWindowRecs, 1024, false><<<ctx_sm_count(ctx), 32 * kRWarpsBig, big_sm,
+                                                       st>>>(ra));
+  SEDEF_CUDA(cudaMemcpyAsync(h_cnt, counters, 64, cudaMemcpyDeviceToHost, st));
+  SEDEF_CUDA(cudaStreamSynchronize(st));
+  {
+    const int64_t stats[8] = {nwin, nov, (int64_t)h_cnt[4], (int64_t)h_cnt[5], total,
+                              (int64_t)(h_cnt[3] & 0xFFFFFFFFull), 0, 0};
+    ctx_set_stats(ctx, stats, 8);
+  }
   SEDEF_CUDA(cudaStreamSynchronize(st));
   return SEDEF_OK;
 }
