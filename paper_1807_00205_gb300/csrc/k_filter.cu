@@ -778,6 +778,7 @@ constexpr int kRWarpsBig = 4;  // large kernel
 template <int QC, int RC>
 struct RefineWarpT {
   static constexpr int DC = QC + RC;  // domain: W_Q u span hashes
+  static_assert((DC & (DC - 1)) == 0, "the sort pads the domain to a power of two");
   uint32_t dom[DC];      // sorted distinct hashes
   uint16_t cntT[DC];     // records of this hash in the target window
   uint16_t cntS[DC];     // shared-compatible records of this hash in the window
@@ -869,6 +870,8 @@ struct RefineArgs {
   int span, max_occ, self_mode;
   uint32_t* big;        // runs handed to the large kernel
   unsigned int* nbig;
+  const uint4* ranges;  // per run: query records [x, y), span records [z, w)
+  unsigned long long* next;  // chunk counters of the two kernels
 };
 
 template <int QC, int RC, bool kLean>
@@ -881,29 +884,36 @@ __global__ void __launch_bounds__(32 * (kLean ? kRWarps : kRWarpsBig)) k_refine(
   RW& R = reinterpret_cast<RW*>(smem_raw)[warp];
   auto pos_of = [](uint64_t r) { return (uint64_t)((r >> 1) & 0xFFFFFFFFull); };
   const int64_t count = kLean ? a.nruns : (int64_t)*a.nbig;
-  for (int64_t t = (int64_t)blockIdx.x * NW + warp; t < count; t += (int64_t)gridDim.x * NW) {
+  // contiguous chunks of runs per warp (runs of one window are adjacent, so
+  // W_Q is built once per window and chunk), handed out dynamically
+  constexpr int kChunk = 16;
+  int64_t prev_qa = -1, prev_qb = -1;
+  int s = 0;
+  while (true) {
+    int64_t c0 = 0;
+    if (lane == 0) c0 = (int64_t)atomicAdd(kLean ? a.next : a.next + 1, (unsigned long long)kChunk);
+    c0 = __shfl_sync(0xffffffffu, c0, 0);
+    if (c0 >= count) break;
+    const int64_t c1 = min(count, c0 + kChunk);
+  for (int64_t t = c0; t < c1; ++t) {
     const int64_t ri = kLean ? t : (int64_t)a.big[t];
     const sedef_run_t run = a.runs[ri];
     const int64_t i = run.i, ja = run.j_a, jb = run.j_b;
     const int o = run.o;
-    int64_t qa = 0, qb = 0, rlo = 0, rend = 0;
-    if (lane == 0) {
-      qa = lower_bound_by(a.qrec, 0, a.nq, (uint64_t)i, pos_of);
-      qb = lower_bound_by(a.qrec, qa, a.nq, (uint64_t)(i + a.span + 1), pos_of);
-      rlo = lower_bound_by(a.trec, 0, a.nt, (uint64_t)ja, pos_of);
-      if (kLean) rend = lower_bound_by(a.trec, rlo, a.nt, (uint64_t)(jb + a.span + 1), pos_of);
-    }
-    qa = __shfl_sync(0xffffffffu, qa, 0);
-    qb = __shfl_sync(0xffffffffu, qb, 0);
-    rlo = __shfl_sync(0xffffffffu, rlo, 0);
+    const uint4 rg = a.ranges[ri];  // query records [qa, qb), span records [rlo, rend)
+    const int64_t qa = rg.x, qb = rg.y;
+    int64_t rlo = rg.z;
+    const int64_t rend = rg.w;
     const int c = (int)(qb - qa);
     if (kLean) {
-      rend = __shfl_sync(0xffffffffu, rend, 0);
       if (c > QC || rend - rlo > RC) {
         if (lane == 0) a.big[atomicAdd(a.nbig, 1u)] = (uint32_t)ri;
         continue;
       }
     }
+    if (qa != prev_qa || qb != prev_qb) {
+    prev_qa = qa;
+    prev_qb = qb;
     // ---- W_Q: sorted hashes with strand masks (capped hashes dropped)
     const int npq = next_pow2(c < 2 ? 2 : c);
     for (int x = lane; x < npq; x += 32) {
@@ -916,7 +926,7 @@ __global__ void __launch_bounds__(32 * (kLean ? kRWarps : kRWarpsBig)) k_refine(
     }
     __syncwarp();
     warp_sort_u32(R.dom, npq);
-    int s = 0;
+    s = 0;
     for (int base = 0; base < c; base += 32) {
       const int x = base + lane;
       uint32_t h = 0, mask = 0;
@@ -938,6 +948,7 @@ __global__ void __launch_bounds__(32 * (kLean ? kRWarps : kRWarpsBig)) k_refine(
       s += __popc(bal);
     }
     __syncwarp();
+    }
     const int mx = run.max_shared;
     int best = -1;
     int64_t jstar = ja;
@@ -958,15 +969,49 @@ __global__ void __launch_bounds__(32 * (kLean ? kRWarps : kRWarpsBig)) k_refine(
       phi = __shfl_sync(0xffffffffu, phi, 0);
       rhi = __shfl_sync(0xffffffffu, rhi, 0);
       const int nr = (int)(rhi - rlo);
-      // ---- relevant span records: a hash above max(W_Q) can never be in U
-      // (W_Q alone supplies s hashes at or below it) nor shared, so such
-      // records never change the estimate and are left out.  cntT/cntS
-      // double as a scratch array of the kept records' hashes until the
-      // domain is built.
-      const uint32_t qmax = s > 0 ? R.wq_h[s - 1] : 0u;
+      // ---- relevant span records.  Only W_Q hashes with a compatible,
+      // non-self occurrence in the span (the candidates C) can ever count,
+      // and a candidate's rank among W_Q u W_T depends only on the hashes
+      // below it.  So the roll needs the candidates' compatible occurrences
+      // and the non-W_Q records whose hash is below max(C); every other
+      // record leaves the estimate unchanged.  W_Q itself stays in the
+      // domain, so at least s hashes are always present.  cntT/cntS double
+      // as a scratch array of the kept records' hashes until the domain is
+      // built.
       uint32_t* tmp_h = reinterpret_cast<uint32_t*>(R.cntT);  // DC u32 (cntT then cntS)
-      int nrel = 0;
+      auto wq_find = [&](uint32_t h) {  // index in W_Q or -1
+        int lo2 = 0, hi2 = s;
+        while (lo2 < hi2) {
+          const int mid = (lo2 + hi2) >> 1;
+          if (R.wq_h[mid] < h) lo2 = mid + 1; else hi2 = mid;
+        }
+        return (lo2 < s && R.wq_h[lo2] == h) ? lo2 : -1;
+      };
+      uint32_t cmax = 0;
+      bool have_c = false;
       for (int base = 0; base < nr; base += 32) {
+        const int x = base + lane;
+        bool cand = false;
+        uint32_t h = 0;
+        if (x < nr) {
+          const uint64_t r = a.trec[rlo + x];
+          h = rec_hash(r);
+          const uint32_t t = rec_pos(r), st = rec_strand(r);
+          const int q = wq_find(h);
+          const bool self = a.self_mode && (int64_t)t >= i && (int64_t)t <= i + a.span;
+          cand = q >= 0 && !self && ((R.wq_m[q] >> (st ^ (uint32_t)o)) & 1u);
+        }
+        uint32_t hm = cand ? h : 0u;
+        const bool any = __any_sync(0xffffffffu, cand);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, d));
+        if (any) {
+          cmax = have_c ? max(cmax, hm) : hm;
+          have_c = true;
+        }
+      }
+      int nrel = 0;
+      for (int base = 0; base < nr && have_c; base += 32) {
         const int x = base + lane;
         bool keep = false;
         uint32_t h = 0, t = 0, st = 0;
@@ -975,7 +1020,13 @@ __global__ void __launch_bounds__(32 * (kLean ? kRWarps : kRWarpsBig)) k_refine(
           h = rec_hash(r);
           t = rec_pos(r);
           st = rec_strand(r);
-          keep = h <= qmax;
+          const int q = wq_find(h);
+          if (q >= 0) {
+            const bool self = a.self_mode && (int64_t)t >= i && (int64_t)t <= i + a.span;
+            keep = !self && ((R.wq_m[q] >> (st ^ (uint32_t)o)) & 1u);
+          } else {
+            keep = h < cmax;
+          }
         }
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         if (keep) {
@@ -1137,6 +1188,405 @@ __global__ void __launch_bounds__(32 * (kLean ? kRWarps : kRWarpsBig)) k_refine(
     }
     __syncwarp();
   }
+  }
+}
+
+// ------------------------------------------------- batched lean refine ----
+//
+// A warp sets up runs one at a time (cooperatively: W_Q, candidates, kept
+// records, domain) into slots of a per-warp arena, then every lane rolls
+// its own run through its slot, so up to 32 rolls proceed side by side.
+// Runs beyond the lean limits (more than 256 query records or 512 span
+// records) go to the large kernel.
+
+constexpr int kBWarps = 4;
+constexpr int kBQC = 256, kBRC = 512, kBDC = kBQC + kBRC;
+static_assert(kBDC <= 1024, "the domain sort buffer holds 1024 entries");
+constexpr int kArenaWords = 2560;  // 10 KB of slots per warp
+
+struct BatchWarp {
+  uint32_t arena[kArenaWords];
+  uint32_t dom[1024];    // domain sort buffer: next power of two >= kBDC
+  uint32_t tmp_h[kBRC];  // kept records' hashes
+  uint32_t wq_h[kBQC];
+  uint8_t wq_m[kBQC];
+  uint32_t h_off[32];    // slot start (words)
+  uint32_t h_run[32];    // run index
+  uint16_t h_nrel[32], h_D[32], h_Dmax[32], h_s[32];
+};
+
+struct Slot {
+  uint32_t* tpos;
+  uint16_t* tdx;
+  uint8_t* tsh;
+  uint16_t* cntT;
+  uint16_t* cntS;
+  uint8_t* qm;
+  uint32_t* pb;
+  uint32_t* sb;
+};
+
+__device__ __forceinline__ int slot_words(int nrel, int dmax) {
+  return nrel + (nrel + 1) / 2 + (nrel + 3) / 4 + dmax + (dmax + 3) / 4 + 2 * ((dmax + 31) / 32);
+}
+
+__device__ __forceinline__ Slot slot_at(uint32_t* base, int nrel, int dmax) {
+  Slot sl;
+  sl.tpos = base;
+  uint32_t* p = base + nrel;
+  sl.tdx = reinterpret_cast<uint16_t*>(p);
+  p += (nrel + 1) / 2;
+  sl.tsh = reinterpret_cast<uint8_t*>(p);
+  p += (nrel + 3) / 4;
+  sl.cntT = reinterpret_cast<uint16_t*>(p);
+  sl.cntS = sl.cntT + dmax;
+  p += dmax;
+  sl.qm = reinterpret_cast<uint8_t*>(p);
+  p += (dmax + 3) / 4;
+  sl.pb = p;
+  sl.sb = p + (dmax + 31) / 32;
+  return sl;
+}
+
+// Rolls one run (single lane): enters the first window's records, finds
+// theta (s-th present hash) and est by scanning the bitsets, then keeps both
+// exact through every enter/leave as in the large kernel.
+__device__ void roll_run(const Slot& sl, int nrel, int D, int s, int mx, int64_t plo, int64_t phi,
+                         int span, int* best_out, int64_t* jstar_out) {
+  const int nwords = (D + 31) >> 5;
+  int e = 0, l = 0;
+  int64_t j = plo;
+  while (e < nrel && (int64_t)sl.tpos[e] <= j + span) {
+    const int d = sl.tdx[e];
+    if (sl.cntT[d]++ == 0) sl.pb[d >> 5] |= 1u << (d & 31);
+    if (sl.tsh[e] && sl.cntS[d]++ == 0) sl.sb[d >> 5] |= 1u << (d & 31);
+    ++e;
+  }
+  int theta = 0, est = 0;
+  {
+    int acc = 0;
+    for (int w = 0; w < nwords; ++w) {
+      const int c = __popc(sl.pb[w]);
+      if (acc + c >= s) {
+        uint32_t v = sl.pb[w];
+        for (int y = 1; y < s - acc; ++y) v &= v - 1u;
+        const int b = __ffs(v) - 1;
+        theta = w * 32 + b;
+        const uint32_t below = (b >= 31) ? 0xFFFFFFFFu : ((2u << b) - 1u);
+        est += __popc(sl.sb[w] & below);
+        break;
+      }
+      acc += c;
+      est += __popc(sl.sb[w]);
+    }
+  }
+  auto bit = [&](const uint32_t* bs, int d) { return (int)((bs[d >> 5] >> (d & 31)) & 1u); };
+  auto pred = [&](int d) {
+    int w = d >> 5;
+    uint32_t bits = sl.pb[w] & ((1u << (d & 31)) - 1u);
+    while (bits == 0 && w > 0) bits = sl.pb[--w];
+    return bits ? w * 32 + 31 - __clz(bits) : 0;
+  };
+  auto succ = [&](int d) {
+    int w = d >> 5;
+    uint32_t bits = ((d & 31) == 31) ? 0u : (sl.pb[w] & ~((2u << (d & 31)) - 1u));
+    while (bits == 0 && w + 1 < nwords) bits = sl.pb[++w];
+    return bits ? w * 32 + __ffs(bits) - 1 : d;
+  };
+  int best = -1;
+  int64_t jstar = plo;
+  while (true) {
+    if (est > best) {
+      best = est;
+      jstar = j;
+      if (best >= mx) break;
+    }
+    const int64_t ne = e < nrel ? (int64_t)sl.tpos[e] - span : INT64_MAX;
+    const int64_t nl = l < e ? (int64_t)sl.tpos[l] + 1 : INT64_MAX;
+    const int64_t nx = min(ne, nl);
+    if (nx > phi) break;
+    j = nx;
+    while (l < e && (int64_t)sl.tpos[l] + 1 <= j) {
+      const int d = sl.tdx[l];
+      if (--sl.cntT[d] == 0 && sl.qm[d] == 0) {
+        sl.pb[d >> 5] &= ~(1u << (d & 31));
+        if (d <= theta) {
+          theta = succ(theta);
+          est += bit(sl.sb, theta);
+        }
+      }
+      if (sl.tsh[l] && --sl.cntS[d] == 0) {
+        sl.sb[d >> 5] &= ~(1u << (d & 31));
+        if (d <= theta) --est;
+      }
+      ++l;
+    }
+    while (e < nrel && (int64_t)sl.tpos[e] - span <= j) {
+      const int d = sl.tdx[e];
+      if (sl.cntT[d]++ == 0 && sl.qm[d] == 0) {
+        sl.pb[d >> 5] |= 1u << (d & 31);
+        if (d < theta) {
+          const int old = theta;
+          theta = pred(theta);
+          est -= bit(sl.sb, old);
+        }
+      }
+      if (sl.tsh[e] && sl.cntS[d]++ == 0) {
+        sl.sb[d >> 5] |= 1u << (d & 31);
+        if (d <= theta) ++est;
+      }
+      ++e;
+    }
+  }
+  *best_out = best;
+  *jstar_out = jstar;
+}
+
+__global__ void __launch_bounds__(32 * kBWarps) k_refine_batch(RefineArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  BatchWarp& B = reinterpret_cast<BatchWarp*>(smem_raw)[warp];
+  constexpr int kChunk = 32;
+  int64_t prev_qa = -1, prev_qb = -1;
+  int s = 0;
+  int nslots = 0, used = 0;
+
+  auto flush = [&]() {
+    __syncwarp();
+    if (lane < nslots) {
+      const int64_t ri = B.h_run[lane];
+      const sedef_run_t run = a.runs[ri];
+      const int nrel = B.h_nrel[lane], D = B.h_D[lane], sq = B.h_s[lane];
+      const Slot sl = slot_at(B.arena + B.h_off[lane], nrel, B.h_Dmax[lane]);
+      int best;
+      int64_t jstar;
+      roll_run(sl, nrel, D, sq, run.max_shared, run.j_a, run.j_b, a.span, &best, &jstar);
+      sedef_run_t& out = a.runs[ri];
+      out.est = (uint16_t)(best < 0 ? 0 : best);
+      out.den = (uint16_t)sq;
+      out.j_star = (uint32_t)jstar;
+      out.keep = (best >= a.mtab[sq]) ? 1 : 0;
+    }
+    __syncwarp();
+    nslots = 0;
+    used = 0;
+  };
+
+  while (true) {
+    int64_t c0 = 0;
+    if (lane == 0) c0 = (int64_t)atomicAdd(a.next, (unsigned long long)kChunk);
+    c0 = __shfl_sync(0xffffffffu, c0, 0);
+    if (c0 >= a.nruns) break;
+    const int64_t c1 = min(a.nruns, c0 + kChunk);
+    for (int64_t ri = c0; ri < c1; ++ri) {
+      const sedef_run_t run = a.runs[ri];
+      const int64_t i = run.i;
+      const int o = run.o;
+      const uint4 rg = a.ranges[ri];
+      const int64_t qa = rg.x, qb = rg.y, rlo = rg.z, rend = rg.w;
+      const int c = (int)(qb - qa);
+      const int nr = (int)(rend - rlo);
+      if (c > kBQC || nr > kBRC) {
+        if (lane == 0) a.big[atomicAdd(a.nbig, 1u)] = (uint32_t)ri;
+        continue;
+      }
+      // ---- W_Q (kept from the previous run of the same window)
+      if (qa != prev_qa || qb != prev_qb) {
+        prev_qa = qa;
+        prev_qb = qb;
+        const int npq = next_pow2(c < 2 ? 2 : c);
+        for (int x = lane; x < npq; x += 32) {
+          uint32_t key = kNone;
+          if (x < c) {
+            const uint64_t r = a.qrec[qa + x];
+            key = (rec_hash(r) << 1) | rec_strand(r);
+          }
+          B.dom[x] = key;
+        }
+        __syncwarp();
+        warp_sort_u32(B.dom, npq);
+        s = 0;
+        for (int base = 0; base < c; base += 32) {
+          const int x = base + lane;
+          uint32_t h = 0, mask = 0;
+          bool first = false;
+          if (x < c) {
+            h = B.dom[x] >> 1;
+            first = (x == 0) || ((B.dom[x - 1] >> 1) != h);
+            if (first) {
+              for (int y = x; y < c && (B.dom[y] >> 1) == h; ++y) mask |= 1u << (B.dom[y] & 1u);
+              if (a.max_occ > 0 && (int)(a.toff[h + 1] - a.toff[h]) > a.max_occ) first = false;
+            }
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, first);
+          if (first) {
+            const int d = s + __popc(bal & lanemask_lt());
+            B.wq_h[d] = h;
+            B.wq_m[d] = (uint8_t)mask;
+          }
+          s += __popc(bal);
+        }
+        __syncwarp();
+      }
+      auto wq_find = [&](uint32_t h) {
+        int lo2 = 0, hi2 = s;
+        while (lo2 < hi2) {
+          const int mid = (lo2 + hi2) >> 1;
+          if (B.wq_h[mid] < h) lo2 = mid + 1; else hi2 = mid;
+        }
+        return (lo2 < s && B.wq_h[lo2] == h) ? lo2 : -1;
+      };
+      // ---- candidates (see the large kernel): max(C), then the kept records
+      uint32_t cmax = 0;
+      bool have_c = false;
+      int nrel = 0;
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int base = 0; base < nr; base += 32) {
+          const int x = base + lane;
+          bool flag = false;
+          uint32_t h = 0;
+          if (x < nr) {
+            const uint64_t r = a.trec[rlo + x];
+            h = rec_hash(r);
+            const uint32_t t = rec_pos(r), st = rec_strand(r);
+            const int q = wq_find(h);
+            const bool self = a.self_mode && (int64_t)t >= i && (int64_t)t <= i + a.span;
+            const bool cand = q >= 0 && !self && ((B.wq_m[q] >> (st ^ (uint32_t)o)) & 1u);
+            flag = pass == 0 ? cand : (q >= 0 ? cand : (have_c && h < cmax));
+          }
+          if (pass == 0) {
+            uint32_t hm = flag ? h : 0u;
+            const bool any = __any_sync(0xffffffffu, flag);
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, d));
+            if (any) {
+              cmax = have_c ? max(cmax, hm) : hm;
+              have_c = true;
+            }
+          } else {
+            nrel += __popc(__ballot_sync(0xffffffffu, flag));
+          }
+        }
+        if (!have_c) break;
+      }
+      const int dmax = s + nrel;
+      const int words = slot_words(nrel, dmax);
+      if (nslots == 32 || used + words > kArenaWords) flush();
+      const int off = used;
+      const Slot sl = slot_at(B.arena + off, nrel, dmax);
+      // ---- kept records: positions, hashes, strands
+      int k = 0;
+      for (int base = 0; base < nr && nrel > 0; base += 32) {
+        const int x = base + lane;
+        bool keep = false;
+        uint32_t h = 0, t = 0, st = 0;
+        if (x < nr) {
+          const uint64_t r = a.trec[rlo + x];
+          h = rec_hash(r);
+          t = rec_pos(r);
+          st = rec_strand(r);
+          const int q = wq_find(h);
+          if (q >= 0) {
+            const bool self = a.self_mode && (int64_t)t >= i && (int64_t)t <= i + a.span;
+            keep = !self && ((B.wq_m[q] >> (st ^ (uint32_t)o)) & 1u);
+          } else {
+            keep = h < cmax;
+          }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+          const int y = k + __popc(bal & lanemask_lt());
+          sl.tpos[y] = t;
+          B.tmp_h[y] = h;
+          sl.tsh[y] = (uint8_t)st;
+        }
+        k += __popc(bal);
+      }
+      __syncwarp();
+      // ---- domain
+      const int nd0 = s + nrel;
+      const int npd = next_pow2(nd0 < 2 ? 2 : nd0);
+      for (int x = lane; x < npd; x += 32) {
+        uint32_t v = kNone;
+        if (x < s) v = B.wq_h[x];
+        else if (x < nd0) v = B.tmp_h[x - s];
+        B.dom[x] = v;
+      }
+      __syncwarp();
+      warp_sort_u32(B.dom, npd);
+      int D = 0;
+      for (int base = 0; base < nd0; base += 32) {
+        const int x = base + lane;
+        const uint32_t v = x < nd0 ? B.dom[x] : kNone;
+        const bool first = x < nd0 && (x == 0 || B.dom[x - 1] != v);
+        const unsigned bal = __ballot_sync(0xffffffffu, first);
+        __syncwarp();
+        if (first) B.dom[D + __popc(bal & lanemask_lt())] = v;
+        __syncwarp();
+        D += __popc(bal);
+      }
+      for (int x = lane; x < nrel; x += 32) sl.tdx[x] = (uint16_t)dom_find(B.dom, D, B.tmp_h[x]);
+      for (int x = lane; x < D; x += 32) {
+        sl.cntT[x] = 0;
+        sl.cntS[x] = 0;
+        sl.qm[x] = 0;
+      }
+      for (int x = lane; x < (dmax + 31) / 32; x += 32) {
+        sl.pb[x] = 0;
+        sl.sb[x] = 0;
+      }
+      __syncwarp();
+      for (int x = lane; x < s; x += 32) {
+        const int d = dom_find(B.dom, D, B.wq_h[x]);
+        sl.qm[d] = B.wq_m[x];
+        atomicOr(&sl.pb[d >> 5], 1u << (d & 31));
+      }
+      __syncwarp();
+      for (int x = lane; x < nrel; x += 32) {
+        const uint32_t t = sl.tpos[x], st = sl.tsh[x];
+        const int d = sl.tdx[x];
+        const bool self = a.self_mode && (int64_t)t >= i && (int64_t)t <= i + a.span;
+        sl.tsh[x] = (!self && ((sl.qm[d] >> (st ^ (uint32_t)o)) & 1u)) ? 1 : 0;
+      }
+      if (lane == 0) {
+        B.h_off[nslots] = (uint32_t)off;
+        B.h_run[nslots] = (uint32_t)ri;
+        B.h_nrel[nslots] = (uint16_t)nrel;
+        B.h_D[nslots] = (uint16_t)D;
+        B.h_Dmax[nslots] = (uint16_t)dmax;
+        B.h_s[nslots] = (uint16_t)s;
+      }
+      __syncwarp();
+      ++nslots;
+      used += words;
+    }
+  }
+  flush();
+}
+
+// Per-run record ranges for the refine: query records of the run's window
+// (from the window table) and target records of its span [j_a, j_b+n-k].
+__global__ void k_run_ranges(const sedef_run_t* runs, int64_t n, const int64_t* qseq, int nqseq,
+                             const int64_t* wbase, int step, const uint32_t* win_qa,
+                             const uint32_t* win_qb, const uint64_t* trec, int64_t nt, int span,
+                             uint4* ranges) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n) return;
+  const sedef_run_t r = runs[x];
+  const int sq = seq_of(qseq, nqseq, r.i);
+  const int64_t w = wbase[sq] + ((int64_t)r.i - qseq[sq]) / step;
+  auto pos_of = [](uint64_t v) { return (uint64_t)((v >> 1) & 0xFFFFFFFFull); };
+  const int64_t lo = lower_bound_by(trec, 0, nt, (uint64_t)r.j_a, pos_of);
+  // the span holds few records: gallop from lo
+  const uint64_t end_pos = (uint64_t)r.j_b + (uint64_t)span + 1;
+  int64_t stepg = 1, hi = lo;
+  while (hi < nt && pos_of(trec[hi]) < end_pos) {
+    hi = lo + stepg;
+    stepg <<= 1;
+  }
+  if (hi > nt) hi = nt;
+  const int64_t b = lower_bound_by(trec, lo + (stepg >> 2), hi, end_pos, pos_of);
+  ranges[x] = make_uint4(win_qa[w], win_qb[w], (uint32_t)lo, (uint32_t)b);
 }
 
 }  // namespace
@@ -1229,9 +1679,8 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   if (!attr) {
     SEDEF_CUDA(cudaFuncSetAttribute(k_filter_fast, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)fsm));
-    SEDEF_CUDA(cudaFuncSetAttribute(k_refine<256, 512, true>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(sizeof(RefineWarpT<256, 512>) * kRWarps)));
+    SEDEF_CUDA(cudaFuncSetAttribute(k_refine_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(sizeof(BatchWarp) * kBWarps)));
     SEDEF_CUDA(cudaFuncSetAttribute(k_refine<kMaxWindowRecs, 1024, false>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)(sizeof(RefineWarpT<kMaxWindowRecs, 1024>) * kRWarpsBig)));
@@ -1354,17 +1803,25 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   ra.self_mode = D.self_mode;
   ra.big = big;
   ra.nbig = (unsigned int*)(counters + 3);
-  using Lean = RefineWarpT<256, 512>;
+  uint4* ranges = (uint4*)ctx_alloc(ctx, (size_t)total * sizeof(uint4));
+  if (!ranges) return SEDEF_ERR_OOM;
+  SEDEF_KERNEL(ctx, "k_run_ranges",
+               k_run_ranges<<<tb, 256, 0, st>>>(runs, total, a.qseq, nqseq, d_wbase, D.step, wqa, wqb,
+                                                trec, nt, D.span, ranges));
+  ra.ranges = ranges;
+  ra.next = counters + 6;
+  SEDEF_CUDA(cudaMemsetAsync(counters + 6, 0, 16, st));
   using Big = RefineWarpT<kMaxWindowRecs, 1024>;
-  const size_t lean_sm = sizeof(Lean) * kRWarps, big_sm = sizeof(Big) * kRWarpsBig;
+  const size_t lean_sm = sizeof(BatchWarp) * kBWarps, big_sm = sizeof(Big) * kRWarpsBig;
   int rper = 0;
-  SEDEF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rper, k_refine<256, 512, true>,
-                                                           32 * kRWarps, lean_sm));
+  SEDEF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rper, k_refine_batch, 32 * kBWarps,
+                                                           lean_sm));
   if (rper < 1) rper = 1;
-  int64_t rgrid = (total + kRWarps - 1) / kRWarps;
+  int64_t rgrid = (total + kBWarps * 32 - 1) / (kBWarps * 32);
   if (rgrid > (int64_t)ctx_sm_count(ctx) * rper) rgrid = (int64_t)ctx_sm_count(ctx) * rper;
+  if (rgrid < 1) rgrid = 1;
   SEDEF_KERNEL(ctx, "k_refine",
-               k_refine<256, 512, true><<<(int)rgrid, 32 * kRWarps, lean_sm, st>>>(ra));
+               k_refine_batch<<<(int)rgrid, 32 * kBWarps, lean_sm, st>>>(ra));
   SEDEF_KERNEL(ctx, "k_refine_big",
                k_refine<kMaxWindowRecs, 1024, false><<<ctx_sm_count(ctx), 32 * kRWarpsBig, big_sm,
                                                        st>>>(ra));

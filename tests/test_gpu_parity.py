@@ -162,6 +162,14 @@ def test_default_params_multi_sequence(ctx, seed):
     assert len(ref["cands"]) > 0
 
 
+def test_dense_winnowing_large_domains(ctx):
+    """w = 5 gives ~246 query minimizers per window and ~490 span records per
+    run, so the refine's domain sort pads to 1024 entries."""
+    g = synth.small_case(34, lengths=(60_000,), n_sd=4, sd_lo=2000, sd_hi=5000, id_lo=0.92,
+                         mask_frac=0.1)
+    full_parity(ctx, g, oracle.params(w=5))
+
+
 def test_occurrence_cap(ctx):
     g = synth.small_case(33, lengths=(150_000,), n_sd=6, sd_lo=1500, sd_hi=6000, id_lo=0.9,
                          mask_frac=0.2)
