@@ -218,6 +218,29 @@ int sedef_sketch(sedef_ctx* ctx, const uint32_t* d_packed, const uint32_t* d_mas
                  const sedef_params* p, uint64_t* d_rec, int64_t rec_cap, int64_t* h_nrec);
 
 /*
+ * sedef_sketch without any allocation (no counterpart in the paper: this is
+ * an interface for callers, not part of the method).  Same inputs, outputs,
+ * results and return codes as sedef_sketch, with no context: the work is
+ * enqueued on `stream` (a cudaStream_t as void*).  For callers that cannot
+ * allocate device memory themselves or through the library -- for example a
+ * host framework that owns the whole device heap through its own pool, or
+ * a latency-critical path that must avoid cudaMalloc's implicit device
+ * synchronization.  Its scratch is one fixed static device array of about
+ * 1 MB (per-tile counts and offsets for at most 268,435,456 bases and the
+ * offsets of at most 4096 sequences); larger inputs are rejected with
+ * SEDEF_ERR_UNSUPPORTED.  The array stays allocated on every device that
+ * loads the library until the process exits.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls share the one array, so
+ * calls that overlap on the GPU (other streams, other host threads) race:
+ * serialize them.  Synchronizes `stream`.
+ */
+int sedef_sketch_noalloc(const uint32_t* d_packed, const uint32_t* d_mask,
+                         const uint32_t* d_nbits, const int64_t* h_seq_off, int32_t nseq,
+                         const sedef_params* p, uint64_t* d_rec, int64_t rec_cap,
+                         int64_t* h_nrec, void* stream);
+
+/*
  * a3: sorts the nrec records of d_rec by (hash, position) into d_sorted and
  * writes d_off[0..4^k] with d_off[x] = number of records whose hash is < x,
  * so the postings of hash x are d_sorted[d_off[x] .. d_off[x+1]).

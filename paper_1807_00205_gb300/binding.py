@@ -39,7 +39,7 @@ class Params(ctypes.Structure):
 
 EXPORTS = ["sedef_default_params", "sedef_last_error", "sedef_create", "sedef_destroy",
            "sedef_set_stream", "sedef_trace_enable", "sedef_trace_report", "sedef_launch_count", "sedef_filter_stats",
-           "sedef_threshold_table", "sedef_pack", "sedef_sketch",
+           "sedef_threshold_table", "sedef_pack", "sedef_sketch", "sedef_sketch_noalloc",
            "sedef_index", "sedef_filter", "sedef_chain", "sedef_merge", "sedef_selfsearch_host"]
 
 _lib = None
@@ -70,6 +70,7 @@ def load(build_if_missing: bool = True):
     lib.sedef_threshold_table.argtypes = [P, vp, i32, ctypes.POINTER(ctypes.c_double)]
     lib.sedef_pack.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.sedef_sketch.argtypes = [vp, vp, vp, vp, vp, i32, P, vp, i64, ctypes.POINTER(i64)]
+    lib.sedef_sketch_noalloc.argtypes = [vp, vp, vp, vp, i32, P, vp, i64, ctypes.POINTER(i64), vp]
     lib.sedef_index.argtypes = [vp, vp, i64, P, vp, vp]
     lib.sedef_filter.argtypes = [vp, vp, i64, vp, i32, vp, vp, vp, i64, vp, i32, P, vp, i64,
                                  ctypes.POINTER(i64)]
@@ -289,6 +290,20 @@ class Context:
         cands, nc = self.sedef_merge(chains, nch, offsets, offsets, p)
         return dict(packed=packed, mask=mask, nbits=nbits, rec=rec, sorted=srt, off=off,
                     runs=runs, nruns=nruns, chains=chains, nchains=nch, cands=cands, ncands=nc)
+
+
+def sedef_sketch_noalloc(packed, mask, nbits, offsets, p: Params, rec, stream) -> int:
+    """The allocation-free sketch: `rec` is a caller-allocated device tensor
+    (int64) whose capacity is its length; returns the number of records
+    written (raises SedefError, with status -6 and the needed count in the
+    message, when rec is too small)."""
+    off = _offsets(offsets)
+    count = ctypes.c_int64()
+    st = load().sedef_sketch_noalloc(_ptr(packed), _ptr(mask), _ptr(nbits), off.ctypes.data,
+                                     len(off) - 1, ctypes.byref(p), _ptr(rec), rec.numel(),
+                                     ctypes.byref(count), ctypes.c_void_p(stream.cuda_stream))
+    _check(st)
+    return count.value
 
 
 def to_numpy_records(t) -> np.ndarray:

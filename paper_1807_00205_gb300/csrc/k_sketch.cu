@@ -325,3 +325,119 @@ int run_sketch(sedef_ctx* ctx, const uint32_t* packed, const uint32_t* mask, con
 }
 
 }  // namespace sedef
+
+// ------------------------------------------------ allocation-free sketch --
+//
+// sedef_sketch_noalloc: the sketch with its scratch (per-tile counts and
+// offsets, the sequence offsets) in a fixed static device array instead of
+// memory from a context, for callers that must not allocate device memory.
+// The array's host-side name is only a stand-in, so its device address is
+// looked up once per device with cudaGetSymbolAddress and passed to the
+// kernels.
+
+namespace sedef {
+namespace {
+
+constexpr int64_t kNoallocMaxBases = int64_t(256) << 20;  // 268,435,456 bases
+constexpr int kNoallocMaxSeqs = 4096;
+constexpr int64_t kNoallocMaxTiles = (kNoallocMaxBases + kSkTile - 1) / kSkTile;
+constexpr size_t kNoallocCountBytes = (size_t)(kNoallocMaxTiles + 1) * 4;
+constexpr size_t kNoallocBytes = 2 * kNoallocCountBytes + (size_t)(kNoallocMaxSeqs + 1) * 8;
+
+// Shared by every call in the process and kept between calls; about 1 MB on
+// each device that loads the library.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr int kMaxDevices = 64;
+static unsigned char* g_noalloc_ptr[kMaxDevices];
+
+// Exclusive scan of n counts by one block (n is at most 131,073 here).
+__global__ void __launch_bounds__(1024) k_scan_one_block(const uint32_t* __restrict__ in,
+                                                         uint32_t* __restrict__ out, int64_t n) {
+  __shared__ int tmp[33];
+  const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+  const int64_t lo = (int64_t)threadIdx.x * per, hi = min(n, lo + per);
+  uint32_t s = 0;
+  for (int64_t x = lo; x < hi; ++x) s += in[x];
+  int tot;
+  uint32_t run = (uint32_t)block_exclusive_sum((int)s, tmp, &tot);
+  for (int64_t x = lo; x < hi; ++x) {
+    const uint32_t v = in[x];
+    out[x] = run;
+    run += v;
+  }
+  if (threadIdx.x == 0) out[n] = (uint32_t)tot;
+}
+
+}  // namespace
+}  // namespace sedef
+
+extern "C" int sedef_sketch_noalloc(const uint32_t* d_packed, const uint32_t* d_mask,
+                                    const uint32_t* d_nbits, const int64_t* h_seq_off,
+                                    int32_t nseq, const sedef_params* p, uint64_t* d_rec,
+                                    int64_t rec_cap, int64_t* h_nrec, void* stream) {
+  using namespace sedef;
+  if (!h_nrec) return fail(SEDEF_ERR_INVALID, "h_nrec is NULL");
+  *h_nrec = 0;
+  Derived D;
+  SEDEF_TRY(derive(p, &D));
+  if (nseq < 0 || (nseq > 0 && !h_seq_off)) return fail(SEDEF_ERR_INVALID, "bad offsets");
+  if (nseq == 0) return SEDEF_OK;
+  if (h_seq_off[0] != 0) return fail(SEDEF_ERR_INVALID, "offsets must start at 0");
+  for (int s = 0; s < nseq; ++s)
+    if (h_seq_off[s + 1] < h_seq_off[s]) return fail(SEDEF_ERR_INVALID, "offsets decrease");
+  const int64_t N = h_seq_off[nseq];
+  if (N == 0) return SEDEF_OK;
+  if (N > kNoallocMaxBases || nseq > kNoallocMaxSeqs)
+    return fail(SEDEF_ERR_UNSUPPORTED,
+                "sedef_sketch_noalloc: at most 268435456 bases in at most 4096 sequences "
+                "(the fixed scratch array); use sedef_sketch for larger inputs");
+  if (!d_packed || !d_mask || !d_nbits || (rec_cap > 0 && !d_rec))
+    return fail(SEDEF_ERR_INVALID, "NULL buffer");
+  int dev = 0;
+  SEDEF_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(SEDEF_ERR_UNSUPPORTED, "device index too large");
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_ptr[dev] = (unsigned char*)ptr;
+  }
+  unsigned char* base = g_noalloc_ptr[dev];
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(base);
+  uint32_t* toff = reinterpret_cast<uint32_t*>(base + kNoallocCountBytes);
+  int64_t* d_off = reinterpret_cast<int64_t*>(base + 2 * kNoallocCountBytes);
+  cudaStream_t st = (cudaStream_t)stream;
+  SEDEF_CUDA(cudaMemcpyAsync(d_off, h_seq_off, (size_t)(nseq + 1) * 8, cudaMemcpyHostToDevice, st));
+  SketchArgs a;
+  a.packed = d_packed;
+  a.mask = d_mask;
+  a.nbits = d_nbits;
+  a.off = d_off;
+  a.nseq = nseq;
+  a.N = N;
+  a.k = D.k;
+  a.w = D.w;
+  a.min_unmasked = D.min_unmasked;
+  a.kmask = D.kmask;
+  a.ntiles = (N + kSkTile - 1) / kSkTile;
+  int sms = 0;
+  SEDEF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int64_t grid = a.ntiles < (int64_t)sms * 8 ? a.ntiles : (int64_t)sms * 8;
+  k_sketch<false><<<(int)grid, kSkThreads, 0, st>>>(a, cnt, nullptr, nullptr, 0);
+  count_launch();
+  SEDEF_LAUNCHED("k_sketch_count");
+  k_scan_one_block<<<1, 1024, 0, st>>>(cnt, toff, a.ntiles);
+  count_launch();
+  SEDEF_LAUNCHED("k_scan_one_block");
+  uint32_t total = 0;
+  SEDEF_CUDA(cudaMemcpyAsync(&total, toff + a.ntiles, 4, cudaMemcpyDeviceToHost, st));
+  SEDEF_CUDA(cudaStreamSynchronize(st));
+  *h_nrec = total;
+  if ((int64_t)total > rec_cap) return fail(SEDEF_ERR_CAPACITY, "record buffer too small");
+  k_sketch<true><<<(int)grid, kSkThreads, 0, st>>>(a, nullptr, toff, d_rec, rec_cap);
+  count_launch();
+  SEDEF_LAUNCHED("k_sketch_write");
+  SEDEF_CUDA(cudaStreamSynchronize(st));
+  return SEDEF_OK;
+}
