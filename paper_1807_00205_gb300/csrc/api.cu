@@ -14,6 +14,7 @@ struct sedef_ctx {
   int sm_count = 0;
   cudaStream_t stream = nullptr;
   sedef::Pool pool;
+  sedef::Pool io;  // buffers of sedef_selfsearch_host, kept across calls
   void* pinned = nullptr;
   size_t pinned_cap = 0;
   // tracing: one (name, start, stop) per traced launch since the last report
@@ -228,6 +229,7 @@ int sedef_create(int device, void* stream, sedef_ctx** out) {
   sedef_ctx* c = new sedef_ctx();
   c->device = device;
   c->pool.device = device;
+  c->io.device = device;
   c->stream = (cudaStream_t)stream;
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
   *out = c;
@@ -244,6 +246,7 @@ int sedef_destroy(sedef_ctx* ctx) {
   }
   for (auto e : ctx->spare) cudaEventDestroy(e);
   ctx->pool.release();
+  ctx->io.release();
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   delete ctx;
   return SEDEF_OK;
@@ -449,19 +452,10 @@ int sedef_selfsearch_host(sedef_ctx* ctx, const uint8_t* h_seq, const int64_t* h
   int status = SEDEF_OK;
   int64_t nrec = 0, nruns = 0, nch = 0, nc = 0;
   const size_t nwords16 = (size_t)((N + 15) / 16), nwords32 = (size_t)((N + 31) / 32);
-  auto cleanup = [&]() {
-    cudaStreamSynchronize(st);
-    cudaFree(seq);
-    cudaFree(packed);
-    cudaFree(mask);
-    cudaFree(nbits);
-    cudaFree(off);
-    cudaFree(rec);
-    cudaFree(sorted);
-    cudaFree(runs);
-    cudaFree(chains);
-    cudaFree(cands);
-  };
+  // Device buffers come from the context's I/O pool: reused by the next
+  // call, released by sedef_destroy.
+  ctx->io.reset();
+  auto cleanup = [&]() { cudaStreamSynchronize(st); };
 #define STEP(x)                   \
   do {                            \
     status = (x);                 \
@@ -472,8 +466,8 @@ int sedef_selfsearch_host(sedef_ctx* ctx, const uint8_t* h_seq, const int64_t* h
   } while (0)
 #define DALLOC(ptr, bytes)                                                   \
   do {                                                                       \
-    if (cudaMalloc((void**)&ptr, (bytes) ? (bytes) : 256) != cudaSuccess) {  \
-      cudaGetLastError();                                                    \
+    ptr = (decltype(ptr))ctx->io.alloc((bytes) ? (bytes) : 256);             \
+    if (!ptr) {                                                              \
       cleanup();                                                             \
       return fail(SEDEF_ERR_OOM, "selfsearch: device allocation failed");    \
     }                                                                        \
@@ -492,8 +486,6 @@ int sedef_selfsearch_host(sedef_ctx* ctx, const uint8_t* h_seq, const int64_t* h
   DALLOC(rec, (size_t)rcap * 8);
   status = sedef_sketch(ctx, packed, mask, nbits, h_seq_off, nseq, p, rec, rcap, &nrec);
   if (status == SEDEF_ERR_CAPACITY) {
-    cudaFree(rec);
-    rec = nullptr;
     rcap = nrec;
     DALLOC(rec, (size_t)rcap * 8);
     status = sedef_sketch(ctx, packed, mask, nbits, h_seq_off, nseq, p, rec, rcap, &nrec);
@@ -507,8 +499,6 @@ int sedef_selfsearch_host(sedef_ctx* ctx, const uint8_t* h_seq, const int64_t* h
   status = sedef_filter(ctx, rec, nrec, h_seq_off, nseq, rec, sorted, off, nrec, h_seq_off, nseq, p,
                         runs, fcap, &nruns);
   if (status == SEDEF_ERR_CAPACITY) {
-    cudaFree(runs);
-    runs = nullptr;
     fcap = nruns;
     DALLOC(runs, (size_t)fcap * sizeof(sedef_run_t));
     status = sedef_filter(ctx, rec, nrec, h_seq_off, nseq, rec, sorted, off, nrec, h_seq_off, nseq,
