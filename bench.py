@@ -155,6 +155,27 @@ def algorithmic_bytes(seq, offsets, rec_rows, sorted_rows, runs, k, n, step):
     }
 
 
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None
+    when there is none or the kernel's source changed since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e or not e.get("sha256"):
+        return None
+    src = os.path.join(ROOT, e["source"])
+    if not os.path.exists(src):
+        return None
+    with open(src, "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != e["sha256"]:
+            return None
+    return int(e["bytes_per_launch"])
+
+
 def run_cpu_oracle_sample(seq):
     import oracle
     X = min(CPU_SAMPLE_BASES, len(seq))
@@ -314,7 +335,7 @@ def main():
     peak, peak_kind = peaks()
     per_launch_ms = dms / dcount
     roof = {"kernel": dname, "bound": "hbm", "peak": peak, "unit": "GB/s",
-            "peak_source": peak_kind, "traffic": None}
+            "peak_source": peak_kind, "traffic": measured_traffic(dname)}
     if dname in algo:
         launches_per_step = dcount / args.steps
         bytes_per_launch = algo[dname] / max(1.0, launches_per_step) if dname.startswith("k_rs") \

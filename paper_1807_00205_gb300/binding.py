@@ -264,7 +264,7 @@ class Context:
     def sedef_selfsearch_host(self, seq: np.ndarray, offsets, p: Params, cap=None):
         seq = np.ascontiguousarray(seq, dtype=np.uint8)
         off = _offsets(offsets)
-        cap = cap if cap is not None else max(1024, len(seq) // 1000)
+        cap = cap if cap is not None else max(4096, len(seq) // 256)
         count = ctypes.c_int64()
         for _ in range(2):
             out = np.zeros(cap, dtype=CAND_DTYPE)

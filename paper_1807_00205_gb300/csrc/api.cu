@@ -494,7 +494,7 @@ int sedef_selfsearch_host(sedef_ctx* ctx, const uint8_t* h_seq, const int64_t* h
   DALLOC(sorted, (size_t)(nrec ? nrec : 1) * 8);
   DALLOC(off, ((size_t(1) << (2 * D.k)) + 1) * 4);
   STEP(sedef_index(ctx, rec, nrec, p, sorted, off));
-  int64_t fcap = N / 64 + 4096;
+  int64_t fcap = N / 32 + 4096;
   DALLOC(runs, (size_t)fcap * sizeof(sedef_run_t));
   status = sedef_filter(ctx, rec, nrec, h_seq_off, nseq, rec, sorted, off, nrec, h_seq_off, nseq, p,
                         runs, fcap, &nruns);
