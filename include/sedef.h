@@ -72,7 +72,11 @@ typedef enum sedef_status {
  *                   the target after the query are reported, the mates may
  *                   overlap by at most floor(delta * n) bases (Section 2),
  *                   and a target occurrence inside the query window's own
- *                   k-mer span is not a shared k-mer
+ *                   k-mer span is not a shared k-mer.  self_mode = 2: the
+ *                   same, but every sequence is an independent genome
+ *                   (targets only on the query's own sequence), so one call
+ *                   self-searches a whole batch of genomes.  0: query
+ *                   windows against a separate target, every target window
  *   gap_max = 750   largest gap between chained anchors on either axis
  *   diag_max = 75   largest drift |gap_q - gap_t| between chained anchors,
  *                   ceil(n * delta_G) (Section 3.3: gaps bounded by l*delta_G)

@@ -154,7 +154,9 @@ std::map<uint64_t, int> window_hashes(const std::vector<Rec>& recs, int64_t lo, 
 // Valid target window starts j for query window i (Section 2 overlap rule in
 // self mode; windows lie inside one sequence).  In self mode only pairs with
 // the target after the query are searched (each unordered pair once), and
-// the mates may overlap by at most floor(delta*n) bases.
+// the mates may overlap by at most floor(delta*n) bases.  self_mode 2 treats
+// every sequence as an independent genome: targets only on the query's own
+// sequence.
 std::vector<std::pair<int64_t, int64_t>> valid_targets(
     const std::vector<std::pair<int64_t, int64_t>>& tr, int qseq, int64_t i, const Par& P) {
   std::vector<std::pair<int64_t, int64_t>> v;
@@ -165,6 +167,7 @@ std::vector<std::pair<int64_t, int64_t>> valid_targets(
     if (P.self_mode) {
       if ((int)u < qseq) continue;
       if ((int)u == qseq) lo = std::max(lo, i + P.n - overlap);
+      if (P.self_mode == 2 && (int)u != qseq) continue;  // each sequence on its own
     }
     if (lo <= hi) v.push_back({lo, hi});
   }

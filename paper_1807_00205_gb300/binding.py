@@ -117,6 +117,15 @@ def params_from_dict(d: dict) -> Params:
     return params(**{k: v for k, v in d.items() if k in keys})
 
 
+def params_from_struct(p: Params, **kw) -> Params:
+    """A copy of p with some fields replaced."""
+    q = Params()
+    ctypes.pointer(q)[0] = p
+    for key, v in kw.items():
+        setattr(q, "query_step" if key == "step" else key, v)
+    return q
+
+
 def _ptr(t) -> int:
     if t is None:
         return None

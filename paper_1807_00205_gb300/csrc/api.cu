@@ -157,7 +157,8 @@ int derive(const sedef_params* p, Derived* d) {
   d->span = p->n - p->k;
   d->step = p->query_step;
   d->max_occ = p->max_occ;
-  d->self_mode = p->self_mode ? 1 : 0;
+  if (p->self_mode < 0 || p->self_mode > 2) return fail(SEDEF_ERR_INVALID, "self_mode must be 0, 1 or 2");
+  d->self_mode = p->self_mode;
   d->gap_max = p->gap_max;
   d->diag_max = p->diag_max;
   d->min_unmasked = p->min_unmasked;

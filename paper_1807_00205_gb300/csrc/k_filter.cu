@@ -125,6 +125,7 @@ __device__ void segment(const FArgs& a, const WinInfo& w, RunState& r, int64_t j
     if (a.self_mode) {
       if (u < w.qseq) ok = false;
       else if (u == w.qseq) lo = max(lo, w.i + a.n - a.overlap);
+      else if (a.self_mode == 2) ok = false;  // independent genomes
     }
     const int64_t pend = min(j1, en - 1);
     const int64_t vlo = max(x, lo), vhi = min(pend, hi);
@@ -290,7 +291,26 @@ struct QBuild {
   int* tmp;
 };
 
-__device__ int build_wq(const FArgs& a, QBuild q, int c) {
+// Postings of hash h restricted to target positions [lo, hi) (binary
+// searches inside the posting list, which is sorted by position).
+__device__ __forceinline__ void posting_window(const uint64_t* idx, uint32_t* st, uint32_t* len,
+                                               int64_t lo, int64_t hi) {
+  uint32_t a0 = *st, a1 = *st + *len;
+  uint32_t l = a0, h = a1;
+  while (l < h) {
+    const uint32_t mid = (l + h) >> 1;
+    if ((int64_t)rec_pos(idx[mid]) < lo) l = mid + 1; else h = mid;
+  }
+  uint32_t l2 = l, h2 = a1;
+  while (l2 < h2) {
+    const uint32_t mid = (l2 + h2) >> 1;
+    if ((int64_t)rec_pos(idx[mid]) < hi) l2 = mid + 1; else h2 = mid;
+  }
+  *st = l;
+  *len = l2 - l;
+}
+
+__device__ int build_wq(const FArgs& a, QBuild q, int c, int64_t seq_lo = 0, int64_t seq_hi = 0) {
   const int np = next_pow2(c < 2 ? 2 : c);
   for (int x = threadIdx.x; x < np; x += blockDim.x)
     if (x >= c) q.qkey[x] = kNone;
@@ -311,6 +331,8 @@ __device__ int build_wq(const FArgs& a, QBuild q, int c) {
         st = a.toff[h];
         len = a.toff[h + 1] - st;
         keep = (a.max_occ > 0 && (int)len > a.max_occ) ? 0 : 1;
+        // independent genomes: only the query's own sequence can hold targets
+        if (keep && a.self_mode == 2) posting_window(a.tsorted, &st, &len, seq_lo, seq_hi);
       }
     }
     int tot;
@@ -405,7 +427,13 @@ __global__ void __launch_bounds__(kFThreads) k_filter_fast(FArgs a) {
     qb_.pst = S.pst;
     qb_.plen = S.plen;
     qb_.tmp = S.tmp;
-    const int s = build_wq(a, qb_, c);
+    int64_t seq_lo = 0, seq_hi = 0;
+    if (a.self_mode == 2) {
+      const int sq = a.win_seq[wdx];
+      seq_lo = a.tseq[sq];
+      seq_hi = a.tseq[sq + 1];
+    }
+    const int s = build_wq(a, qb_, c, seq_lo, seq_hi);
     if (s == 0) continue;
     // prefix of posting lengths (hit enumeration)
     if (threadIdx.x < 32) {
@@ -560,7 +588,13 @@ __device__ int slow_wq(const FArgs& a, SlowSmem& S, int64_t wdx) {
   q.pst = S.pst;
   q.plen = S.plen;
   q.tmp = S.tmp;
-  return build_wq(a, q, c);
+  int64_t seq_lo = 0, seq_hi = 0;
+  if (a.self_mode == 2) {
+    const int sq = a.win_seq[wdx];
+    seq_lo = a.tseq[sq];
+    seq_hi = a.tseq[sq + 1];
+  }
+  return build_wq(a, q, c, seq_lo, seq_hi);
 }
 
 // Hits of overflow window v: visits (t, hid, o) for every compatible posting.

@@ -106,6 +106,8 @@ def filter_runs(qrecs, qoff, trecs, toff, p, tau):
                         continue
                     if u == qs_:
                         lo = max(lo, i + n - overlap)
+                    elif p["self_mode"] == 2:
+                        continue
                 run = None
                 for j in range(lo, hi + 1):
                     c = shared(j)

@@ -170,6 +170,7 @@ FILTER_CASES = [
     (13, dict(TINY, self_mode=0)),
     (14, dict(TINY, max_occ=4)),
     (15, dict(TINY, k=4, w=3, n=25, step=5)),
+    (16, dict(TINY, self_mode=2)),
 ]
 
 
