@@ -285,15 +285,57 @@ def batch_arm(args):
     ctx.close()
 
 
+def serve_arm(args):
+    """Resident index of the 100 Mbp chromosome workload; Poisson streams of
+    query regions (10 kbp-5 Mbp, 0-25% mutation) at each rate, served by two
+    continuously batching workers and by the plain one-request-per-pass form."""
+    import torch
+    from paper_1807_00205_gb300 import binding, serve, synth
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    g = synth.chromosome_100mbp()
+    pool = synth.query_regions(g, 48)
+    p = binding.params()
+    ctx = binding.Context(local)
+    index = serve.ResidentIndex(ctx, g.seq, g.offsets, p)
+    results = []
+    for rate in [float(x) for x in args.rates.split(",")]:
+        row = {"rate": rate}
+        for mode, workers, batching in [("served", 2, True), ("plain", 1, False)]:
+            srv = serve.Server(index, p, workers=workers, batching=batching, device=local)
+            srv.warm(pool[:2])
+            srv.start()
+            row[mode] = serve.run_load(srv, pool, rate, args.requests, seed=int(rate))
+            srv.close()
+        results.append(row)
+    top = results[-1]
+    line = {
+        "metric": METRIC, "value": top["served"]["mbp_s"], "unit": "Mbp/s", "n_gpus": 1,
+        "steps": args.requests, "warmup": 2, "ms_per_step": top["served"]["mean_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": "serving: resident index of the 100 Mbp chromosome workload "
+                               "(stand-in for 3.1 Gbp); Poisson query regions 10 kbp-5 Mbp "
+                               "log-uniform cut from it with 0-25% mutation",
+                   "served": "2 workers (own streams), continuous batching, admission by free HBM",
+                   "plain": "1 worker, one request per pass"},
+        "rates": results,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="chromosome", choices=["chromosome", "plain", "batch"])
+    ap.add_argument("--workload", default="chromosome", choices=["chromosome", "plain", "batch", "serve"])
     ap.add_argument("--batch-count", type=int, default=200,
                     help="genomes in the batch workload")
+    ap.add_argument("--rates", default="50,200,1000", help="serving: request rates per second")
+    ap.add_argument("--requests", type=int, default=200, help="serving: requests per rate")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--trace", action="store_true", help="print the per-kernel table to stderr")
@@ -303,6 +345,9 @@ def main():
         return
     if args.workload == "batch":
         batch_arm(args)
+        return
+    if args.workload == "serve":
+        serve_arm(args)
         return
 
     import torch

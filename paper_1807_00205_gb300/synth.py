@@ -330,3 +330,24 @@ def small_case(seed: int, lengths=(20_000,), n_sd: int = 3, sd_lo: int = 1000,
             if L > 400:
                 add_n_gaps(rng, sub, max(L // 2, 200), 5, min(60, L // 8))
     return Genome(seq, offs, planted, f"small-{seed}")
+
+
+def query_regions(genome: Genome, count: int, seed: int = 0x5EDEF005, len_lo: int = 10_000,
+                  len_hi: int = 5_000_000, mut_lo: float = 0.0, mut_hi: float = 0.25) -> list:
+    """Query regions for the serving workload: lengths log-uniform in
+    [len_lo, len_hi] cut from the genome (within one sequence), mutated by a
+    fraction U[mut_lo, mut_hi] of edit events, reverse-complemented half of
+    the time.  Returns uint8 ASCII arrays."""
+    rng = np.random.default_rng(seed)
+    out = []
+    seq_len = np.diff(genome.offsets)
+    for _ in range(count):
+        L = int(log_uniform_int(rng, len_lo, len_hi + 1))
+        s = int(rng.choice(len(seq_len), p=seq_len / seq_len.sum()))
+        L = min(L, int(seq_len[s]))
+        a = int(genome.offsets[s] + rng.integers(0, seq_len[s] - L + 1))
+        piece = mutate(rng, genome.seq[a:a + L], 1.0 - float(rng.uniform(mut_lo, mut_hi)))
+        if rng.random() < 0.5:
+            piece = reverse_complement(piece)
+        out.append(np.ascontiguousarray(piece))
+    return out

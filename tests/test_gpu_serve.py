@@ -1,0 +1,37 @@
+"""Serving: each request's candidates are the same alone, in one batch, and
+through the continuously batched server with overlapping workers."""
+import numpy as np
+import pytest
+
+from paper_1807_00205_gb300 import binding, serve, synth
+from tests.gpu_helpers import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def test_results_same_alone_and_in_the_mix():
+    need_gpu()
+    g = synth.plain_2mbp()
+    ctx = binding.Context(0)
+    p = binding.params()
+    index = serve.ResidentIndex(ctx, g.seq, g.offsets, p)
+    pool = synth.query_regions(g, 14, seed=9, len_lo=5_000, len_hi=60_000)
+    alone = []
+    for k, q in enumerate(pool):
+        r = serve.Request(rid=k, seq=q)
+        serve.search(ctx, index, [r], p)
+        alone.append(r.cands)
+    mix = [serve.Request(rid=k, seq=q) for k, q in enumerate(pool)]
+    serve.search(ctx, index, mix, p)
+    for a, r in zip(alone, mix):
+        assert np.array_equal(a, r.cands)
+    assert sum(len(a) for a in alone) > 0
+    srv = serve.Server(index, p, workers=2, batching=True)
+    srv.start()
+    res = serve.run_load(srv, pool, rate=2000.0, count=28, seed=1)
+    srv.close()
+    got = {r.rid: r.cands for r in srv.completed}
+    for k in range(28):
+        assert np.array_equal(got[k], alone[k % len(pool)]), k
+    assert res["requests"] == 28
+    ctx.close()
