@@ -136,9 +136,10 @@ class Server:
                         for c in self.ctxs]
         self.batches = 0
 
-    def warm(self, reqs: list):
+    def warm(self, seqs: list):
+        """One untimed pass per worker over these query sequences."""
         for c in self.ctxs:
-            search(c, self.index, reqs, self.p)
+            search(c, self.index, [Request(rid=-1, seq=q) for q in seqs], self.p)
 
     def start(self):
         for t in self.threads:
