@@ -15,6 +15,22 @@ import numpy as np
 from . import binding
 
 
+def shard(items: list, rank: int, world: int) -> list:
+    """The items rank `rank` of `world` processes: a contiguous block, sizes
+    balanced by total length when items have `.length` (greedy by prefix)."""
+    if world <= 1:
+        return list(items)
+    lengths = [getattr(x, "length", 1) for x in items]
+    total = float(sum(lengths)) or 1.0
+    out, acc = [], 0.0
+    for x, ln in zip(items, lengths):
+        mid = acc + ln / 2.0
+        if int(mid * world / total) == rank or (rank == world - 1 and mid * world / total >= world):
+            out.append(x)
+        acc += ln
+    return out
+
+
 def concatenate(genomes) -> tuple:
     """(seq, offsets) of the genomes, one sequence per genome."""
     parts = [np.ascontiguousarray(g.seq, dtype=np.uint8) for g in genomes]
