@@ -1227,54 +1227,58 @@ __global__ void __launch_bounds__(32 * (kLean ? kRWarps : kRWarpsBig)) k_refine(
 
 // ------------------------------------------------- batched lean refine ----
 //
-// A warp sets up runs one at a time (cooperatively: W_Q, candidates, kept
-// records, domain) into slots of a per-warp arena, then every lane rolls
-// its own run through its slot, so up to 32 rolls proceed side by side.
-// Runs beyond the lean limits (more than 256 query records or 512 span
-// records) go to the large kernel.
+// A warp sets up runs one at a time (cooperatively) into slots of a per-warp
+// arena, then every lane rolls its own run through its slot, so many rolls
+// proceed side by side.  Setup per run: the span records are read once
+// (hash, W_Q membership, candidate flag); the domain is W_Q (already
+// sorted) merged by rank with the sorted distinct non-W_Q kept hashes, so
+// W_Q is never re-sorted; slots keep 16-bit offsets of positions and one
+// counter per domain hash (presence for non-W_Q hashes, sharedness for W_Q
+// hashes).  Transient setup data lives in the arena above the new slot.
+// Runs beyond the lean limits (more than 256 query records, 512 span
+// records or a span of 65,536 bases) go to the large kernel.
 
 constexpr int kBWarps = 4;
-constexpr int kBQC = 256, kBRC = 512, kBDC = kBQC + kBRC;
-static_assert(kBDC <= 1024, "the domain sort buffer holds 1024 entries");
-constexpr int kArenaWords = 2560;  // 10 KB of slots per warp
+constexpr int kBQC = 256, kBRC = 512;
+constexpr int kArenaWords = 2816;  // 11 KB per warp
 
 struct BatchWarp {
   uint32_t arena[kArenaWords];
-  uint32_t dom[1024];    // domain sort buffer: next power of two >= kBDC
-  uint32_t tmp_h[kBRC];  // kept records' hashes
   uint32_t wq_h[kBQC];
+  uint16_t wq_dom[kBQC];  // domain index of each W_Q hash (current run)
   uint8_t wq_m[kBQC];
-  uint32_t h_off[32];    // slot start (words)
-  uint32_t h_run[32];    // run index
-  uint16_t h_nrel[32], h_D[32], h_Dmax[32], h_s[32];
+  uint8_t rflag[kBRC];    // span record: bit0 strand, bit1 in W_Q, bit2 candidate, bit3 kept
+  uint32_t h_off[32];     // slot start (words)
+  uint32_t h_run[32];     // run index
+  uint16_t h_nrel[32], h_D[32], h_dmax[32], h_s[32];
 };
 
 struct Slot {
-  uint32_t* tpos;
-  uint16_t* tdx;
-  uint8_t* tsh;
-  uint16_t* cntT;
-  uint16_t* cntS;
-  uint8_t* qm;
-  uint32_t* pb;
-  uint32_t* sb;
+  uint16_t* tpos;  // position - j_a
+  uint16_t* tdx;   // domain index
+  uint8_t* tsh;    // 1: a W_Q hash (shared-compatible occurrence); 0: a non-W_Q hash
+  uint16_t* cnt;   // per domain hash: occurrences in the window
+  uint8_t* qm;     // nonzero for W_Q hashes
+  uint32_t* pb;    // present
+  uint32_t* sb;    // shared
 };
 
 __device__ __forceinline__ int slot_words(int nrel, int dmax) {
-  return nrel + (nrel + 1) / 2 + (nrel + 3) / 4 + dmax + (dmax + 3) / 4 + 2 * ((dmax + 31) / 32);
+  return (nrel + 1) / 2 + (nrel + 1) / 2 + (nrel + 3) / 4 + (dmax + 1) / 2 + (dmax + 3) / 4 +
+         2 * ((dmax + 31) / 32);
 }
 
 __device__ __forceinline__ Slot slot_at(uint32_t* base, int nrel, int dmax) {
   Slot sl;
-  sl.tpos = base;
-  uint32_t* p = base + nrel;
+  uint32_t* p = base;
+  sl.tpos = reinterpret_cast<uint16_t*>(p);
+  p += (nrel + 1) / 2;
   sl.tdx = reinterpret_cast<uint16_t*>(p);
   p += (nrel + 1) / 2;
   sl.tsh = reinterpret_cast<uint8_t*>(p);
   p += (nrel + 3) / 4;
-  sl.cntT = reinterpret_cast<uint16_t*>(p);
-  sl.cntS = sl.cntT + dmax;
-  p += dmax;
+  sl.cnt = reinterpret_cast<uint16_t*>(p);
+  p += (dmax + 1) / 2;
   sl.qm = reinterpret_cast<uint8_t*>(p);
   p += (dmax + 3) / 4;
   sl.pb = p;
@@ -1284,16 +1288,19 @@ __device__ __forceinline__ Slot slot_at(uint32_t* base, int nrel, int dmax) {
 
 // Rolls one run (single lane): enters the first window's records, finds
 // theta (s-th present hash) and est by scanning the bitsets, then keeps both
-// exact through every enter/leave as in the large kernel.
+// exact through every enter/leave (as in the large kernel).
 __device__ void roll_run(const Slot& sl, int nrel, int D, int s, int mx, int64_t plo, int64_t phi,
                          int span, int* best_out, int64_t* jstar_out) {
   const int nwords = (D + 31) >> 5;
+  const int64_t base = plo;
   int e = 0, l = 0;
   int64_t j = plo;
-  while (e < nrel && (int64_t)sl.tpos[e] <= j + span) {
+  while (e < nrel && base + sl.tpos[e] <= j + span) {
     const int d = sl.tdx[e];
-    if (sl.cntT[d]++ == 0) sl.pb[d >> 5] |= 1u << (d & 31);
-    if (sl.tsh[e] && sl.cntS[d]++ == 0) sl.sb[d >> 5] |= 1u << (d & 31);
+    if (sl.cnt[d]++ == 0) {
+      if (sl.tsh[e]) sl.sb[d >> 5] |= 1u << (d & 31);
+      else sl.pb[d >> 5] |= 1u << (d & 31);
+    }
     ++e;
   }
   int theta = 0, est = 0;
@@ -1335,45 +1342,56 @@ __device__ void roll_run(const Slot& sl, int nrel, int D, int s, int mx, int64_t
       jstar = j;
       if (best >= mx) break;
     }
-    const int64_t ne = e < nrel ? (int64_t)sl.tpos[e] - span : INT64_MAX;
-    const int64_t nl = l < e ? (int64_t)sl.tpos[l] + 1 : INT64_MAX;
+    const int64_t ne = e < nrel ? base + sl.tpos[e] - span : INT64_MAX;
+    const int64_t nl = l < e ? base + sl.tpos[l] + 1 : INT64_MAX;
     const int64_t nx = min(ne, nl);
     if (nx > phi) break;
     j = nx;
-    while (l < e && (int64_t)sl.tpos[l] + 1 <= j) {
+    while (l < e && base + sl.tpos[l] + 1 <= j) {
       const int d = sl.tdx[l];
-      if (--sl.cntT[d] == 0 && sl.qm[d] == 0) {
-        sl.pb[d >> 5] &= ~(1u << (d & 31));
-        if (d <= theta) {
-          theta = succ(theta);
-          est += bit(sl.sb, theta);
+      if (--sl.cnt[d] == 0) {
+        if (sl.tsh[l]) {
+          sl.sb[d >> 5] &= ~(1u << (d & 31));
+          if (d <= theta) --est;
+        } else {
+          sl.pb[d >> 5] &= ~(1u << (d & 31));
+          if (d <= theta) {
+            theta = succ(theta);
+            est += bit(sl.sb, theta);
+          }
         }
-      }
-      if (sl.tsh[l] && --sl.cntS[d] == 0) {
-        sl.sb[d >> 5] &= ~(1u << (d & 31));
-        if (d <= theta) --est;
       }
       ++l;
     }
-    while (e < nrel && (int64_t)sl.tpos[e] - span <= j) {
+    while (e < nrel && base + sl.tpos[e] - span <= j) {
       const int d = sl.tdx[e];
-      if (sl.cntT[d]++ == 0 && sl.qm[d] == 0) {
-        sl.pb[d >> 5] |= 1u << (d & 31);
-        if (d < theta) {
-          const int old = theta;
-          theta = pred(theta);
-          est -= bit(sl.sb, old);
+      if (sl.cnt[d]++ == 0) {
+        if (sl.tsh[e]) {
+          sl.sb[d >> 5] |= 1u << (d & 31);
+          if (d <= theta) ++est;
+        } else {
+          sl.pb[d >> 5] |= 1u << (d & 31);
+          if (d < theta) {
+            const int old = theta;
+            theta = pred(theta);
+            est -= bit(sl.sb, old);
+          }
         }
-      }
-      if (sl.tsh[e] && sl.cntS[d]++ == 0) {
-        sl.sb[d >> 5] |= 1u << (d & 31);
-        if (d <= theta) ++est;
       }
       ++e;
     }
   }
   *best_out = best;
   *jstar_out = jstar;
+}
+
+__device__ __forceinline__ int lb_u32(const uint32_t* v, int n, uint32_t x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (v[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
 }
 
 __global__ void __launch_bounds__(32 * kBWarps) k_refine_batch(RefineArgs a) {
@@ -1391,7 +1409,7 @@ __global__ void __launch_bounds__(32 * kBWarps) k_refine_batch(RefineArgs a) {
       const int64_t ri = B.h_run[lane];
       const sedef_run_t run = a.runs[ri];
       const int nrel = B.h_nrel[lane], D = B.h_D[lane], sq = B.h_s[lane];
-      const Slot sl = slot_at(B.arena + B.h_off[lane], nrel, B.h_Dmax[lane]);
+      const Slot sl = slot_at(B.arena + B.h_off[lane], nrel, B.h_dmax[lane]);
       int best;
       int64_t jstar;
       roll_run(sl, nrel, D, sq, run.max_shared, run.j_a, run.j_b, a.span, &best, &jstar);
@@ -1420,7 +1438,7 @@ __global__ void __launch_bounds__(32 * kBWarps) k_refine_batch(RefineArgs a) {
       const int64_t qa = rg.x, qb = rg.y, rlo = rg.z, rend = rg.w;
       const int c = (int)(qb - qa);
       const int nr = (int)(rend - rlo);
-      if (c > kBQC || nr > kBRC) {
+      if (c > kBQC || nr > kBRC || (int64_t)run.j_b + a.span - run.j_a >= 65536) {
         if (lane == 0) a.big[atomicAdd(a.nbig, 1u)] = (uint32_t)ri;
         continue;
       }
@@ -1429,26 +1447,28 @@ __global__ void __launch_bounds__(32 * kBWarps) k_refine_batch(RefineArgs a) {
         prev_qa = qa;
         prev_qb = qb;
         const int npq = next_pow2(c < 2 ? 2 : c);
+        if (used + npq > kArenaWords) flush();
+        uint32_t* buf = B.arena + used;  // sort space above the slots (transient)
         for (int x = lane; x < npq; x += 32) {
           uint32_t key = kNone;
           if (x < c) {
             const uint64_t r = a.qrec[qa + x];
             key = (rec_hash(r) << 1) | rec_strand(r);
           }
-          B.dom[x] = key;
+          buf[x] = key;
         }
         __syncwarp();
-        warp_sort_u32(B.dom, npq);
+        warp_sort_u32(buf, npq);
         s = 0;
         for (int base = 0; base < c; base += 32) {
           const int x = base + lane;
           uint32_t h = 0, mask = 0;
           bool first = false;
           if (x < c) {
-            h = B.dom[x] >> 1;
-            first = (x == 0) || ((B.dom[x - 1] >> 1) != h);
+            h = buf[x] >> 1;
+            first = (x == 0) || ((buf[x - 1] >> 1) != h);
             if (first) {
-              for (int y = x; y < c && (B.dom[y] >> 1) == h; ++y) mask |= 1u << (B.dom[y] & 1u);
+              for (int y = x; y < c && (buf[y] >> 1) == h; ++y) mask |= 1u << (buf[y] & 1u);
               if (a.max_occ > 0 && (int)(a.toff[h + 1] - a.toff[h]) > a.max_occ) first = false;
             }
           }
@@ -1463,106 +1483,118 @@ __global__ void __launch_bounds__(32 * kBWarps) k_refine_batch(RefineArgs a) {
         __syncwarp();
       }
       auto wq_find = [&](uint32_t h) {
-        int lo2 = 0, hi2 = s;
-        while (lo2 < hi2) {
-          const int mid = (lo2 + hi2) >> 1;
-          if (B.wq_h[mid] < h) lo2 = mid + 1; else hi2 = mid;
-        }
+        const int lo2 = lb_u32(B.wq_h, s, h);
         return (lo2 < s && B.wq_h[lo2] == h) ? lo2 : -1;
       };
-      // ---- candidates (see the large kernel): max(C), then the kept records
+      // ---- space: the slot's worst case plus transient hashes and sort buffer
+      const int slot_bound = slot_words(nr, s + nr);
+      const int need = slot_bound + nr + next_pow2(nr < 2 ? 2 : nr);
+      if (nslots == 32 || used + need > kArenaWords) flush();
+      // ---- pass over the span records: hash (transient), flags, max(C)
+      uint32_t* th = B.arena + used + slot_bound;  // transient: hashes of the span records
       uint32_t cmax = 0;
       bool have_c = false;
-      int nrel = 0;
-      for (int pass = 0; pass < 2; ++pass) {
-        for (int base = 0; base < nr; base += 32) {
-          const int x = base + lane;
-          bool flag = false;
-          uint32_t h = 0;
-          if (x < nr) {
-            const uint64_t r = a.trec[rlo + x];
-            h = rec_hash(r);
-            const uint32_t t = rec_pos(r), st = rec_strand(r);
-            const int q = wq_find(h);
-            const bool self = a.self_mode && (int64_t)t >= i && (int64_t)t <= i + a.span;
-            const bool cand = q >= 0 && !self && ((B.wq_m[q] >> (st ^ (uint32_t)o)) & 1u);
-            flag = pass == 0 ? cand : (q >= 0 ? cand : (have_c && h < cmax));
-          }
-          if (pass == 0) {
-            uint32_t hm = flag ? h : 0u;
-            const bool any = __any_sync(0xffffffffu, flag);
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, d));
-            if (any) {
-              cmax = have_c ? max(cmax, hm) : hm;
-              have_c = true;
-            }
-          } else {
-            nrel += __popc(__ballot_sync(0xffffffffu, flag));
-          }
-        }
-        if (!have_c) break;
-      }
-      const int dmax = s + nrel;
-      const int words = slot_words(nrel, dmax);
-      if (nslots == 32 || used + words > kArenaWords) flush();
-      const int off = used;
-      const Slot sl = slot_at(B.arena + off, nrel, dmax);
-      // ---- kept records: positions, hashes, strands
-      int k = 0;
-      for (int base = 0; base < nr && nrel > 0; base += 32) {
+      for (int base = 0; base < nr; base += 32) {
         const int x = base + lane;
-        bool keep = false;
-        uint32_t h = 0, t = 0, st = 0;
+        bool cand = false;
+        uint32_t h = 0;
         if (x < nr) {
           const uint64_t r = a.trec[rlo + x];
           h = rec_hash(r);
-          t = rec_pos(r);
-          st = rec_strand(r);
+          const uint32_t t = rec_pos(r), st = rec_strand(r);
           const int q = wq_find(h);
-          if (q >= 0) {
-            const bool self = a.self_mode && (int64_t)t >= i && (int64_t)t <= i + a.span;
-            keep = !self && ((B.wq_m[q] >> (st ^ (uint32_t)o)) & 1u);
-          } else {
-            keep = h < cmax;
-          }
+          const bool self = a.self_mode && (int64_t)t >= i && (int64_t)t <= i + a.span;
+          cand = q >= 0 && !self && ((B.wq_m[q] >> (st ^ (uint32_t)o)) & 1u);
+          th[x] = h;
+          B.rflag[x] = (uint8_t)(st | ((q >= 0) ? 2u : 0u) | (cand ? 4u : 0u));
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-          const int y = k + __popc(bal & lanemask_lt());
-          sl.tpos[y] = t;
-          B.tmp_h[y] = h;
-          sl.tsh[y] = (uint8_t)st;
+        uint32_t hm = cand ? h : 0u;
+        const bool any = __any_sync(0xffffffffu, cand);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) hm = max(hm, __shfl_xor_sync(0xffffffffu, hm, d));
+        if (any) {
+          cmax = have_c ? max(cmax, hm) : hm;
+          have_c = true;
         }
-        k += __popc(bal);
       }
       __syncwarp();
-      // ---- domain
-      const int nd0 = s + nrel;
-      const int npd = next_pow2(nd0 < 2 ? 2 : nd0);
-      for (int x = lane; x < npd; x += 32) {
-        uint32_t v = kNone;
-        if (x < s) v = B.wq_h[x];
-        else if (x < nd0) v = B.tmp_h[x - s];
-        B.dom[x] = v;
-      }
-      __syncwarp();
-      warp_sort_u32(B.dom, npd);
-      int D = 0;
-      for (int base = 0; base < nd0; base += 32) {
+      // ---- kept records: candidates' occurrences and non-W_Q hashes below max(C)
+      int nrel = 0, n1 = 0;
+      for (int base = 0; base < nr && have_c; base += 32) {
         const int x = base + lane;
-        const uint32_t v = x < nd0 ? B.dom[x] : kNone;
-        const bool first = x < nd0 && (x == 0 || B.dom[x - 1] != v);
+        bool keep = false, nonq = false;
+        if (x < nr) {
+          const uint32_t f = B.rflag[x];
+          nonq = !(f & 2u) && th[x] < cmax;
+          keep = (f & 4u) || nonq;
+          if (keep) B.rflag[x] = (uint8_t)(f | 8u);
+        }
+        nrel += __popc(__ballot_sync(0xffffffffu, keep));
+        n1 += __popc(__ballot_sync(0xffffffffu, nonq));
+      }
+      __syncwarp();
+      const int dmax = s + n1;
+      const Slot sl = slot_at(B.arena + used, nrel, dmax);
+      uint32_t* u1 = th + nr;  // transient sort buffer of the non-W_Q kept hashes
+      const int np1 = next_pow2(n1 < 2 ? 2 : n1);
+      {
+        int y = 0, z = 0;
+        for (int base = 0; base < nr && nrel > 0; base += 32) {
+          const int x = base + lane;
+          bool keep = false, nonq = false;
+          uint32_t f = 0;
+          if (x < nr) {
+            f = B.rflag[x];
+            keep = (f & 8u) != 0;
+            nonq = keep && !(f & 2u);
+          }
+          const unsigned bk = __ballot_sync(0xffffffffu, keep);
+          const unsigned bn = __ballot_sync(0xffffffffu, nonq);
+          if (keep) {
+            const int yy = y + __popc(bk & lanemask_lt());
+            sl.tpos[yy] = (uint16_t)(rec_pos(a.trec[rlo + x]) - run.j_a);
+            sl.tsh[yy] = (f & 2u) ? 1 : 0;
+          }
+          if (nonq) u1[z + __popc(bn & lanemask_lt())] = th[x];
+          y += __popc(bk);
+          z += __popc(bn);
+        }
+        for (int x = n1 + lane; x < np1; x += 32) u1[x] = kNone;
+      }
+      __syncwarp();
+      warp_sort_u32(u1, np1);
+      int u = 0;  // distinct non-W_Q kept hashes, compacted in place
+      for (int base = 0; base < n1; base += 32) {
+        const int x = base + lane;
+        const uint32_t v = x < n1 ? u1[x] : kNone;
+        const bool first = x < n1 && (x == 0 || u1[x - 1] != v);
         const unsigned bal = __ballot_sync(0xffffffffu, first);
         __syncwarp();
-        if (first) B.dom[D + __popc(bal & lanemask_lt())] = v;
+        if (first) u1[u + __popc(bal & lanemask_lt())] = v;
         __syncwarp();
-        D += __popc(bal);
+        u += __popc(bal);
       }
-      for (int x = lane; x < nrel; x += 32) sl.tdx[x] = (uint16_t)dom_find(B.dom, D, B.tmp_h[x]);
-      for (int x = lane; x < D; x += 32) {
-        sl.cntT[x] = 0;
-        sl.cntS[x] = 0;
+      const int D = s + u;
+      for (int k = lane; k < s; k += 32) B.wq_dom[k] = (uint16_t)(k + lb_u32(u1, u, B.wq_h[k]));
+      __syncwarp();
+      {
+        int y = 0;
+        for (int base = 0; base < nr && nrel > 0; base += 32) {
+          const int x = base + lane;
+          const bool keep = x < nr && (B.rflag[x] & 8u);
+          const unsigned bk = __ballot_sync(0xffffffffu, keep);
+          if (keep) {
+            const uint32_t h = th[x];
+            int d;
+            if (B.rflag[x] & 2u) d = B.wq_dom[wq_find(h)];
+            else d = lb_u32(u1, u, h) + lb_u32(B.wq_h, s, h);
+            sl.tdx[y + __popc(bk & lanemask_lt())] = (uint16_t)d;
+          }
+          y += __popc(bk);
+        }
+      }
+      for (int x = lane; x < dmax; x += 32) {
+        sl.cnt[x] = 0;
         sl.qm[x] = 0;
       }
       for (int x = lane; x < (dmax + 31) / 32; x += 32) {
@@ -1570,29 +1602,22 @@ __global__ void __launch_bounds__(32 * kBWarps) k_refine_batch(RefineArgs a) {
         sl.sb[x] = 0;
       }
       __syncwarp();
-      for (int x = lane; x < s; x += 32) {
-        const int d = dom_find(B.dom, D, B.wq_h[x]);
-        sl.qm[d] = B.wq_m[x];
+      for (int k = lane; k < s; k += 32) {
+        const int d = B.wq_dom[k];
+        sl.qm[d] = 1;
         atomicOr(&sl.pb[d >> 5], 1u << (d & 31));
       }
-      __syncwarp();
-      for (int x = lane; x < nrel; x += 32) {
-        const uint32_t t = sl.tpos[x], st = sl.tsh[x];
-        const int d = sl.tdx[x];
-        const bool self = a.self_mode && (int64_t)t >= i && (int64_t)t <= i + a.span;
-        sl.tsh[x] = (!self && ((sl.qm[d] >> (st ^ (uint32_t)o)) & 1u)) ? 1 : 0;
-      }
       if (lane == 0) {
-        B.h_off[nslots] = (uint32_t)off;
+        B.h_off[nslots] = (uint32_t)used;
         B.h_run[nslots] = (uint32_t)ri;
         B.h_nrel[nslots] = (uint16_t)nrel;
         B.h_D[nslots] = (uint16_t)D;
-        B.h_Dmax[nslots] = (uint16_t)dmax;
+        B.h_dmax[nslots] = (uint16_t)dmax;
         B.h_s[nslots] = (uint16_t)s;
       }
       __syncwarp();
       ++nslots;
-      used += words;
+      used += slot_words(nrel, dmax);
     }
   }
   flush();
