@@ -275,6 +275,25 @@ int sedef_filter(sedef_ctx* ctx, const uint64_t* d_qrec, int64_t nq, const int64
                  const sedef_params* p, sedef_run_t* d_runs, int64_t run_cap, int64_t* h_nruns);
 
 /*
+ * Autotuner of the filter's first shared-memory tier: times each compiled
+ * shape (threads per query window; hits and dense groups a window may keep
+ * in shared memory) on a uniform sample of at most 8192 of the query
+ * windows (same arguments as sedef_filter) and keeps the fastest for later
+ * sedef_filter calls on this context; *variant_out receives its number.
+ * Results never depend on the shape: windows a shape cannot hold move to
+ * the next tier.  Synchronizes.
+ */
+int sedef_filter_autotune(sedef_ctx* ctx, const uint64_t* d_qrec, int64_t nq,
+                          const int64_t* h_qoff, int32_t nqseq, const uint64_t* d_trec,
+                          const uint64_t* d_tsorted, const uint32_t* d_toff, int64_t nt,
+                          const int64_t* h_toff, int32_t ntseq, const sedef_params* p,
+                          int32_t* variant_out);
+
+/* Sets the first-tier filter shape when set >= 0; returns the current one
+ * and the number of shapes (either pointer may be NULL). */
+int sedef_filter_variant(sedef_ctx* ctx, int32_t set, int32_t* current, int32_t* count);
+
+/*
  * a7 (chaining): for each kept run, the anchors are the pairs (p, t) of a
  * query-window minimizer and a target minimizer starting in [j_a, j_b+n-k]
  * with equal hash and strands differing by o (self mode: t outside the query

@@ -40,7 +40,8 @@ class Params(ctypes.Structure):
 EXPORTS = ["sedef_default_params", "sedef_last_error", "sedef_create", "sedef_destroy",
            "sedef_set_stream", "sedef_trace_enable", "sedef_trace_report", "sedef_launch_count", "sedef_filter_stats",
            "sedef_threshold_table", "sedef_pack", "sedef_sketch", "sedef_sketch_noalloc",
-           "sedef_index", "sedef_filter", "sedef_chain", "sedef_merge", "sedef_selfsearch_host"]
+           "sedef_index", "sedef_filter", "sedef_filter_autotune", "sedef_filter_variant",
+           "sedef_chain", "sedef_merge", "sedef_selfsearch_host"]
 
 _lib = None
 
@@ -74,6 +75,9 @@ def load(build_if_missing: bool = True):
     lib.sedef_index.argtypes = [vp, vp, i64, P, vp, vp]
     lib.sedef_filter.argtypes = [vp, vp, i64, vp, i32, vp, vp, vp, i64, vp, i32, P, vp, i64,
                                  ctypes.POINTER(i64)]
+    lib.sedef_filter_autotune.argtypes = [vp, vp, i64, vp, i32, vp, vp, vp, i64, vp, i32, P,
+                                          ctypes.POINTER(i32)]
+    lib.sedef_filter_variant.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.sedef_chain.argtypes = [vp, vp, i64, vp, i64, vp, i32, vp, vp, i64, vp, i32, P, vp, i64,
                                 ctypes.POINTER(i64)]
     lib.sedef_merge.argtypes = [vp, vp, i64, vp, i32, vp, i32, P, vp, i64, ctypes.POINTER(i64)]
@@ -249,6 +253,20 @@ class Context:
             return runs[:count.value * RUN_DTYPE.itemsize], count.value
         raise SedefError(SEDEF_ERR_CAPACITY, "filter capacity")
 
+    def sedef_filter_autotune(self, qrec, qoff, trec, tsorted, toff_tab, toff, p: Params) -> int:
+        qo, to = _offsets(qoff), _offsets(toff)
+        v = ctypes.c_int32()
+        _check(self.lib.sedef_filter_autotune(self.handle, _ptr(qrec), qrec.numel(), qo.ctypes.data,
+                                              len(qo) - 1, _ptr(trec), _ptr(tsorted), _ptr(toff_tab),
+                                              trec.numel(), to.ctypes.data, len(to) - 1,
+                                              ctypes.byref(p), ctypes.byref(v)))
+        return v.value
+
+    def sedef_filter_variant(self, set_to: int = -1) -> tuple:
+        cur, cnt = ctypes.c_int32(), ctypes.c_int32()
+        _check(self.lib.sedef_filter_variant(self.handle, set_to, ctypes.byref(cur), ctypes.byref(cnt)))
+        return cur.value, cnt.value
+
     def sedef_chain(self, runs, nruns, qrec, qoff, tsorted, toff_tab, toff, p: Params):
         qo, to = _offsets(qoff), _offsets(toff)
         cap = max(int(nruns), 1)
@@ -289,11 +307,14 @@ class Context:
 
     # -- whole path -------------------------------------------------------------
 
-    def selfsearch(self, d_seq, offsets, p: Params):
-        """All stages on a device-resident sequence; returns every output."""
+    def selfsearch(self, d_seq, offsets, p: Params, autotune: bool = False):
+        """All stages on a device-resident sequence; returns every output.
+        With autotune, the filter's first-tier shape is chosen first."""
         packed, mask, nbits = self.sedef_pack(d_seq)
         rec = self.sedef_sketch(packed, mask, nbits, offsets, p)
         srt, off = self.sedef_index(rec, p)
+        if autotune:
+            self.sedef_filter_autotune(rec, offsets, rec, srt, off, offsets, p)
         runs, nruns = self.sedef_filter(rec, offsets, rec, srt, off, offsets, p)
         chains, nch = self.sedef_chain(runs, nruns, rec, offsets, srt, off, offsets, p)
         cands, nc = self.sedef_merge(chains, nch, offsets, offsets, p)

@@ -26,6 +26,7 @@ struct sedef_ctx {
   std::vector<Mark> marks;
   std::vector<cudaEvent_t> spare;  // recycled events
   int64_t filter_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int filter_variant = 0;  // first-tier filter shape (sedef_filter_autotune)
 };
 
 namespace sedef {
@@ -106,6 +107,9 @@ TraceScope::~TraceScope() {
 }
 
 cudaStream_t ctx_stream(sedef_ctx* ctx) { return ctx->stream; }
+
+int ctx_filter_variant(sedef_ctx* ctx) { return ctx->filter_variant; }
+void ctx_set_filter_variant(sedef_ctx* ctx, int v) { ctx->filter_variant = v; }
 
 void ctx_set_stats(sedef_ctx* ctx, const int64_t* v, int n) {
   for (int x = 0; x < 8; ++x) ctx->filter_stats[x] = x < n ? v[x] : 0;
@@ -385,7 +389,42 @@ int sedef_filter(sedef_ctx* ctx, const uint64_t* d_qrec, int64_t nq, const int64
   mtable(p, mt.data(), kMaxWindowRecs, nullptr);
   *h_nruns = 0;
   return run_filter(ctx, d_qrec, nq, h_qoff, nqseq, d_trec, d_tsorted, d_toff, nt, h_toff, ntseq,
-                    D, mt.data(), d_runs, run_cap, h_nruns);
+                    D, mt.data(), d_runs, run_cap, h_nruns, 0);
+}
+
+int sedef_filter_autotune(sedef_ctx* ctx, const uint64_t* d_qrec, int64_t nq, const int64_t* h_qoff,
+                          int32_t nqseq, const uint64_t* d_trec, const uint64_t* d_tsorted,
+                          const uint32_t* d_toff, int64_t nt, const int64_t* h_toff,
+                          int32_t ntseq, const sedef_params* p, int32_t* variant_out) {
+  if (!ctx) return fail(SEDEF_ERR_INVALID, "ctx is NULL");
+  Derived D;
+  SEDEF_TRY(derive(p, &D));
+  SEDEF_TRY(check_offsets(h_qoff, nqseq, "query"));
+  SEDEF_TRY(check_offsets(h_toff, ntseq, "target"));
+  if (nq < 0 || nt < 0 || (nq > 0 && !d_qrec) || (nt > 0 && (!d_trec || !d_tsorted)) || !d_toff)
+    return fail(SEDEF_ERR_INVALID, "bad record arrays");
+  SEDEF_CUDA(cudaSetDevice(ctx->device));
+  ctx->pool.reset();
+  std::vector<int32_t> mt(kMaxWindowRecs + 1);
+  mtable(p, mt.data(), kMaxWindowRecs, nullptr);
+  int64_t chosen = 0;
+  // runs from the timing passes are discarded (capacity 1)
+  sedef_run_t* scratch = (sedef_run_t*)ctx_alloc(ctx, sizeof(sedef_run_t));
+  if (!scratch) return SEDEF_ERR_OOM;
+  SEDEF_TRY(run_filter(ctx, d_qrec, nq, h_qoff, nqseq, d_trec, d_tsorted, d_toff, nt, h_toff, ntseq,
+                       D, mt.data(), scratch, 1, &chosen, 1));
+  SEDEF_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (variant_out) *variant_out = (int32_t)ctx->filter_variant;
+  return SEDEF_OK;
+}
+
+int sedef_filter_variant(sedef_ctx* ctx, int32_t set, int32_t* current, int32_t* count) {
+  if (!ctx) return fail(SEDEF_ERR_INVALID, "ctx is NULL");
+  if (set >= filter_variant_count()) return fail(SEDEF_ERR_INVALID, "no such variant");
+  if (set >= 0) ctx->filter_variant = set;
+  if (current) *current = ctx->filter_variant;
+  if (count) *count = filter_variant_count();
+  return SEDEF_OK;
 }
 
 int sedef_chain(sedef_ctx* ctx, const sedef_run_t* d_runs, int64_t nruns, const uint64_t* d_qrec,

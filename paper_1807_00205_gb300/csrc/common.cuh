@@ -170,7 +170,8 @@ int build_offsets(sedef_ctx* ctx, const uint64_t* sorted, int64_t n, int k, uint
 int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* h_qoff, int nqseq,
                const uint64_t* trec, const uint64_t* tsorted, const uint32_t* toff, int64_t nt,
                const int64_t* h_toff, int ntseq, const Derived& D, const int32_t* h_mtab,
-               sedef_run_t* runs, int64_t cap, int64_t* nruns);
+               sedef_run_t* runs, int64_t cap, int64_t* nruns, int tune);
+int filter_variant_count();
 int run_chain(sedef_ctx* ctx, const sedef_run_t* runs, int64_t nruns, const uint64_t* qrec, int64_t nq,
               const int64_t* h_qoff, int nqseq, const uint64_t* tsorted, int64_t nt,
               const uint32_t* toff, const int64_t* h_toff, int ntseq, const Derived& D,
@@ -193,4 +194,6 @@ void* ctx_host(sedef_ctx* ctx, size_t bytes);  // pinned host scratch
 int ctx_device(sedef_ctx* ctx);
 int ctx_sm_count(sedef_ctx* ctx);
 void ctx_set_stats(sedef_ctx* ctx, const int64_t* v, int n);  // last sedef_filter call
+int ctx_filter_variant(sedef_ctx* ctx);
+void ctx_set_filter_variant(sedef_ctx* ctx, int v);
 }  // namespace sedef

@@ -30,13 +30,10 @@ namespace sedef {
 
 namespace {
 
-constexpr int kFThreads = 128;
 constexpr int kQCap = 256;        // query records per window (fast path)
 constexpr int kBinShift = 10;     // 1024-base bins (>= n - k + 1)
 constexpr int kSlots = 2048;      // (bin, o) counters (16-bit)
-constexpr int kLCap = 2048;       // collected hits (fast path)
 constexpr int kHMax = 65535;      // hits per window (fast path; 16-bit counters)
-constexpr int kGCap = 512;        // dense groups per window (fast path)
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 
 struct FArgs {
@@ -353,7 +350,8 @@ __device__ int build_wq(const FArgs& a, QBuild q, int c, int64_t seq_lo = 0, int
 
 // ------------------------------------------------------------- fast path --
 
-struct FastSmem {
+template <int TPB, int LCAP, int GCAP>
+struct FastSmemT {
   uint32_t qkey[kQCap];
   uint32_t dh[kQCap];
   uint32_t pst[kQCap];
@@ -361,13 +359,24 @@ struct FastSmem {
   uint32_t pre[kQCap + 1];
   uint8_t dm[kQCap];
   uint32_t slots[kSlots / 2];  // two 16-bit counters per word
-  unsigned long long hits[kLCap];
-  uint32_t glo[kGCap];     // dense groups: Jlo (clamped to >= 0), Jhi
-  uint32_t ghi[kGCap];
-  uint16_t cnt[kFThreads / 32][kQCap];  // one counter array per warp
+  unsigned long long hits[LCAP];
+  uint32_t glo[GCAP];     // dense groups: Jlo (clamped to >= 0), Jhi
+  uint32_t ghi[GCAP];
+  uint16_t cnt[TPB / 32][kQCap];  // one counter array per warp
   int tmp[33];
   int64_t win;
   int nhit, s, ovf, ng0, ng;
+};
+
+// Where a tier of the shared-memory path takes its windows from (all
+// windows, or a list) and where it sends the windows it cannot hold.
+struct TierIO {
+  const uint32_t* in_list;        // nullptr: windows 0..nwin-1
+  const unsigned int* in_count;
+  uint32_t* out_list;
+  unsigned int* out_count;
+  unsigned int* next;             // work counter of this tier
+  int stats;                      // count hits in the filter statistics
 };
 
 __device__ __forceinline__ uint32_t slot_of(uint32_t t, uint32_t o) {
@@ -380,8 +389,8 @@ __device__ __forceinline__ uint32_t slot_count(const uint32_t* slots, uint32_t s
 
 // Enumerates the window's hits: calls f(t, hid, o) for every posting of every
 // kept hash with a compatible relative strand (self positions skipped).
-template <typename F>
-__device__ __forceinline__ void for_hits(const FArgs& a, const FastSmem& S, int64_t i, int H, F f) {
+template <typename Smem, typename F>
+__device__ __forceinline__ void for_hits(const FArgs& a, const Smem& S, int64_t i, int H, F f) {
   for (int e = threadIdx.x; e < H; e += blockDim.x) {
     int lo = 0, hi = S.s;  // list with pre[l] <= e < pre[l+1]
     while (hi - lo > 1) {
@@ -397,22 +406,31 @@ __device__ __forceinline__ void for_hits(const FArgs& a, const FastSmem& S, int6
   }
 }
 
-__global__ void __launch_bounds__(kFThreads) k_filter_fast(FArgs a) {
+template <int TPB, int LCAP, int GCAP>
+__global__ void __launch_bounds__(TPB) k_filter_fast(FArgs a, TierIO io) {
+  using FastSmem = FastSmemT<TPB, LCAP, GCAP>;
+  constexpr int kFThreads = TPB;
+  constexpr int kLCap = LCAP;
+  constexpr int kGCap = GCAP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FastSmem& S = *reinterpret_cast<FastSmem*>(smem_raw);
   for (int x = threadIdx.x; x < kQCap * (kFThreads / 32); x += blockDim.x) (&S.cnt[0][0])[x] = 0;
+  const int64_t count = io.in_list ? (int64_t)*io.in_count : a.nwin;
   while (true) {
     __syncthreads();
-    if (threadIdx.x == 0) S.win = atomicAdd(a.next_window, 1u);
+    if (threadIdx.x == 0) {
+      const int64_t k = atomicAdd(io.next, 1u);
+      S.win = k < count ? (io.in_list ? (int64_t)io.in_list[k] : k) : -1;
+    }
     __syncthreads();
     const int64_t wdx = S.win;
-    if (wdx >= a.nwin) break;
+    if (wdx < 0) break;
     const int64_t i = a.win_i[wdx];
     const uint32_t qa = a.win_qa[wdx], qb = a.win_qb[wdx];
     const int c = (int)(qb - qa);
     if (c == 0) continue;
     if (c > kQCap) {
-      if (threadIdx.x == 0) a.ov_list[atomicAdd(a.nov, 1u)] = (uint32_t)wdx;
+      if (threadIdx.x == 0) io.out_list[atomicAdd(io.out_count, 1u)] = (uint32_t)wdx;
       continue;
     }
     for (int x = threadIdx.x; x < c; x += blockDim.x) {
@@ -457,11 +475,11 @@ __global__ void __launch_bounds__(kFThreads) k_filter_fast(FArgs a) {
     const uint32_t H = S.pre[s];
     if (H == 0) continue;
     if (H > (uint32_t)kHMax) {
-      if (threadIdx.x == 0) a.ov_list[atomicAdd(a.nov, 1u)] = (uint32_t)wdx;
+      if (threadIdx.x == 0) io.out_list[atomicAdd(io.out_count, 1u)] = (uint32_t)wdx;
       continue;
     }
     const int m = a.mtab[s];
-    if (threadIdx.x == 0) atomicAdd(a.stats + 0, (unsigned long long)H);
+    if (io.stats && threadIdx.x == 0) atomicAdd(a.stats + 0, (unsigned long long)H);
     // pass 1: (bin, o) counts
     for_hits(a, S, i, (int)H, [&](uint32_t t, uint32_t, uint32_t o) {
       const uint32_t sl = slot_of(t, o);
@@ -486,9 +504,9 @@ __global__ void __launch_bounds__(kFThreads) k_filter_fast(FArgs a) {
     });
     __syncthreads();
     const int L = S.nhit;
-    if (threadIdx.x == 0) atomicAdd(a.stats + 1, (unsigned long long)L);
+    if (io.stats && threadIdx.x == 0) atomicAdd(a.stats + 1, (unsigned long long)L);
     if (L > kLCap) {
-      if (threadIdx.x == 0) a.ov_list[atomicAdd(a.nov, 1u)] = (uint32_t)wdx;
+      if (threadIdx.x == 0) io.out_list[atomicAdd(io.out_count, 1u)] = (uint32_t)wdx;
       continue;
     }
     if (L < m) continue;
@@ -531,7 +549,7 @@ __global__ void __launch_bounds__(kFThreads) k_filter_fast(FArgs a) {
     __syncthreads();
     const int ng = S.ng, ng0 = S.ng0;
     if (ng > kGCap) {
-      if (threadIdx.x == 0) a.ov_list[atomicAdd(a.nov, 1u)] = (uint32_t)wdx;
+      if (threadIdx.x == 0) io.out_list[atomicAdd(io.out_count, 1u)] = (uint32_t)wdx;
       continue;
     }
     {
@@ -1648,7 +1666,46 @@ __global__ void k_run_ranges(const sedef_run_t* runs, int64_t n, const int64_t* 
   ranges[x] = make_uint4(win_qa[w], win_qb[w], (uint32_t)lo, (uint32_t)b);
 }
 
+// ------------------------------------------------------- tier launchers --
+
+template <int TPB, int LCAP, int GCAP>
+int launch_fast(sedef_ctx* ctx, const FArgs& a, const TierIO& io, int64_t max_windows,
+                const char* name) {
+  const size_t sm = sizeof(FastSmemT<TPB, LCAP, GCAP>);
+  static bool attr = false;  // one per instantiation
+  if (!attr) {
+    SEDEF_CUDA(cudaFuncSetAttribute(k_filter_fast<TPB, LCAP, GCAP>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    attr = true;
+  }
+  int per_sm = 0;
+  SEDEF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_fast<TPB, LCAP, GCAP>,
+                                                           TPB, sm));
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)ctx_sm_count(ctx) * per_sm;
+  if (grid > max_windows) grid = max_windows;
+  if (grid < 1) grid = 1;
+  SEDEF_KERNEL(ctx, name,
+               k_filter_fast<TPB, LCAP, GCAP><<<(int)grid, TPB, sm, ctx_stream(ctx)>>>(a, io));
+  return SEDEF_OK;
+}
+
+using FastLaunch = int (*)(sedef_ctx*, const FArgs&, const TierIO&, int64_t, const char*);
+
+// First-tier shapes the autotuner chooses from: threads per window, hits and
+// dense groups the window may hold in shared memory.
+const FastLaunch kTier1[] = {launch_fast<128, 2048, 512>, launch_fast<64, 1024, 256>,
+                             launch_fast<256, 2048, 512>, launch_fast<128, 1024, 256>};
+constexpr int kNumTier1 = 4;
+// Second-tier shapes (windows the first tier could not hold).
+const FastLaunch kTier2[] = {launch_fast<256, 8192, 2048>, launch_fast<256, 4096, 1024>,
+                             launch_fast<512, 8192, 2048>};
+constexpr int kNumTier2 = 3;
+constexpr int kNumVariants = kNumTier1 * kNumTier2;  // variant = t1 * kNumTier2 + t2
+
 }  // namespace
+
+int filter_variant_count() { return kNumVariants; }
 
 int scan_exclusive_u32(sedef_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n,
                        uint32_t* d_total);
@@ -1656,7 +1713,7 @@ int scan_exclusive_u32(sedef_ctx* ctx, const uint32_t* in, uint32_t* out, int64_
 int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* h_qoff, int nqseq,
                const uint64_t* trec, const uint64_t* tsorted, const uint32_t* toff, int64_t nt,
                const int64_t* h_toff, int ntseq, const Derived& D, const int32_t* h_mtab,
-               sedef_run_t* runs, int64_t cap, int64_t* nruns) {
+               sedef_run_t* runs, int64_t cap, int64_t* nruns, int tune) {
   cudaStream_t st = ctx_stream(ctx);
   // windows per query sequence
   std::vector<int64_t> wbase(nqseq + 1, 0);
@@ -1694,10 +1751,14 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   uint32_t* wqb = (uint32_t*)ctx_alloc(ctx, (size_t)nwin * 4);
   int32_t* wseq = (int32_t*)ctx_alloc(ctx, (size_t)nwin * 4);
   uint32_t* ovl = (uint32_t*)ctx_alloc(ctx, (size_t)nwin * 4);
-  unsigned long long* counters = (unsigned long long*)ctx_alloc(ctx, 64);
+  uint32_t* ovl1 = (uint32_t*)ctx_alloc(ctx, (size_t)nwin * 4);
+  // [0] runs, [1] windows for the global path, [2] tier-1 work, [3] large
+  // refine runs, [4] hits, [5] collected hits, [6]/[7] task and refine work,
+  // [8] tier-2 work, [9] windows tier 1 handed to tier 2, [10] sample size
+  unsigned long long* counters = (unsigned long long*)ctx_alloc(ctx, 128);
   sedef_run_t* raw = (sedef_run_t*)ctx_alloc(ctx, (size_t)(cap > 0 ? cap : 1) * sizeof(sedef_run_t));
-  if (!wi || !wqa || !wqb || !wseq || !ovl || !counters || !raw) return SEDEF_ERR_OOM;
-  SEDEF_CUDA(cudaMemsetAsync(counters, 0, 64, st));
+  if (!wi || !wqa || !wqb || !wseq || !ovl || !ovl1 || !counters || !raw) return SEDEF_ERR_OOM;
+  SEDEF_CUDA(cudaMemsetAsync(counters, 0, 128, st));
 
   FArgs a;
   a.qrec = qrec;
@@ -1734,10 +1795,7 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
                    qrec, nq, a.qseq, nqseq, (const int64_t*)(d_up + ow), nwin, D.step, D.span, wi,
                    wqa, wqb, wseq));
   static bool attr = false;
-  const size_t fsm = sizeof(FastSmem);
   if (!attr) {
-    SEDEF_CUDA(cudaFuncSetAttribute(k_filter_fast, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)fsm));
     SEDEF_CUDA(cudaFuncSetAttribute(k_refine_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)(sizeof(BatchWarp) * kBWarps)));
     SEDEF_CUDA(cudaFuncSetAttribute(k_refine<kMaxWindowRecs, 1024, false>,
@@ -1745,12 +1803,58 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
                                     (int)(sizeof(RefineWarpT<kMaxWindowRecs, 1024>) * kRWarpsBig)));
     attr = true;
   }
-  int per_sm = 0;
-  SEDEF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_fast, kFThreads, fsm));
-  if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)ctx_sm_count(ctx) * per_sm;
-  if (grid > nwin) grid = nwin;
-  SEDEF_KERNEL(ctx, "k_filter_fast", k_filter_fast<<<(int)grid, kFThreads, fsm, st>>>(a));
+  if (tune) {
+    // time every first-tier shape on a uniform sample of windows; keep the fastest
+    const int64_t stride = nwin > 8192 ? nwin / 8192 : 1;
+    std::vector<uint32_t> sample;
+    for (int64_t w = 0; w < nwin; w += stride) sample.push_back((uint32_t)w);
+    const unsigned int ns = (unsigned int)sample.size();
+    uint32_t* d_sample = (uint32_t*)ctx_alloc(ctx, (size_t)ns * 4 + 8);
+    if (!d_sample) return SEDEF_ERR_OOM;
+    SEDEF_CUDA(cudaMemcpyAsync(d_sample, sample.data(), (size_t)ns * 4, cudaMemcpyHostToDevice, st));
+    SEDEF_CUDA(cudaMemcpyAsync(counters + 10, &ns, 4, cudaMemcpyHostToDevice, st));
+    cudaEvent_t e0, e1;
+    SEDEF_CUDA(cudaEventCreate(&e0));
+    SEDEF_CUDA(cudaEventCreate(&e1));
+    int best_v = 0;
+    float best_ms = 1e30f;
+    for (int v = 0; v < kNumVariants; ++v) {
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {  // the first repetition warms up
+        SEDEF_CUDA(cudaMemsetAsync(counters, 0, 80, st));
+        TierIO io{d_sample, (const unsigned int*)(counters + 10), ovl1,
+                  (unsigned int*)(counters + 9), (unsigned int*)(counters + 2), 0};
+        TierIO io2{ovl1, (const unsigned int*)(counters + 9), ovl, (unsigned int*)(counters + 1),
+                   (unsigned int*)(counters + 8), 0};
+        SEDEF_CUDA(cudaEventRecord(e0, st));
+        SEDEF_TRY(kTier1[v / kNumTier2](ctx, a, io, ns, "k_filter_tune"));
+        SEDEF_TRY(kTier2[v % kNumTier2](ctx, a, io2, ns, "k_filter_tune"));
+        SEDEF_CUDA(cudaEventRecord(e1, st));
+        SEDEF_CUDA(cudaEventSynchronize(e1));
+        SEDEF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_v = v;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx_set_filter_variant(ctx, best_v);
+    *nruns = best_v;
+    return SEDEF_OK;
+  }
+  {
+    // tier 1 (autotuned shape) over all windows, tier 2 (8,192 hits in
+    // shared memory) over what tier 1 could not hold, the global path after
+    int v = ctx_filter_variant(ctx);
+    if (v < 0 || v >= kNumVariants) v = 0;
+    TierIO io1{nullptr, nullptr, ovl1, (unsigned int*)(counters + 9), (unsigned int*)(counters + 2), 1};
+    SEDEF_TRY(kTier1[v / kNumTier2](ctx, a, io1, nwin, "k_filter_fast"));
+    TierIO io2{ovl1, (const unsigned int*)(counters + 9), ovl, (unsigned int*)(counters + 1),
+               (unsigned int*)(counters + 8), 0};
+    SEDEF_TRY(kTier2[v % kNumTier2](ctx, a, io2, nwin, "k_filter_mid"));
+  }
 
   unsigned long long* h_cnt = (unsigned long long*)ctx_host(ctx, 64);
   if (!h_cnt) return SEDEF_ERR_OOM;

@@ -269,3 +269,28 @@ def test_selfsearch_host_matches_stages(ctx):
     ref = oracle.selfsearch(g.seq, g.offsets, pd)
     cands = ctx.sedef_selfsearch_host(g.seq, g.offsets, binding.params_from_dict(pd))
     assert_rows_equal(cand_rows_global(cands, g.offsets), ref["cands"], "candidates")
+
+
+def test_every_filter_shape_gives_the_same_runs(ctx):
+    """The first-tier shapes the autotuner picks from (and the tiers windows
+    overflow into) must not change any result."""
+    g = synth.small_case(61, lengths=(150_000, 40_000), n_sd=8, sd_lo=1500, sd_hi=9000,
+                         id_lo=0.85, mask_frac=0.25, n_gaps=True, inter_frac=0.4)
+    rng = np.random.default_rng(61)
+    unit = synth.random_bases(rng, 600)
+    g.seq[20_000:20_000 + 600 * 12] = np.tile(unit, 12)  # a 12-copy tandem array: large windows
+    pd = oracle.params()
+    recs = oracle.sketch(g.seq, g.offsets, pd)
+    want = oracle.filter_runs(recs, g.offsets, recs, g.offsets, pd)
+    p = binding.params_from_dict(pd)
+    rec = ctx.sedef_sketch(*ctx.sedef_pack(to_dev(g.seq)), g.offsets, p)
+    srt, off = ctx.sedef_index(rec, p)
+    _, count = ctx.sedef_filter_variant()
+    assert count >= 2
+    for v in range(count):
+        ctx.sedef_filter_variant(v)
+        runs, _ = ctx.sedef_filter(rec, g.offsets, rec, srt, off, g.offsets, p)
+        assert_rows_equal(run_rows(runs), want, f"runs (shape {v})")
+    chosen = ctx.sedef_filter_autotune(rec, g.offsets, rec, srt, off, g.offsets, p)
+    assert 0 <= chosen < count and ctx.sedef_filter_variant()[0] == chosen
+    ctx.sedef_filter_variant(0)
