@@ -294,6 +294,26 @@ int sedef_filter_autotune(sedef_ctx* ctx, const uint64_t* d_qrec, int64_t nq,
 int sedef_filter_variant(sedef_ctx* ctx, int32_t set, int32_t* current, int32_t* count);
 
 /*
+ * Index persistence (checkpoint and restart of a serving process).  A blob
+ * holds the sequence offsets, the records by position (sedef_sketch), the
+ * records by hash (sedef_index), the 4^k + 1 offsets and a checksum.
+ * sedef_index_blob_size gives its size; sedef_index_save fills a host
+ * buffer of at least that size (synchronizes); sedef_index_blob_info checks
+ * the header, size and checksum and reports k, nrec and nseq;
+ * sedef_index_load copies the blob back to caller-allocated device arrays
+ * and host offsets (SEDEF_ERR_INVALID on a damaged or mismatched blob).
+ */
+int64_t sedef_index_blob_size(int32_t k, int64_t nrec, int32_t nseq);
+int sedef_index_save(sedef_ctx* ctx, const uint64_t* d_rec, const uint64_t* d_sorted,
+                     const uint32_t* d_off, int64_t nrec, int32_t k, const int64_t* h_seq_off,
+                     int32_t nseq, void* h_blob, int64_t cap);
+int sedef_index_blob_info(const void* h_blob, int64_t size, int32_t* k, int64_t* nrec,
+                          int32_t* nseq);
+int sedef_index_load(sedef_ctx* ctx, const void* h_blob, int64_t size, int64_t* h_seq_off,
+                     int32_t nseq_cap, uint64_t* d_rec, uint64_t* d_sorted, uint32_t* d_off,
+                     int64_t rec_cap);
+
+/*
  * a7 (chaining): for each kept run, the anchors are the pairs (p, t) of a
  * query-window minimizer and a target minimizer starting in [j_a, j_b+n-k]
  * with equal hash and strands differing by o (self mode: t outside the query

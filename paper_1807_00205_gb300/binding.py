@@ -41,7 +41,8 @@ EXPORTS = ["sedef_default_params", "sedef_last_error", "sedef_create", "sedef_de
            "sedef_set_stream", "sedef_trace_enable", "sedef_trace_report", "sedef_launch_count", "sedef_filter_stats",
            "sedef_threshold_table", "sedef_pack", "sedef_sketch", "sedef_sketch_noalloc",
            "sedef_index", "sedef_filter", "sedef_filter_autotune", "sedef_filter_variant",
-           "sedef_chain", "sedef_merge", "sedef_selfsearch_host"]
+           "sedef_chain", "sedef_merge", "sedef_selfsearch_host", "sedef_index_blob_size",
+           "sedef_index_save", "sedef_index_blob_info", "sedef_index_load"]
 
 _lib = None
 
@@ -78,6 +79,12 @@ def load(build_if_missing: bool = True):
     lib.sedef_filter_autotune.argtypes = [vp, vp, i64, vp, i32, vp, vp, vp, i64, vp, i32, P,
                                           ctypes.POINTER(i32)]
     lib.sedef_filter_variant.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.sedef_index_blob_size.restype = i64
+    lib.sedef_index_blob_size.argtypes = [i32, i64, i32]
+    lib.sedef_index_save.argtypes = [vp, vp, vp, vp, i64, i32, vp, i32, vp, i64]
+    lib.sedef_index_blob_info.argtypes = [vp, i64, ctypes.POINTER(i32), ctypes.POINTER(i64),
+                                          ctypes.POINTER(i32)]
+    lib.sedef_index_load.argtypes = [vp, vp, i64, vp, i32, vp, vp, vp, i64]
     lib.sedef_chain.argtypes = [vp, vp, i64, vp, i64, vp, i32, vp, vp, i64, vp, i32, P, vp, i64,
                                 ctypes.POINTER(i64)]
     lib.sedef_merge.argtypes = [vp, vp, i64, vp, i32, vp, i32, P, vp, i64, ctypes.POINTER(i64)]
@@ -88,7 +95,8 @@ def load(build_if_missing: bool = True):
     lib.sedef_launch_count.argtypes = []
     lib.sedef_filter_stats.argtypes = [vp, vp, i32]
     for name in EXPORTS:
-        if name not in ("sedef_default_params", "sedef_last_error", "sedef_launch_count"):
+        if name not in ("sedef_default_params", "sedef_last_error", "sedef_launch_count",
+                        "sedef_index_blob_size"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -266,6 +274,29 @@ class Context:
         cur, cnt = ctypes.c_int32(), ctypes.c_int32()
         _check(self.lib.sedef_filter_variant(self.handle, set_to, ctypes.byref(cur), ctypes.byref(cnt)))
         return cur.value, cnt.value
+
+    def sedef_index_save(self, rec, srt, off, k: int, offsets) -> bytes:
+        o = _offsets(offsets)
+        n = self.lib.sedef_index_blob_size(k, rec.numel(), len(o) - 1)
+        blob = np.zeros(n, dtype=np.uint8)
+        _check(self.lib.sedef_index_save(self.handle, _ptr(rec), _ptr(srt), _ptr(off), rec.numel(),
+                                         k, o.ctypes.data, len(o) - 1, blob.ctypes.data, n))
+        return blob.tobytes()
+
+    def sedef_index_load(self, blob: bytes):
+        """(records by position, records by hash, offsets, sequence offsets, k)."""
+        b = np.frombuffer(blob, dtype=np.uint8)
+        k, nrec, nseq = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+        _check(self.lib.sedef_index_blob_info(b.ctypes.data, len(b), ctypes.byref(k),
+                                              ctypes.byref(nrec), ctypes.byref(nseq)))
+        t = self.torch
+        rec = self._empty(nrec.value, t.int64)
+        srt = self._empty(nrec.value, t.int64)
+        off = self._empty((1 << (2 * k.value)) + 1, t.int32)
+        so = np.zeros(nseq.value + 1, dtype=np.int64)
+        _check(self.lib.sedef_index_load(self.handle, b.ctypes.data, len(b), so.ctypes.data,
+                                         nseq.value, _ptr(rec), _ptr(srt), _ptr(off), nrec.value))
+        return rec[:nrec.value], srt[:nrec.value], off, so, k.value
 
     def sedef_chain(self, runs, nruns, qrec, qoff, tsorted, toff_tab, toff, p: Params):
         qo, to = _offsets(qoff), _offsets(toff)

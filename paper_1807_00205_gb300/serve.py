@@ -75,17 +75,29 @@ class Admission:
 
 
 class ResidentIndex:
-    """The target genome's records and index, kept on the device."""
+    """The target genome's records and index, kept on the device.  Built
+    from the sequence, or restored from a blob written by `save` (a serving
+    process restarts without re-indexing)."""
 
-    def __init__(self, ctx: "binding.Context", seq: np.ndarray, offsets, p: "binding.Params"):
+    def __init__(self, ctx: "binding.Context", seq: np.ndarray, offsets, p: "binding.Params",
+                 blob: bytes = None):
         import torch
-        self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
         self.p_index = binding.params_from_struct(p, self_mode=1)
-        d = torch.from_numpy(np.ascontiguousarray(seq)).to(ctx.device)
-        packed, mask, nbits = ctx.sedef_pack(d)
-        self.trec = ctx.sedef_sketch(packed, mask, nbits, self.offsets, self.p_index)
-        self.tsorted, self.toff = ctx.sedef_index(self.trec, self.p_index)
+        if blob is not None:
+            self.trec, self.tsorted, self.toff, self.offsets, k = ctx.sedef_index_load(blob)
+            if k != p.k:
+                raise ValueError(f"index blob has k={k}, parameters have k={p.k}")
+        else:
+            self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+            d = torch.from_numpy(np.ascontiguousarray(seq)).to(ctx.device)
+            packed, mask, nbits = ctx.sedef_pack(d)
+            self.trec = ctx.sedef_sketch(packed, mask, nbits, self.offsets, self.p_index)
+            self.tsorted, self.toff = ctx.sedef_index(self.trec, self.p_index)
         torch.cuda.synchronize(ctx.device)
+
+    def save(self, ctx: "binding.Context") -> bytes:
+        return ctx.sedef_index_save(self.trec, self.tsorted, self.toff, self.p_index.k,
+                                    self.offsets)
 
 
 def search(ctx: "binding.Context", index: ResidentIndex, reqs: list, p: "binding.Params"):

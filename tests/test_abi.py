@@ -45,3 +45,22 @@ def test_host_only_calls():
     bad = binding.params(k=16)
     assert lib.sedef_threshold_table(ctypes.byref(bad), m, 739, ctypes.byref(tau)) == -5
     assert b"k must be" in lib.sedef_last_error()
+
+
+def test_index_blob_checks_on_host():
+    """The blob size follows its stated layout, and a buffer that is not a
+    well-formed blob is refused without touching a device."""
+    import numpy as np
+    lib = binding.load()
+    assert lib.sedef_index_blob_size(12, 1000, 3) == 32 + 8 * 4 + 16 * 1000 + 4 * (4**12 + 1) + 8
+    assert lib.sedef_index_blob_size(16, 10, 1) == -1
+    k, n, s = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+    junk = np.zeros(4096, dtype=np.uint8)
+    assert lib.sedef_index_blob_info(junk.ctypes.data, len(junk), ctypes.byref(k),
+                                     ctypes.byref(n), ctypes.byref(s)) == -1
+    assert b"not an index blob" in lib.sedef_last_error()
+    head = np.frombuffer(b"SEDEFIDX" + bytes([1, 0, 0, 0, 12, 0, 0, 0]) + bytes(16), np.uint8)
+    junk[:32] = head
+    assert lib.sedef_index_blob_info(junk.ctypes.data, len(junk), ctypes.byref(k),
+                                     ctypes.byref(n), ctypes.byref(s)) == -1
+    assert b"size does not match" in lib.sedef_last_error()

@@ -35,3 +35,30 @@ def test_results_same_alone_and_in_the_mix():
         assert np.array_equal(got[k], alone[k % len(pool)]), k
     assert res["requests"] == 28
     ctx.close()
+
+
+def test_index_blob_round_trip():
+    """A resident index saved and restored gives the same arrays and the same
+    candidates; a damaged blob is refused."""
+    torch = need_gpu()
+    g = synth.small_case(77, lengths=(200_000, 50_000), n_sd=5, sd_lo=2000, sd_hi=6000,
+                         id_lo=0.9, mask_frac=0.2)
+    ctx = binding.Context(0)
+    p = binding.params()
+    a = serve.ResidentIndex(ctx, g.seq, g.offsets, p)
+    blob = a.save(ctx)
+    b = serve.ResidentIndex(ctx, None, None, p, blob=blob)
+    assert torch.equal(a.trec, b.trec) and torch.equal(a.tsorted, b.tsorted)
+    assert torch.equal(a.toff, b.toff) and np.array_equal(a.offsets, b.offsets)
+    pool = synth.query_regions(g, 4, seed=3, len_lo=3000, len_hi=20_000)
+    ra = [serve.Request(rid=k, seq=q) for k, q in enumerate(pool)]
+    rb = [serve.Request(rid=k, seq=q) for k, q in enumerate(pool)]
+    serve.search(ctx, a, ra, p)
+    serve.search(ctx, b, rb, p)
+    for x, y in zip(ra, rb):
+        assert np.array_equal(x.cands, y.cands)
+    bad = bytearray(blob)
+    bad[100] ^= 1
+    with pytest.raises(binding.SedefError):
+        serve.ResidentIndex(ctx, None, None, p, blob=bytes(bad))
+    ctx.close()
