@@ -68,6 +68,19 @@ def random_bases(rng: np.random.Generator, length: int, gc: float = 0.5) -> np.n
     return _ACGT[idx]
 
 
+def random_bases_chunked(rng: np.random.Generator, out: np.ndarray, gc: float = 0.5,
+                         chunk: int = 1 << 24) -> None:
+    """Fill ``out`` with i.i.d. uppercase bases, drawn in chunks so that
+    gigabase sequences need no 8-byte-per-base temporaries."""
+    c0, c1, c2 = (1.0 - gc) / 2.0, 0.5, 0.5 + gc / 2.0
+    for a in range(0, len(out), chunk):
+        u = rng.random(min(chunk, len(out) - a), dtype=np.float32)
+        idx = (u >= c0).astype(np.uint8)
+        idx += u >= c1
+        idx += u >= c2
+        out[a:a + len(u)] = _ACGT[idx]
+
+
 def reverse_complement(seq: np.ndarray) -> np.ndarray:
     """Case-preserving reverse complement (N stays N)."""
     return _COMP[seq[::-1]]
@@ -305,6 +318,34 @@ def batch_genomes(seed: int = 0x5EDEF003, count: int = 200, len_lo: int = 1_000_
         planted = plant_duplications(rng, seq, nsd, 1000, 50_000, 0.75, 0.99)
         out.append(genome_from_parts([seq], planted, f"batch-{g}"))
     return out
+
+
+def human_3gbp(seed: int = 0x5EDEF004, total: int = 3_100_000_000, nchrom: int = 24,
+               len_lo: int = 50_000_000, len_hi: int = 250_000_000, n_sd: int = 20_000,
+               sd_hi: int = 300_000, mask_frac: float = 0.50, inter_frac: float = 0.3) -> Genome:
+    """Human-assembly-scale input: ``nchrom`` chromosomes of len_lo..len_hi
+    bases summing to ``total``, 41% GC, soft-masked repeat families covering
+    about ``mask_frac`` of each chromosome, N-gaps of 10-50 kbp every ~10 Mbp
+    and ``n_sd`` duplications of 1 kbp-``sd_hi`` (log-uniform) at 75-99.5%
+    identity, both orientations, a fraction ``inter_frac`` of them placed on
+    another chromosome."""
+    rng = np.random.default_rng(seed)
+    share = rng.uniform(0.0, 1.0, size=nchrom)
+    lengths = len_lo + np.floor((total - nchrom * len_lo) * share / share.sum()).astype(np.int64)
+    lengths[-1] += total - lengths.sum()
+    assert lengths.min() >= len_lo and lengths.max() <= len_hi
+    offs = np.zeros(nchrom + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(lengths)
+    seq = np.empty(total, dtype=np.uint8)
+    for c in range(nchrom):
+        sub = seq[offs[c]:offs[c + 1]]
+        random_bases_chunked(rng, sub, 0.41)
+        add_masked_repeats(rng, sub, mask_frac)
+    planted = plant_duplications(rng, seq, n_sd, 1000, sd_hi, 0.75, 0.995, offsets=offs,
+                                 inter_frac=inter_frac)
+    for c in range(nchrom):
+        add_n_gaps(rng, seq[offs[c]:offs[c + 1]], 10_000_000, 10_000, 50_000)
+    return Genome(seq, offs, planted, f"human-{total / 1e9:.1f}Gbp")
 
 
 def small_case(seed: int, lengths=(20_000,), n_sd: int = 3, sd_lo: int = 1000,
