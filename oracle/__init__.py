@@ -46,7 +46,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC",
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread",
                            "-o", tmp, _SRC])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -72,7 +72,7 @@ def _load():
             lib.orc_tau.argtypes = [i64, ctypes.c_double, ctypes.c_double]
             lib.orc_mtable.argtypes = [i64, ctypes.c_double, ctypes.c_double, i64, vp]
             lib.orc_sketch.restype = vp
-            lib.orc_sketch.argtypes = [vp, vp, i32, vp]
+            lib.orc_sketch.argtypes = [vp, vp, i32, vp, i32]
             lib.orc_index.restype = vp
             lib.orc_index.argtypes = [vp, i64, i32, vp]
             lib.orc_filter.restype = vp
@@ -156,13 +156,14 @@ def mtable(k=12, delta_m=0.15, delta_g=0.10, smax=739) -> np.ndarray:
     return out
 
 
-def sketch(seq: np.ndarray, offsets: np.ndarray, p: dict) -> np.ndarray:
-    """a2: rows (hash, pos, strand), sorted by pos."""
+def sketch(seq: np.ndarray, offsets: np.ndarray, p: dict, threads: int = 1) -> np.ndarray:
+    """a2: rows (hash, pos, strand), sorted by pos.  `threads` > 1 shares the
+    (independent) sequences out to threads; the rows are the same."""
     lib = _load()
     seq = _c(seq, np.uint8)
     offsets = _c(offsets, np.int64)
     return _table(lib, lib.orc_sketch(_ptr(seq), _ptr(offsets), len(offsets) - 1,
-                                      _ptr(_par_array(p))))
+                                      _ptr(_par_array(p)), int(threads)))
 
 
 def index(recs: np.ndarray, k: int):

@@ -30,11 +30,13 @@
 // copy + free) so that the Python test harness can read them with ctypes.
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <map>
 #include <set>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -180,10 +182,14 @@ std::vector<Rec> rows_to_recs(const int64_t* rows, int64_t nrec) {
   return v;
 }
 
-// Target postings: hash -> positions with strands (the reverse index).
-std::map<uint64_t, std::vector<std::pair<int64_t, int>>> postings_of(const std::vector<Rec>& t) {
+// Target postings: hash -> positions with strands (the reverse index).  With
+// `only`, postings are kept for those hashes alone (a caller that looks up
+// no other hash gets the same answers with less memory).
+std::map<uint64_t, std::vector<std::pair<int64_t, int>>> postings_of(
+    const std::vector<Rec>& t, const std::set<uint64_t>* only = nullptr) {
   std::map<uint64_t, std::vector<std::pair<int64_t, int>>> m;
-  for (const Rec& r : t) m[r.h].push_back({r.pos, r.sigma});
+  for (const Rec& r : t)
+    if (!only || only->count(r.h)) m[r.h].push_back({r.pos, r.sigma});
   for (auto& kv : m) std::sort(kv.second.begin(), kv.second.end());
   return m;
 }
@@ -263,14 +269,40 @@ void orc_mtable(int64_t k, double dm, double dg, int64_t smax, int64_t* out) {
 
 // ---- a2 sketch: canonical k-mers + winnowing (Section 2.2, Section 3.2) -----
 // Output rows (hash, pos, strand) sorted by pos.
-void* orc_sketch(const uint8_t* seq, const int64_t* off, int nseq, const int64_t* par) {
+// Sequences are independent (windows never cross a boundary), so with
+// nthreads > 1 they are shared out to threads and their rows joined in
+// sequence order; the result does not depend on nthreads.
+static void sketch_one(const uint8_t* seq, int64_t st, int64_t en, const Par& P, Table* T);
+
+void* orc_sketch(const uint8_t* seq, const int64_t* off, int nseq, const int64_t* par,
+                 int nthreads) {
   Par P = read_par(par);
   Table* T = new Table();
   T->ncols = 3;
-  for (int s = 0; s < nseq; ++s) {
-    const int64_t st = off[s], en = off[s + 1];
+  if (nthreads < 1) nthreads = 1;
+  std::vector<Table> part(nseq);
+  std::atomic<int> next(0);
+  auto work = [&]() {
+    for (int s; (s = next.fetch_add(1)) < nseq;) {
+      part[s].ncols = 3;
+      sketch_one(seq, off[s], off[s + 1], P, &part[s]);
+    }
+  };
+  std::vector<std::thread> th;
+  for (int x = 1; x < nthreads; ++x) th.emplace_back(work);
+  work();
+  for (auto& t : th) t.join();
+  for (auto& p : part) {
+    T->v.insert(T->v.end(), p.v.begin(), p.v.end());
+    std::vector<int64_t>().swap(p.v);
+  }
+  return T;
+}
+
+static void sketch_one(const uint8_t* seq, int64_t st, int64_t en, const Par& P, Table* T) {
+  {
     const int64_t nk = en - st - P.k + 1;  // k-mer starts inside the sequence
-    if (nk <= 0) continue;
+    if (nk <= 0) return;
     std::vector<uint64_t> h(nk);
     std::vector<int> sig(nk);
     for (int64_t a = 0; a < nk; ++a) {
@@ -307,7 +339,6 @@ void* orc_sketch(const uint8_t* seq, const int64_t* off, int nseq, const int64_t
     }
     for (int64_t a : chosen) T->row({(int64_t)h[a], st + a, sig[a]});
   }
-  return T;
 }
 
 // ---- a3 index: I_G sorted by (hash, position) plus offsets (Section 3.1) ----
@@ -349,7 +380,6 @@ void* orc_filter(const int64_t* qrows, int64_t nq, const int64_t* qoff, int nqse
   Par P = read_par(par);
   std::vector<Rec> qrecs = rows_to_recs(qrows, nq);
   std::vector<Rec> trecs = rows_to_recs(trows, nt);
-  auto post = postings_of(trecs);
   auto qr = seq_ranges(qoff, nqseq);
   auto tr = seq_ranges(toff, ntseq);
   const double tau = tau_of(P.k, P.delta_m, P.delta_g);
@@ -362,6 +392,11 @@ void* orc_filter(const int64_t* qrows, int64_t nq, const int64_t* qoff, int nqse
     for (auto& r : qr)
       for (int64_t i = r.first; i + P.n <= r.second; i += P.step) starts.push_back(i);
   }
+  // postings of the hashes the windows hold (the only ones looked up)
+  std::set<uint64_t> needed;
+  for (int64_t i : starts)
+    for (auto& kv : window_hashes(qrecs, i, i + span)) needed.insert(kv.first);
+  auto post = postings_of(trecs, &needed);
 
   Table* T = new Table();
   T->ncols = 12;
@@ -516,7 +551,9 @@ void* orc_chain(const int64_t* runs, int64_t nruns, int64_t run_cols,
   Par P = read_par(par);
   std::vector<Rec> qrecs = rows_to_recs(qrows, nq);
   std::vector<Rec> trecs = rows_to_recs(trows, nt);
-  auto post = postings_of(trecs);
+  // postings are needed only for the optional occurrence cap
+  std::map<uint64_t, std::vector<std::pair<int64_t, int>>> post;
+  if (P.max_occ > 0) post = postings_of(trecs);
   auto qr = seq_ranges(qoff, nqseq);
   auto tr = seq_ranges(toff, ntseq);
   const double tau = tau_of(P.k, P.delta_m, P.delta_g);

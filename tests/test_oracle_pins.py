@@ -377,3 +377,26 @@ def test_oracle_matches_stored_digests():
     with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_small.json")) as f:
         want = json.load(f)
     assert make_golden.compute() == want
+
+
+def test_sketch_threads_do_not_change_rows():
+    """Sequences are sketched independently, so sharing them out to threads
+    gives the same rows in the same order."""
+    g = synth.small_case(41, lengths=(30_000, 5, 2000, 60_000, 900), mask_frac=0.3, n_gaps=True)
+    pd = oracle.params()
+    one = oracle.sketch(g.seq, g.offsets, pd)
+    for t in (2, 3, 8):
+        assert np.array_equal(oracle.sketch(g.seq, g.offsets, pd, threads=t), one)
+
+
+def test_filter_window_subset_equals_full_rows():
+    """Filtering a subset of windows gives exactly those windows' rows of the
+    full run (postings are built only for the hashes the subset holds)."""
+    g = synth.small_case(42, lengths=(40_000, 25_000), n_sd=4, mask_frac=0.1)
+    pd = oracle.params()
+    recs = oracle.sketch(g.seq, g.offsets, pd)
+    full = oracle.filter_runs(recs, g.offsets, recs, g.offsets, pd)
+    win = np.unique(full[:, 0])[::3]
+    sub = oracle.filter_runs(recs, g.offsets, recs, g.offsets, pd, windows=win)
+    assert len(sub) > 0
+    assert np.array_equal(sub, full[np.isin(full[:, 0], win)])
