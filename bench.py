@@ -35,6 +35,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "query Mbp/s through sketch+Jaccard filter+chain (batched/served vs plain), p99 latency, HBM %"
 WORKLOAD = "chromosome-100Mbp self-search (41% GC, 40% soft-masked repeats, N-gaps, 2000 planted SDs 1-200 kbp)"
+WORKLOADS = {
+    "chromosome": WORKLOAD,
+    "plain": "plain-2Mbp self-search (i.i.d. ACGT, 20 planted SDs 1-20 kbp)",
+    "human": "human-scale 3.1 Gbp self-search (24 chromosomes of 50-250 Mbp, 41% GC, 50% soft-masked "
+             "repeats, N-gaps, 20000 planted SDs 1-300 kbp intra- and inter-chromosomal)",
+}
+
+
+def make_genome(name: str):
+    from paper_1807_00205_gb300 import synth
+    return {"chromosome": synth.chromosome_100mbp, "plain": synth.plain_2mbp,
+            "human": synth.human_3gbp}[name]()
 CPU_SAMPLE_BASES = 10_000_000
 FALLBACK_HBM_GBS = 6800.0
 
@@ -131,17 +143,25 @@ def algorithmic_bytes(seq, offsets, rec_rows, sorted_rows, runs, k, n, step):
     # distinct query hash and every posting of those hashes once
     pos, hsh = rec_rows[:, 1], rec_rows[:, 0]
     occ = np.bincount(hsh, minlength=1 << (2 * k)).astype(np.int64)
-    w_lo = np.ceil((pos - span) / step).clip(min=0).astype(np.int64)
-    w_hi = (pos // step).astype(np.int64)
+    # windows start at each sequence start, then every `step`, and end
+    # inside the sequence; number them globally
+    off = np.asarray(offsets, dtype=np.int64)
+    nwin = np.maximum(0, (np.diff(off) - n) // step + 1)
+    wbase = np.concatenate([[0], np.cumsum(nwin)])
+    sq = np.searchsorted(off, pos, side="right") - 1
+    local = pos - off[sq]
+    w_lo = np.ceil((local - span) / step).clip(min=0).astype(np.int64)
+    w_hi = np.minimum(local // step, nwin[sq] - 1).astype(np.int64)
+    filt_q = 0
     pairs = []
     for d in range(0, span // step + 2):
         w = w_lo + d
         ok = w <= w_hi
-        pairs.append((w[ok] << 32) | hsh[ok])
+        filt_q += int(ok.sum())
+        pairs.append(((wbase[sq[ok]] + w[ok]) << 32) | hsh[ok])
     pairs = np.unique(np.concatenate(pairs))
     hashes = (pairs & 0xFFFFFFFF).astype(np.int64)
-    recs_per_window_total = sum(int(((w_lo + d) <= w_hi).sum()) for d in range(span // step + 2))
-    filt = 8 * recs_per_window_total + 8 * len(pairs) + 8 * int(occ[hashes].sum())
+    filt = 8 * filt_q + 8 * len(pairs) + 8 * int(occ[hashes].sum())
     # refine: per run the query records of its window and the target records
     # of its span
     ref = 0
@@ -187,16 +207,30 @@ def measured_traffic(kernel: str):
     return int(e["bytes_per_launch"])
 
 
-def run_cpu_oracle_sample(seq):
+def run_cpu_oracle_sample(seq, bases=CPU_SAMPLE_BASES, threads=1):
+    """The oracle self-searching a prefix of the workload: (Mbp/s, s, bases)."""
     import oracle
-    X = min(CPU_SAMPLE_BASES, len(seq))
+    X = min(bases, len(seq))
     s = np.ascontiguousarray(seq[:X])
     off = np.array([0, X], dtype=np.int64)
     oracle.build()
     t = time.perf_counter()
-    oracle.selfsearch(s, off, oracle.params())
+    oracle.selfsearch(s, off, oracle.params(), threads=threads)
     dt = time.perf_counter() - t
     return X / dt / 1e6, dt, X
+
+
+def cpu_baseline_line(seq) -> dict:
+    """The oracle on all host cores (threads over windows) on a 30 Mbp
+    prefix, and on one core on a 10 Mbp prefix."""
+    cores = os.cpu_count() or 1
+    v, dt, X = run_cpu_oracle_sample(seq, 3 * CPU_SAMPLE_BASES, threads=cores)
+    v1, dt1, X1 = run_cpu_oracle_sample(seq, CPU_SAMPLE_BASES, threads=1)
+    return {"value": v, "unit": "Mbp/s", "cores": cores, "kind": "oracle",
+            "sample": f"self-search of the first {X} bases of the workload ({dt:.1f} s wall, "
+                      f"threads over windows)",
+            "single_thread": {"value": v1, "unit": "Mbp/s", "cores": 1,
+                              "sample": f"first {X1} bases ({dt1:.1f} s)"}}
 
 
 def reference_arm(args):
@@ -207,15 +241,16 @@ def reference_arm(args):
     g = synth.chromosome_100mbp()
     import oracle
     oracle.build()
-    X = 2_000_000
+    X = 10_000_000
+    cores = os.cpu_count() or 1
     s = np.ascontiguousarray(g.seq[:X])
     off = np.array([0, X], dtype=np.int64)
     for _ in range(args.warmup):
-        oracle.selfsearch(s, off, oracle.params())
+        oracle.selfsearch(s, off, oracle.params(), threads=cores)
     times = []
     for _ in range(args.steps):
         t = time.perf_counter()
-        oracle.selfsearch(s, off, oracle.params())
+        oracle.selfsearch(s, off, oracle.params(), threads=cores)
         times.append(time.perf_counter() - t)
     ms = 1000 * sum(times) / len(times)
     value = X / (ms / 1000) / 1e6
@@ -226,8 +261,9 @@ def reference_arm(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": f"self-search of the first {X} bases",
                    "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": value, "unit": "Mbp/s", "cores": 1, "kind": "oracle",
-                         "sample": f"self-search of the first {X} bases of the workload"},
+        "cpu_baseline": {"value": value, "unit": "Mbp/s", "cores": cores, "kind": "oracle",
+                         "sample": f"self-search of the first {X} bases of the workload, "
+                                   f"threads over windows"},
         "e2e": {"value": value, "unit": "Mbp/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -311,14 +347,15 @@ def batch_arm(args):
 
 
 def serve_arm(args):
-    """Resident index of the 100 Mbp chromosome workload; Poisson streams of
-    query regions (10 kbp-5 Mbp, 0-25% mutation) at each rate, served by two
-    continuously batching workers and by the plain one-request-per-pass form."""
+    """Resident index of the 3.1 Gbp human-scale workload (or the 100 Mbp
+    chromosome); Poisson streams of query regions (10 kbp-5 Mbp, 0-25%
+    mutation) at each rate, served by two continuously batching workers and
+    by the plain one-request-per-pass form."""
     import torch
     from paper_1807_00205_gb300 import binding, serve, synth
     ws, rank, local = dist_info()
     torch.cuda.set_device(local)
-    g = synth.chromosome_100mbp()
+    g = make_genome(args.serve_genome)
     pool = synth.query_regions(g, 48)
     p = binding.params()
     ctx = binding.Context(local)
@@ -339,9 +376,9 @@ def serve_arm(args):
         "steps": args.requests, "warmup": 2, "ms_per_step": top["served"]["mean_ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": "serving: resident index of the 100 Mbp chromosome workload "
-                               "(stand-in for 3.1 Gbp); Poisson query regions 10 kbp-5 Mbp "
-                               "log-uniform cut from it with 0-25% mutation",
+        "config": {"workload": f"serving: resident index of the {WORKLOADS[args.serve_genome]}; "
+                               "Poisson query regions 10 kbp-5 Mbp log-uniform cut from it "
+                               "with 0-25% mutation",
                    "served": "2 workers (own streams), continuous batching, admission by free HBM",
                    "plain": "1 worker, one request per pass"},
         "rates": results,
@@ -356,7 +393,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="chromosome", choices=["chromosome", "plain", "batch", "serve"])
+    ap.add_argument("--workload", default="chromosome",
+                    choices=["chromosome", "plain", "human", "batch", "serve"])
+    ap.add_argument("--serve-genome", default="human", choices=["human", "chromosome"],
+                    help="serving: the genome whose index stays resident")
     ap.add_argument("--batch-count", type=int, default=200,
                     help="genomes in the batch workload")
     ap.add_argument("--rates", default="50,200,1000", help="serving: request rates per second")
@@ -384,7 +424,7 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    g = synth.chromosome_100mbp() if args.workload == "chromosome" else synth.plain_2mbp()
+    g = make_genome(args.workload)
     N = g.length
     p = binding.params()
     stream = torch.cuda.Stream(dev)
@@ -439,6 +479,34 @@ def main():
     ms = aggregate_max_ms(sum(step_ms) / len(step_ms), ws, dev)
     value = ws * N / (ms / 1000) / 1e6
 
+    # ---- the same step as one captured graph (sedef_graph_*): built once,
+    # outside the timing, then replayed
+    with torch.cuda.stream(stream):
+        graph = ctx.selfsearch_graph(d_seq, g.offsets, p)
+        for _ in range(args.warmup):
+            graph.launch(stream)
+            graph.wait()
+            flush.fill_(1)
+    barrier()
+    torch.cuda.synchronize()
+    g_ms = []
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.launch(stream)
+            e1.record(stream)
+            e1.synchronize()
+            graph.wait()
+            g_ms.append(e0.elapsed_time(e1))
+    graph_ms = aggregate_max_ms(sum(g_ms) / len(g_ms), ws, dev)
+    graph_info = {"value": ws * N / (graph_ms / 1000) / 1e6, "unit": "Mbp/s", "ms_per_step": graph_ms,
+                  "kernel_nodes": graph.nodes, "capacities": graph.caps,
+                  "same_candidates": bool(graph.need["cands"] == int(out["ncands"]))}
+    graph.close()
+
     # ---- end to end through the host-buffer entry point
     host_seq = torch.from_numpy(g.seq).pin_memory().numpy()
     e2e_times = []
@@ -492,15 +560,13 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        v, dt, X = run_cpu_oracle_sample(g.seq)
-        cpu = {"value": v, "unit": "Mbp/s", "cores": 1, "kind": "oracle",
-               "sample": f"self-search of the first {X} bases of the workload ({dt:.1f} s)"}
+        cpu = cpu_baseline_line(g.seq)
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mbp/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "genome_bases": N, "k": p.k, "w": p.w, "n": p.n,
+        "config": {"workload": WORKLOADS[args.workload], "genome_bases": N, "k": p.k, "w": p.w, "n": p.n,
                    "query_step": p.query_step, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 and a 256 MB L2 flush between steps",
                    "runs": int(out["nruns"]), "chains": int(out["nchains"]),
@@ -513,6 +579,7 @@ def main():
         "cpu_baseline": cpu,
         "gpu_launches": int(launches),
         "clocks": clk,
+        "graph": graph_info,
         "kernels": kernels,
     }
     print(json.dumps(line), flush=True)

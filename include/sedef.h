@@ -354,6 +354,49 @@ int sedef_selfsearch_host(sedef_ctx* ctx, const uint8_t* h_seq, const int64_t* h
                           int32_t nseq, const sedef_params* p, sedef_cand_t* h_cands, int64_t cap,
                           int64_t* h_ncands);
 
+/*
+ * Captured self-search pass (one CUDA graph).  The paper has no counterpart:
+ * this is the batched driver's launch form.  sedef_graph_create records
+ * pack, sketch, index, filter, refine, chain and merge for the device
+ * sequence d_seq (sequences at h_seq_off; self_mode from p: 1 for one
+ * genome, 2 for a batch of independent genomes) into a graph whose every
+ * data-dependent size is a capacity from `caps`: no stage synchronizes with
+ * the host, exact counts stay on the device, and work past a capacity is
+ * skipped and flagged.  Capacities below 1 are taken as 1; each must be
+ * below 2^32 (chains below 2^31).
+ *
+ * The graph reads d_seq and writes the caller's buffers at every launch:
+ * d_rec and d_sorted (caps->records entries each), d_off (4^k + 1),
+ * d_runs (caps->runs), d_chains (caps->chains), d_cands (caps->cands).
+ * They must stay allocated, and d_seq keep its layout, until
+ * sedef_graph_destroy.  Scratch memory and the pinned copies of uploads
+ * belong to the graph (a private context on `ctx`'s device, with the filter
+ * shape `ctx` was autotuned to).
+ *
+ * sedef_graph_launch enqueues one replay on `stream` (NULL: the graph's own
+ * stream).  sedef_graph_wait synchronizes that stream and fills
+ * h_need[0..5] with the exact totals (records, global-path hits, runs,
+ * anchors, chains, candidates); each output holds min(total, capacity)
+ * entries.  It returns SEDEF_ERR_CAPACITY when a total exceeded its
+ * capacity (outputs are then incomplete: create a graph with the reported
+ * totals as capacities) and SEDEF_ERR_UNSUPPORTED when a seed exceeded the
+ * 65,536-anchor limit.  sedef_graph_nodes gives the number of kernel nodes
+ * one launch runs.
+ */
+typedef struct sedef_graph sedef_graph;
+typedef struct sedef_graph_caps {
+  int64_t records, slow_hits, runs, anchors, chains, cands;
+} sedef_graph_caps;
+
+int sedef_graph_create(sedef_ctx* ctx, const uint8_t* d_seq, const int64_t* h_seq_off,
+                       int32_t nseq, const sedef_params* p, const sedef_graph_caps* caps,
+                       uint64_t* d_rec, uint64_t* d_sorted, uint32_t* d_off, sedef_run_t* d_runs,
+                       sedef_chain_t* d_chains, sedef_cand_t* d_cands, sedef_graph** out);
+int sedef_graph_launch(sedef_graph* g, void* stream);
+int sedef_graph_wait(sedef_graph* g, int64_t* h_need);
+int64_t sedef_graph_nodes(sedef_graph* g);
+int sedef_graph_destroy(sedef_graph* g);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,7 +76,7 @@ def _load():
             lib.orc_index.restype = vp
             lib.orc_index.argtypes = [vp, i64, i32, vp]
             lib.orc_filter.restype = vp
-            lib.orc_filter.argtypes = [vp, i64, vp, i32, vp, i64, vp, i32, vp, vp, i64, i32]
+            lib.orc_filter.argtypes = [vp, i64, vp, i32, vp, i64, vp, i32, vp, vp, i64, i32, i32]
             lib.orc_chain.restype = vp
             lib.orc_chain.argtypes = [vp, i64, i64, vp, i64, vp, i32, vp, i64, vp, i32, vp]
             lib.orc_chain_anchors.restype = vp
@@ -175,8 +175,10 @@ def index(recs: np.ndarray, k: int):
     return rows, off
 
 
-def filter_runs(qrecs, qoff, trecs, toff, p: dict, windows=None, dense=False) -> np.ndarray:
-    """a4-a6: run rows (see RUN_COLS), in (i, o, j_a) order."""
+def filter_runs(qrecs, qoff, trecs, toff, p: dict, windows=None, dense=False,
+                threads: int = 1) -> np.ndarray:
+    """a4-a6: run rows (see RUN_COLS), in (i, o, j_a) order.  `threads` > 1
+    shares the (independent) windows out to threads; the rows are the same."""
     lib = _load()
     qrecs, trecs = _c(qrecs, np.int64), _c(trecs, np.int64)
     qoff, toff = _c(qoff, np.int64), _c(toff, np.int64)
@@ -187,7 +189,7 @@ def filter_runs(qrecs, qoff, trecs, toff, p: dict, windows=None, dense=False) ->
         nwin = len(win)
     h = lib.orc_filter(_ptr(qrecs), len(qrecs), _ptr(qoff), len(qoff) - 1,
                        _ptr(trecs), len(trecs), _ptr(toff), len(toff) - 1,
-                       _ptr(_par_array(p)), _ptr(win), nwin, 1 if dense else 0)
+                       _ptr(_par_array(p)), _ptr(win), nwin, 1 if dense else 0, int(threads))
     return _table(lib, h)
 
 
@@ -225,11 +227,13 @@ def jaccard(seq: np.ndarray, i: int, j: int, n: int, k: int) -> float:
     return float(_load().orc_jaccard(_ptr(seq), i, j, n, k))
 
 
-def selfsearch(seq, offsets, p: dict):
-    """All steps for a self-search: returns dict of every intermediate."""
-    recs = sketch(seq, offsets, p)
+def selfsearch(seq, offsets, p: dict, threads: int = 1):
+    """All steps for a self-search: returns dict of every intermediate.
+    `threads` > 1 runs the sketch (per sequence) and the filter (per window)
+    on threads; the results are the same."""
+    recs = sketch(seq, offsets, p, threads=threads)
     idx_rows, off = index(recs, p["k"])
-    runs = filter_runs(recs, offsets, recs, offsets, p)
+    runs = filter_runs(recs, offsets, recs, offsets, p, threads=threads)
     chains = chain(runs, recs, offsets, recs, offsets, p)
     cands = merge(chains, p)
     return dict(recs=recs, index=idx_rows, offsets=off, runs=runs, chains=chains, cands=cands)

@@ -374,9 +374,13 @@ void* orc_index(const int64_t* rows, int64_t nrec, int k, uint32_t* off_out) {
 // `windows` (optional, nwin >= 0) restricts the query windows to that list of
 // starts; nwin < 0 means all windows.  dense != 0 evaluates the refine
 // estimate at every j of the run instead of at its breakpoints.
+// Windows are independent: with nthreads > 1 contiguous blocks of windows
+// go to threads and their rows are joined in window order (the result does
+// not depend on nthreads).
 void* orc_filter(const int64_t* qrows, int64_t nq, const int64_t* qoff, int nqseq,
                  const int64_t* trows, int64_t nt, const int64_t* toff, int ntseq,
-                 const int64_t* par, const int64_t* windows, int64_t nwin, int dense) {
+                 const int64_t* par, const int64_t* windows, int64_t nwin, int dense,
+                 int nthreads) {
   Par P = read_par(par);
   std::vector<Rec> qrecs = rows_to_recs(qrows, nq);
   std::vector<Rec> trecs = rows_to_recs(trows, nt);
@@ -398,9 +402,7 @@ void* orc_filter(const int64_t* qrows, int64_t nq, const int64_t* qoff, int nqse
     for (auto& kv : window_hashes(qrecs, i, i + span)) needed.insert(kv.first);
   auto post = postings_of(trecs, &needed);
 
-  Table* T = new Table();
-  T->ncols = 12;
-  for (int64_t i : starts) {
+  auto one = [&](int64_t i, Table* T) {
     const int qseq = seq_of(qr, i);
     std::map<uint64_t, int> wq = window_hashes(qrecs, i, i + span);
     if (P.max_occ > 0) {  // optional occurrence cap (off by default)
@@ -411,7 +413,7 @@ void* orc_filter(const int64_t* qrows, int64_t nq, const int64_t* qoff, int nqse
       }
     }
     const int64_t s = (int64_t)wq.size();
-    if (s == 0) continue;
+    if (s == 0) return;
     const int64_t m = min_shared(tau, s);
     auto valid = valid_targets(tr, qseq, i, P);
 
@@ -529,7 +531,23 @@ void* orc_filter(const int64_t* qrows, int64_t nq, const int64_t* qoff, int nqse
       }
       close_run();
     }
+  };
+  Table* T = new Table();
+  T->ncols = 12;
+  if (nthreads < 1) nthreads = 1;
+  const int64_t nw = (int64_t)starts.size();
+  std::vector<Table> part(nthreads);
+  std::vector<std::thread> th;
+  for (int x = 0; x < nthreads; ++x) {
+    part[x].ncols = 12;
+    auto work = [&, x]() {
+      const int64_t lo = nw * x / nthreads, hi = nw * (x + 1) / nthreads;
+      for (int64_t w = lo; w < hi; ++w) one(starts[w], &part[x]);
+    };
+    if (x + 1 < nthreads) th.emplace_back(work); else work();
   }
+  for (auto& t : th) t.join();
+  for (auto& pt : part) T->v.insert(T->v.end(), pt.v.begin(), pt.v.end());
   return T;
 }
 

@@ -42,7 +42,14 @@ EXPORTS = ["sedef_default_params", "sedef_last_error", "sedef_create", "sedef_de
            "sedef_threshold_table", "sedef_pack", "sedef_sketch", "sedef_sketch_noalloc",
            "sedef_index", "sedef_filter", "sedef_filter_autotune", "sedef_filter_variant",
            "sedef_chain", "sedef_merge", "sedef_selfsearch_host", "sedef_index_blob_size",
-           "sedef_index_save", "sedef_index_blob_info", "sedef_index_load"]
+           "sedef_index_save", "sedef_index_blob_info", "sedef_index_load", "sedef_graph_create",
+           "sedef_graph_launch", "sedef_graph_wait", "sedef_graph_nodes", "sedef_graph_destroy"]
+
+CAP_NAMES = ["records", "slow_hits", "runs", "anchors", "chains", "cands"]
+
+
+class GraphCaps(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in CAP_NAMES]
 
 _lib = None
 
@@ -85,6 +92,13 @@ def load(build_if_missing: bool = True):
     lib.sedef_index_blob_info.argtypes = [vp, i64, ctypes.POINTER(i32), ctypes.POINTER(i64),
                                           ctypes.POINTER(i32)]
     lib.sedef_index_load.argtypes = [vp, vp, i64, vp, i32, vp, vp, vp, i64]
+    lib.sedef_graph_create.argtypes = [vp, vp, vp, i32, P, ctypes.POINTER(GraphCaps), vp, vp, vp,
+                                       vp, vp, vp, ctypes.POINTER(vp)]
+    lib.sedef_graph_launch.argtypes = [vp, vp]
+    lib.sedef_graph_wait.argtypes = [vp, vp]
+    lib.sedef_graph_nodes.restype = i64
+    lib.sedef_graph_nodes.argtypes = [vp]
+    lib.sedef_graph_destroy.argtypes = [vp]
     lib.sedef_chain.argtypes = [vp, vp, i64, vp, i64, vp, i32, vp, vp, i64, vp, i32, P, vp, i64,
                                 ctypes.POINTER(i64)]
     lib.sedef_merge.argtypes = [vp, vp, i64, vp, i32, vp, i32, P, vp, i64, ctypes.POINTER(i64)]
@@ -96,7 +110,7 @@ def load(build_if_missing: bool = True):
     lib.sedef_filter_stats.argtypes = [vp, vp, i32]
     for name in EXPORTS:
         if name not in ("sedef_default_params", "sedef_last_error", "sedef_launch_count",
-                        "sedef_index_blob_size"):
+                        "sedef_index_blob_size", "sedef_graph_nodes"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -246,7 +260,7 @@ class Context:
 
     def sedef_filter(self, qrec, qoff, trec, tsorted, toff_tab, toff, p: Params, cap=None):
         qo, to = _offsets(qoff), _offsets(toff)
-        cap = cap if cap is not None else max(4096, int(qo[-1]) // 64)
+        cap = cap if cap is not None else max(4096, int(qo[-1]) // 16)
         count = ctypes.c_int64()
         for _ in range(2):
             runs = self._empty(cap * RUN_DTYPE.itemsize, self.torch.uint8)
@@ -338,6 +352,28 @@ class Context:
 
     # -- whole path -------------------------------------------------------------
 
+    def selfsearch_graph(self, d_seq, offsets, p: Params, caps: dict = None, slack: float = 1.25):
+        """A Graph for this device sequence, run once; rebuilt with larger
+        capacities (reported totals x slack) until nothing overflows."""
+        caps = dict(caps or default_caps(int(_offsets(offsets)[-1])))
+        # a stage's total is exact only once the stages before it fit, so a
+        # pass that starts far too small takes a few rebuilds
+        for _ in range(8):
+            g = Graph(self, d_seq, offsets, p, caps)
+            g.launch()
+            try:
+                g.wait()
+                return g
+            except SedefError as e:
+                if e.status != SEDEF_ERR_CAPACITY:
+                    g.close()
+                    raise
+                for k, v in e.need.items():
+                    if v > caps[k]:
+                        caps[k] = int(v * slack) + 1024
+                g.close()
+        raise SedefError(SEDEF_ERR_CAPACITY, "graph capacities did not converge")
+
     def selfsearch(self, d_seq, offsets, p: Params, autotune: bool = False):
         """All stages on a device-resident sequence; returns every output.
         With autotune, the filter's first-tier shape is chosen first."""
@@ -351,6 +387,80 @@ class Context:
         cands, nc = self.sedef_merge(chains, nch, offsets, offsets, p)
         return dict(packed=packed, mask=mask, nbits=nbits, rec=rec, sorted=srt, off=off,
                     runs=runs, nruns=nruns, chains=chains, nchains=nch, cands=cands, ncands=nc)
+
+
+class Graph:
+    """One captured self-search pass (sedef_graph_*): recorded once for a
+    device sequence and its offsets, replayed by `run`.  Output buffers are
+    torch tensors held here; `need` after a run holds the exact totals."""
+
+    def __init__(self, ctx: "Context", d_seq, offsets, p: Params, caps: dict):
+        t = ctx.torch
+        self.ctx, self.lib, self.d_seq = ctx, ctx.lib, d_seq
+        self.offsets = _offsets(offsets)
+        self.p = params_from_struct(p)
+        self.caps = {k: max(1, int(caps[k])) for k in CAP_NAMES}
+        c = self.caps
+        self.rec = ctx._empty(c["records"], t.int64)
+        self.sorted = ctx._empty(c["records"], t.int64)
+        self.off = ctx._empty((1 << (2 * p.k)) + 1, t.int32)
+        self.runs = ctx._empty(c["runs"] * RUN_DTYPE.itemsize, t.uint8)
+        self.chains = ctx._empty(c["chains"] * CHAIN_DTYPE.itemsize, t.uint8)
+        self.cands = ctx._empty(c["cands"] * CAND_DTYPE.itemsize, t.uint8)
+        gc = GraphCaps(**c)
+        h = ctypes.c_void_p()
+        _check(self.lib.sedef_graph_create(
+            ctx.handle, _ptr(d_seq), self.offsets.ctypes.data, len(self.offsets) - 1,
+            ctypes.byref(self.p), ctypes.byref(gc), _ptr(self.rec), _ptr(self.sorted),
+            _ptr(self.off), _ptr(self.runs), _ptr(self.chains), _ptr(self.cands), ctypes.byref(h)))
+        self.handle = h
+        self.nodes = int(self.lib.sedef_graph_nodes(h))
+        self.need = None
+
+    def launch(self, stream=None):
+        """Enqueues one replay on `stream` (default: the context's stream, so
+        that it follows the work that filled the input)."""
+        stream = stream if stream is not None else self.ctx.stream
+        _check(self.lib.sedef_graph_launch(self.handle, ctypes.c_void_p(stream.cuda_stream)))
+
+    def wait(self) -> dict:
+        """Synchronizes; the exact totals.  Raises SedefError (with .need)
+        when a capacity was exceeded."""
+        need = np.zeros(6, dtype=np.int64)
+        st = self.lib.sedef_graph_wait(self.handle, need.ctypes.data)
+        self.need = {k: int(v) for k, v in zip(CAP_NAMES, need)}
+        if st != SEDEF_OK:
+            err = SedefError(st, self.lib.sedef_last_error().decode())
+            err.need = self.need
+            raise err
+        return self.need
+
+    def outputs(self) -> dict:
+        """The last run's outputs (views of the graph's buffers)."""
+        n = {k: min(self.need[k], self.caps[k]) for k in CAP_NAMES}
+        return dict(rec=self.rec[:n["records"]], sorted=self.sorted[:n["records"]], off=self.off,
+                    runs=self.runs[:n["runs"] * RUN_DTYPE.itemsize], nruns=n["runs"],
+                    chains=self.chains[:n["chains"] * CHAIN_DTYPE.itemsize], nchains=n["chains"],
+                    cands=self.cands[:n["cands"] * CAND_DTYPE.itemsize], ncands=n["cands"])
+
+    def close(self):
+        if self.handle:
+            self.lib.sedef_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def default_caps(n_bases: int) -> dict:
+    """First-guess capacities for a pass over n_bases bases (a graph that
+    overflows is rebuilt from the reported totals)."""
+    return {"records": n_bases // 4 + 1024, "slow_hits": n_bases // 2 + (1 << 20),
+            "runs": n_bases // 32 + 4096, "anchors": n_bases // 2 + (1 << 16),
+            "chains": n_bases // 32 + 4096, "cands": n_bases // 32 + 4096}
 
 
 def sedef_sketch_noalloc(packed, mask, nbits, offsets, p: Params, rec, stream) -> int:

@@ -70,6 +70,17 @@ void Pool::reset() {
   for (auto& b : blocks) b.used = false;
 }
 
+std::vector<char> Pool::snapshot() const {
+  std::vector<char> u(blocks.size());
+  for (size_t b = 0; b < blocks.size(); ++b) u[b] = blocks[b].used ? 1 : 0;
+  return u;
+}
+
+void Pool::restore(const std::vector<char>& used_before) {
+  for (size_t b = 0; b < blocks.size(); ++b)
+    if (b >= used_before.size() || !used_before[b]) blocks[b].used = false;
+}
+
 void Pool::release() {
   for (auto& b : blocks) cudaFree(b.ptr);
   blocks.clear();
@@ -78,6 +89,7 @@ void Pool::release() {
 static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 static cudaEvent_t take_event(sedef_ctx* c) {
   if (!c->spare.empty()) {
@@ -116,6 +128,52 @@ void ctx_set_stats(sedef_ctx* ctx, const int64_t* v, int n) {
 }
 int ctx_device(sedef_ctx* ctx) { return ctx->device; }
 int ctx_sm_count(sedef_ctx* ctx) { return ctx->sm_count; }
+
+void* host_buf(sedef_ctx* ctx, Planned* pl, size_t bytes) {
+  if (!pl) return ctx_host(ctx, bytes);
+  void* p = nullptr;
+  if (cudaMallocHost(&p, bytes < 64 ? 64 : bytes) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("pinned host allocation failed");
+    return nullptr;
+  }
+  pl->host_keep.push_back(p);
+  return p;
+}
+
+namespace {
+__global__ void k_plan_check(const uint32_t* count, int64_t cap, int which, uint32_t* flags,
+                             unsigned long long* need) {
+  const uint32_t v = *count;
+  need[which] = v;
+  if ((int64_t)v > cap) atomicOr(flags, 1u << which);
+}
+}  // namespace
+
+__global__ void k_plan_check64(const unsigned long long* count, int64_t cap, int which,
+                               uint32_t* flags, unsigned long long* need) {
+  const unsigned long long v = *count;
+  need[which] = v;
+  if (v > (unsigned long long)cap) atomicOr(flags, 1u << which);
+}
+
+int plan_check64(sedef_ctx* ctx, Planned* pl, const unsigned long long* d_count, int64_t cap,
+                 int which) {
+  SEDEF_KERNEL(ctx, "k_plan_check",
+               k_plan_check64<<<1, 1, 0, ctx->stream>>>(d_count, cap, which, pl->flags, pl->need));
+  return SEDEF_OK;
+}
+
+int plan_check(sedef_ctx* ctx, Planned* pl, const uint32_t* d_count, int64_t cap, int which) {
+  SEDEF_KERNEL(ctx, "k_plan_check",
+               k_plan_check<<<1, 1, 0, ctx->stream>>>(d_count, cap, which, pl->flags, pl->need));
+  return SEDEF_OK;
+}
+
+std::vector<char> ctx_pool_snapshot(sedef_ctx* ctx) { return ctx->pool.snapshot(); }
+void ctx_pool_restore(sedef_ctx* ctx, const std::vector<char>& used_before) {
+  ctx->pool.restore(used_before);
+}
 
 void* ctx_alloc(sedef_ctx* ctx, size_t bytes) {
   void* p = ctx->pool.alloc(bytes);
@@ -173,7 +231,7 @@ int derive(const sedef_params* p, Derived* d) {
 }
 
 // m(s) table for s in [0, smax] (Section 3.1 tau; Section 2.2 count test).
-static void mtable(const sedef_params* p, int32_t* m, int smax, double* tau_out) {
+void mtable(const sedef_params* p, int32_t* m, int smax, double* tau_out) {
   const double tau = (1.0 - p->delta_g) / (1.0 + p->delta_g) *
                      (1.0 / (2.0 * std::exp((double)p->k * p->delta_m) - 1.0));
   if (tau_out) *tau_out = tau;

@@ -63,6 +63,10 @@ struct Pool {
   void* alloc(size_t bytes);
   void reset();
   void release();
+  // Blocks in use now; restore() hands back every block taken since (the
+  // stream orders later kernels after the ones that used them).
+  std::vector<char> snapshot() const;
+  void restore(const std::vector<char>& used_before);
 };
 
 // Launch-time derived parameters shared by the kernels (computed on the host
@@ -138,6 +142,15 @@ __device__ __forceinline__ int64_t lower_bound_by(const uint64_t* a, int64_t lo,
   return lo;
 }
 
+// A data-dependent count inside a captured pass.  Host code sizes grids and
+// buffers by a planned capacity `n`; the exact count stays on the device at
+// `d` (nullptr in an eager call, where `n` is exact).  Kernels read it here.
+__device__ __forceinline__ int64_t live_n(int64_t n, const uint32_t* d) {
+  if (!d) return n;
+  const int64_t v = (int64_t)*d;
+  return v < n ? v : n;
+}
+
 // Record field access (layout in sedef.h).
 __device__ __forceinline__ uint32_t rec_hash(uint64_t r) { return (uint32_t)(r >> 33); }
 __device__ __forceinline__ uint32_t rec_pos(uint64_t r) { return (uint32_t)(r >> 1); }
@@ -159,28 +172,67 @@ __device__ __forceinline__ int seq_of(const int64_t* off, int nseq, int64_t pos)
 // Launchers implemented in the kernel translation units.
 namespace sedef {
 struct Ctx;
+
+// A pass without host synchronization (one CUDA graph): every stage sizes
+// its buffers and grids by these capacities, leaves its exact counts on the
+// device and records overflow in `flags` instead of returning.  The counts
+// in `need` (device, u64) are the exact totals, so that a caller whose
+// capacities were too small learns the sizes to plan for.
+struct Planned {
+  int64_t rec = 0, slow_hits = 0, runs = 0, anchors = 0, chains = 0, cands = 0;
+  const uint32_t* n_rec = nullptr;     // set by the sketch
+  const uint32_t* n_runs = nullptr;    // set by the filter
+  const uint32_t* n_chains = nullptr;  // set by the chain
+  const uint32_t* n_cands = nullptr;   // set by the merge
+  // device words: [0] flags (bit 0 records, 1 slow hits, 2 runs, 3 anchors,
+  // 4 chains, 5 candidates over capacity; bit 6 a seed over the anchor
+  // limit), [1..7] reserved; need[0..5] exact totals in the order above
+  uint32_t* flags = nullptr;
+  unsigned long long* need = nullptr;
+  std::vector<void*> host_keep;  // pinned uploads the graph reads at replay
+};
+enum PlanFlag : uint32_t {
+  kOverRec = 1u, kOverSlowHits = 2u, kOverRuns = 4u, kOverAnchors = 8u, kOverChains = 16u,
+  kOverCands = 32u, kAnchorLimit = 64u
+};
+// Pinned host memory for an upload: the context's reusable buffer in an
+// eager call (drains the stream first), a buffer kept for the graph's
+// lifetime in a planned pass.
+void* host_buf(sedef_ctx* ctx, Planned* pl, size_t bytes);
+// Enqueues: need[which] = *d_count; flags |= 1 << which when it exceeds cap.
+int plan_check(sedef_ctx* ctx, Planned* pl, const uint32_t* d_count, int64_t cap, int which);
+int plan_check64(sedef_ctx* ctx, Planned* pl, const unsigned long long* d_count, int64_t cap,
+                 int which);
+// m(s) for s in [0, smax] from the parameters' tau (Section 3.1).
+void mtable(const sedef_params* p, int32_t* m, int smax, double* tau_out);
 int launch_pack(sedef_ctx* ctx, const uint8_t* seq, int64_t n, uint32_t* packed, uint32_t* mask,
                 uint32_t* nbits);
 int run_sketch(sedef_ctx* ctx, const uint32_t* packed, const uint32_t* mask, const uint32_t* nbits,
                const int64_t* h_off, int nseq, const Derived& D, uint64_t* rec, int64_t cap,
-               int64_t* nrec);
+               int64_t* nrec, Planned* pl = nullptr);
 int radix_sort_u64(sedef_ctx* ctx, const uint64_t* keys_in, const uint32_t* vals_in,
-                   uint64_t* keys_out, uint32_t* vals_out, int64_t n, int bit_lo, int bit_hi);
-int build_offsets(sedef_ctx* ctx, const uint64_t* sorted, int64_t n, int k, uint32_t* off);
+                   uint64_t* keys_out, uint32_t* vals_out, int64_t n, int bit_lo, int bit_hi,
+                   const uint32_t* dn = nullptr);
+int build_offsets(sedef_ctx* ctx, const uint64_t* sorted, int64_t n, int k, uint32_t* off,
+                  const uint32_t* dn = nullptr);
 int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* h_qoff, int nqseq,
                const uint64_t* trec, const uint64_t* tsorted, const uint32_t* toff, int64_t nt,
                const int64_t* h_toff, int ntseq, const Derived& D, const int32_t* h_mtab,
-               sedef_run_t* runs, int64_t cap, int64_t* nruns, int tune);
+               sedef_run_t* runs, int64_t cap, int64_t* nruns, int tune, Planned* pl = nullptr);
 int filter_variant_count();
 int run_chain(sedef_ctx* ctx, const sedef_run_t* runs, int64_t nruns, const uint64_t* qrec, int64_t nq,
               const int64_t* h_qoff, int nqseq, const uint64_t* tsorted, int64_t nt,
               const uint32_t* toff, const int64_t* h_toff, int ntseq, const Derived& D,
-              const int32_t* h_mtab, sedef_chain_t* chains, int64_t cap, int64_t* nchains);
+              const int32_t* h_mtab, sedef_chain_t* chains, int64_t cap, int64_t* nchains,
+              Planned* pl = nullptr);
 int run_merge(sedef_ctx* ctx, const sedef_chain_t* chains, int64_t nchains, const int64_t* h_qoff,
               int nqseq, const int64_t* h_toff, int ntseq, const Derived& D, sedef_cand_t* cands,
-              int64_t cap, int64_t* ncands);
+              int64_t cap, int64_t* ncands, Planned* pl = nullptr);
+int scan_exclusive_u32(sedef_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n,
+                       uint32_t* d_total);
 // Tracing (per-kernel CUDA events on the context's stream) and launch count.
 void count_launch();
+void count_launches(unsigned long long n);  // kernel nodes of a graph replay
 struct TraceScope {
   sedef_ctx* ctx;
   int slot;
@@ -190,6 +242,8 @@ struct TraceScope {
 // Context accessors for the kernel translation units.
 cudaStream_t ctx_stream(sedef_ctx* ctx);
 void* ctx_alloc(sedef_ctx* ctx, size_t bytes);
+std::vector<char> ctx_pool_snapshot(sedef_ctx* ctx);
+void ctx_pool_restore(sedef_ctx* ctx, const std::vector<char>& used_before);
 void* ctx_host(sedef_ctx* ctx, size_t bytes);  // pinned host scratch
 int ctx_device(sedef_ctx* ctx);
 int ctx_sm_count(sedef_ctx* ctx);

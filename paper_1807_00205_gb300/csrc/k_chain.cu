@@ -37,7 +37,24 @@ struct ChainArgs {
   int ntseq;
   const int32_t* mtab;
   int k, span, max_occ, self_mode, gap_max, diag_max;
+  // live counts of a planned pass, the anchor capacity and its overflow flags
+  const uint32_t* dnruns = nullptr;
+  const uint32_t* dnq = nullptr;
+  const uint32_t* dnt = nullptr;
+  int64_t acap = 0;
+  uint32_t* flags = nullptr;
+  unsigned long long* atotal = nullptr;  // exact anchor total (planned pass)
 };
+
+// The chain DP is quadratic in a seed's anchors; a seed inside an unmasked
+// low-complexity run can have millions.  Such seeds are refused.
+constexpr int kMaxChainAnchors = 1 << 16;
+
+__device__ __forceinline__ void resolve(ChainArgs& a) {
+  a.nruns = live_n(a.nruns, a.dnruns);
+  a.nq = live_n(a.nq, a.dnq);
+  a.nt = live_n(a.nt, a.dnt);
+}
 
 __device__ __forceinline__ int64_t posting_lb(const uint64_t* idx, int64_t lo, int64_t hi,
                                               uint32_t pos) {
@@ -84,6 +101,7 @@ __device__ __forceinline__ void window_range(const ChainArgs& a, int64_t i, int6
 
 // Anchors per kept run (0 for runs that are not kept).
 __global__ void k_anchor_count(ChainArgs a, uint32_t* count) {
+  resolve(a);
   const int lane = lane_id();
   const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (r >= a.nruns) return;
@@ -98,16 +116,24 @@ __global__ void k_anchor_count(ChainArgs a, uint32_t* count) {
       total += record_anchors(a, run, a.qrec[x], [](int, uint32_t, uint32_t) {});
     total = warp_sum(total);
   }
-  if (lane == 0) count[r] = (uint32_t)total;
+  if (lane == 0) {
+    count[r] = (uint32_t)total;
+    if (a.atotal && total) atomicAdd(a.atotal, (unsigned long long)total);
+  }
 }
 
 // Writes anchors as (p << 32 | t') at the run's offset, in (p, t') order.
 __global__ void k_anchor_fill(ChainArgs a, const uint32_t* aoff, uint64_t* anchors) {
+  resolve(a);
   const int lane = lane_id();
   const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (r >= a.nruns) return;
   const sedef_run_t run = a.runs[r];
   if (!run.keep) return;
+  // 32-bit offsets: a range that wraps or ends past the capacity is skipped
+  if (aoff[r + 1] < aoff[r] || (int64_t)aoff[r + 1] > a.acap ||
+      aoff[r + 1] - aoff[r] > (uint32_t)kMaxChainAnchors)
+    return;
   int64_t qa = 0, qb = 0;
   if (lane == 0) window_range(a, run.i, &qa, &qb);
   qa = __shfl_sync(0xffffffffu, qa, 0);
@@ -132,6 +158,7 @@ __global__ void k_anchor_fill(ChainArgs a, const uint32_t* aoff, uint64_t* ancho
 // DP over each kept run's anchors; writes the run's chain (score 0 = none).
 __global__ void k_chain_dp(ChainArgs a, const uint32_t* aoff, const uint64_t* anchors, int32_t* f,
                            int32_t* pred, sedef_chain_t* out) {
+  resolve(a);
   const int lane = lane_id();
   const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (r >= a.nruns) return;
@@ -143,7 +170,12 @@ __global__ void k_chain_dp(ChainArgs a, const uint32_t* aoff, const uint64_t* an
   c.score = 0;
   c.reserved = 0;
   const uint32_t A0 = aoff[r], A = aoff[r + 1] - A0;
-  if (!run.keep || A == 0) {
+  const bool wrapped = aoff[r + 1] < A0;
+  const bool over = wrapped || (int64_t)aoff[r + 1] > a.acap;
+  const bool big = !wrapped && A > (uint32_t)kMaxChainAnchors;
+  if (run.keep && (over || big) && a.flags && lane == 0)
+    atomicOr(a.flags, (over ? (uint32_t)kOverAnchors : 0u) | (big ? (uint32_t)kAnchorLimit : 0u));
+  if (!run.keep || A == 0 || over || big) {
     if (lane == 0) {
       c.qseq = c.q0 = c.q1 = c.tseq = c.t0 = c.t1 = 0;
       out[r] = c;
@@ -229,15 +261,18 @@ __global__ void k_max_u32(const uint32_t* v, int64_t n, uint32_t* out) {
   if (lane_id() == 0) atomicMax(out, m);
 }
 
-__global__ void k_chain_flags(const sedef_chain_t* c, int64_t n, uint32_t* flag) {
+// Flags over all n slots (zero past the live count, so that a scan over n
+// counts the live chains only).
+__global__ void k_chain_flags(const sedef_chain_t* c, int64_t n, uint32_t* flag,
+                              const uint32_t* dn) {
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x < n) flag[x] = c[x].score > 0 ? 1u : 0u;
+  if (x < n) flag[x] = (x < live_n(n, dn) && c[x].score > 0) ? 1u : 0u;
 }
 
 __global__ void k_chain_compact(const sedef_chain_t* c, int64_t n, const uint32_t* pos,
-                                sedef_chain_t* out, int64_t cap) {
+                                sedef_chain_t* out, int64_t cap, const uint32_t* dn) {
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x < n && c[x].score > 0 && (int64_t)pos[x] < cap) out[pos[x]] = c[x];
+  if (x < live_n(n, dn) && c[x].score > 0 && (int64_t)pos[x] < cap) out[pos[x]] = c[x];
 }
 
 // ----------------------------------------------------------------- merge --
@@ -249,6 +284,7 @@ struct MergeArgs {
   int32_t* parent;       // over sorted positions
   int diag_max;
   double delta_g;
+  const uint32_t* dn = nullptr;  // live chain count of a planned pass
 };
 
 __device__ __forceinline__ int uf_find(int32_t* parent, int x) {
@@ -295,6 +331,7 @@ __global__ void k_merge_init(int32_t* parent, int64_t n) {
 }
 
 __global__ void k_merge_link(MergeArgs a) {
+  a.n = live_n(a.n, a.dn);
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= a.n) return;
   const sedef_chain_t A = a.ch[a.perm[x]];
@@ -310,6 +347,7 @@ struct Agg {
 };
 
 __global__ void k_merge_agg(MergeArgs a, Agg* agg) {
+  a.n = live_n(a.n, a.dn);
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= a.n) return;
   const int root = uf_find(a.parent, (int)x);
@@ -334,17 +372,18 @@ __global__ void k_agg_init(Agg* agg, int64_t n) {
   }
 }
 
-__global__ void k_root_flags(const int32_t* parent, int64_t n, uint32_t* flag) {
+__global__ void k_root_flags(const int32_t* parent, int64_t n, uint32_t* flag, const uint32_t* dn) {
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x < n) flag[x] = parent[x] == (int32_t)x ? 1u : 0u;
+  if (x < n) flag[x] = (x < live_n(n, dn) && parent[x] == (int32_t)x) ? 1u : 0u;
 }
 
 // Candidate keys: primary (q0 << 32 | t0); the tie order (o, q1, t1) is
 // applied by k_fix_ties after the primary sort.
 __global__ void k_cand_emit(MergeArgs a, const Agg* agg, const uint32_t* pos, sedef_cand_t* tmp,
-                            uint64_t* key) {
+                            uint64_t* key, int64_t ccap) {
+  a.n = live_n(a.n, a.dn);
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= a.n || a.parent[x] != (int32_t)x) return;
+  if (x >= a.n || a.parent[x] != (int32_t)x || (int64_t)pos[x] >= ccap) return;
   const sedef_chain_t c = a.ch[a.perm[x]];
   const Agg g = agg[x];
   sedef_cand_t d;
@@ -377,7 +416,9 @@ __device__ __forceinline__ bool cand_less(const sedef_cand_t& x, const sedef_can
 // Gathers candidates in primary-key order, orders equal-key groups by the
 // full comparator (groups are tiny) and converts to per-sequence coordinates.
 __global__ void k_cand_final(const sedef_cand_t* tmp, const uint32_t* perm, const uint64_t* skey,
-                             int64_t n, const int64_t* qseq, const int64_t* tseq, sedef_cand_t* out) {
+                             int64_t n, const int64_t* qseq, const int64_t* tseq, sedef_cand_t* out,
+                             const uint32_t* dn) {
+  n = live_n(n, dn);
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= n) return;
   if (x > 0 && skey[x - 1] == skey[x]) return;  // group leader handles the group
@@ -410,25 +451,23 @@ __global__ void k_cand_final(const sedef_cand_t* tmp, const uint32_t* perm, cons
   }
 }
 
-__global__ void k_chain_keys(const sedef_chain_t* c, int64_t n, uint64_t* key) {
+__global__ void k_chain_keys(const sedef_chain_t* c, int64_t n, uint64_t* key, const uint32_t* dn) {
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x < n) key[x] = ((uint64_t)c[x].o << 32) | c[x].q0;
+  if (x < live_n(n, dn)) key[x] = ((uint64_t)c[x].o << 32) | c[x].q0;
 }
 
 int grid_of(int64_t n, int b) { return (int)((n + b - 1) / b); }
-
-constexpr int kMaxChainAnchors = 1 << 16;
 
 }  // namespace
 
 int scan_exclusive_u32(sedef_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n,
                        uint32_t* d_total);
 
-static int upload_offsets(sedef_ctx* ctx, const int64_t* h_q, int nq, const int64_t* h_t, int nt,
-                          int64_t** d_q, int64_t** d_t) {
+static int upload_offsets(sedef_ctx* ctx, Planned* pl, const int64_t* h_q, int nq,
+                          const int64_t* h_t, int nt, int64_t** d_q, int64_t** d_t) {
   cudaStream_t st = ctx_stream(ctx);
   const size_t bytes = (size_t)(nq + 1 + nt + 1) * 8;
-  int64_t* h = (int64_t*)ctx_host(ctx, bytes);
+  int64_t* h = (int64_t*)host_buf(ctx, pl, bytes);
   int64_t* d = (int64_t*)ctx_alloc(ctx, bytes);
   if (!h || !d) return SEDEF_ERR_OOM;
   std::memcpy(h, h_q, (size_t)(nq + 1) * 8);
@@ -442,14 +481,22 @@ static int upload_offsets(sedef_ctx* ctx, const int64_t* h_q, int nq, const int6
 int run_chain(sedef_ctx* ctx, const sedef_run_t* runs, int64_t nruns, const uint64_t* qrec, int64_t nq,
               const int64_t* h_qoff, int nqseq, const uint64_t* tsorted, int64_t nt,
               const uint32_t* toff, const int64_t* h_toff, int ntseq, const Derived& D,
-              const int32_t* h_mtab, sedef_chain_t* chains, int64_t cap, int64_t* nchains) {
+              const int32_t* h_mtab, sedef_chain_t* chains, int64_t cap, int64_t* nchains,
+              Planned* pl) {
   cudaStream_t st = ctx_stream(ctx);
   int64_t *dq = nullptr, *dt = nullptr;
-  SEDEF_TRY(upload_offsets(ctx, h_qoff, nqseq, h_toff, ntseq, &dq, &dt));
+  SEDEF_TRY(upload_offsets(ctx, pl, h_qoff, nqseq, h_toff, ntseq, &dq, &dt));
   int32_t* dm = (int32_t*)ctx_alloc(ctx, (size_t)(kMaxWindowRecs + 1) * 4);
   if (!dm) return SEDEF_ERR_OOM;
-  SEDEF_CUDA(cudaMemcpyAsync(dm, h_mtab, (size_t)(kMaxWindowRecs + 1) * 4, cudaMemcpyHostToDevice, st));
-  SEDEF_CUDA(cudaStreamSynchronize(st));  // the mtab upload reads caller memory
+  if (pl) {
+    int32_t* hm = (int32_t*)host_buf(ctx, pl, (size_t)(kMaxWindowRecs + 1) * 4);
+    if (!hm) return SEDEF_ERR_OOM;
+    std::memcpy(hm, h_mtab, (size_t)(kMaxWindowRecs + 1) * 4);
+    SEDEF_CUDA(cudaMemcpyAsync(dm, hm, (size_t)(kMaxWindowRecs + 1) * 4, cudaMemcpyHostToDevice, st));
+  } else {
+    SEDEF_CUDA(cudaMemcpyAsync(dm, h_mtab, (size_t)(kMaxWindowRecs + 1) * 4, cudaMemcpyHostToDevice, st));
+    SEDEF_CUDA(cudaStreamSynchronize(st));  // the mtab upload reads caller memory
+  }
 
   ChainArgs a;
   a.runs = runs;
@@ -470,12 +517,24 @@ int run_chain(sedef_ctx* ctx, const sedef_run_t* runs, int64_t nruns, const uint
   a.self_mode = D.self_mode;
   a.gap_max = D.gap_max;
   a.diag_max = D.diag_max;
+  unsigned long long* atotal = nullptr;
+  if (pl) {
+    a.dnruns = pl->n_runs;
+    a.dnq = pl->n_rec;
+    a.dnt = pl->n_rec;
+    a.flags = pl->flags;
+    atotal = (unsigned long long*)ctx_alloc(ctx, 8);
+    if (!atotal) return SEDEF_ERR_OOM;
+    SEDEF_CUDA(cudaMemsetAsync(atotal, 0, 8, st));
+    a.atotal = atotal;
+  }
 
   uint32_t* cnt = (uint32_t*)ctx_alloc(ctx, (size_t)(nruns + 1) * 4);
   uint32_t* aoff = (uint32_t*)ctx_alloc(ctx, (size_t)(nruns + 1) * 4);
   sedef_chain_t* tmp = (sedef_chain_t*)ctx_alloc(ctx, (size_t)nruns * sizeof(sedef_chain_t));
   if (!cnt || !aoff || !tmp) return SEDEF_ERR_OOM;
   const int wb = grid_of(nruns * 32, 256);
+  if (pl) SEDEF_CUDA(cudaMemsetAsync(cnt, 0, (size_t)(nruns + 1) * 4, st));
   SEDEF_KERNEL(ctx, "k_anchor_count", k_anchor_count<<<wb, 256, 0, st>>>(a, cnt));
   uint32_t* amax = (uint32_t*)ctx_alloc(ctx, 8);
   if (!amax) return SEDEF_ERR_OOM;
@@ -483,18 +542,26 @@ int run_chain(sedef_ctx* ctx, const sedef_run_t* runs, int64_t nruns, const uint
   SEDEF_KERNEL(ctx, "k_max_u32",
                k_max_u32<<<grid_of(nruns < 65536 ? nruns : 65536, 256), 256, 0, st>>>(cnt, nruns, amax));
   SEDEF_TRY(scan_exclusive_u32(ctx, cnt, aoff, nruns, aoff + nruns));
-  uint32_t* h_tot = (uint32_t*)ctx_host(ctx, 8);
-  if (!h_tot) return SEDEF_ERR_OOM;
-  SEDEF_CUDA(cudaMemcpyAsync(h_tot, aoff + nruns, 4, cudaMemcpyDeviceToHost, st));
-  SEDEF_CUDA(cudaMemcpyAsync(h_tot + 1, amax, 4, cudaMemcpyDeviceToHost, st));
-  SEDEF_CUDA(cudaStreamSynchronize(st));
-  const int64_t A = *h_tot;
-  // The chain DP is quadratic in a seed's anchors; a seed inside an unmasked
-  // low-complexity run can have millions.  Refuse instead of running for hours.
-  if (h_tot[1] > (uint32_t)kMaxChainAnchors)
-    return fail(SEDEF_ERR_UNSUPPORTED,
-                "sedef_chain: a seed has " + std::to_string(h_tot[1]) +
-                    " anchors (limit 65536); soft-mask low-complexity repeats or set max_occ");
+  int64_t A;
+  if (pl) {
+    // anchors: planned capacity; seeds past it or over the limit are
+    // skipped and flagged by the DP
+    A = pl->anchors;
+    SEDEF_TRY(plan_check64(ctx, pl, atotal, A, 3));
+  } else {
+    uint32_t* h_tot = (uint32_t*)ctx_host(ctx, 8);
+    if (!h_tot) return SEDEF_ERR_OOM;
+    SEDEF_CUDA(cudaMemcpyAsync(h_tot, aoff + nruns, 4, cudaMemcpyDeviceToHost, st));
+    SEDEF_CUDA(cudaMemcpyAsync(h_tot + 1, amax, 4, cudaMemcpyDeviceToHost, st));
+    SEDEF_CUDA(cudaStreamSynchronize(st));
+    A = *h_tot;
+    // refuse instead of running for hours
+    if (h_tot[1] > (uint32_t)kMaxChainAnchors)
+      return fail(SEDEF_ERR_UNSUPPORTED,
+                  "sedef_chain: a seed has " + std::to_string(h_tot[1]) +
+                      " anchors (limit 65536); soft-mask low-complexity repeats or set max_occ");
+  }
+  a.acap = A;
   uint64_t* anchors = (uint64_t*)ctx_alloc(ctx, (size_t)(A ? A : 1) * 8);
   int32_t* f = (int32_t*)ctx_alloc(ctx, (size_t)(A ? A : 1) * 4);
   int32_t* pred = (int32_t*)ctx_alloc(ctx, (size_t)(A ? A : 1) * 4);
@@ -504,25 +571,39 @@ int run_chain(sedef_ctx* ctx, const sedef_run_t* runs, int64_t nruns, const uint
   uint32_t* flag = cnt;  // reuse
   uint32_t* pos = (uint32_t*)ctx_alloc(ctx, (size_t)(nruns + 1) * 4);
   if (!pos) return SEDEF_ERR_OOM;
-  SEDEF_KERNEL(ctx, "k_chain_flags", k_chain_flags<<<grid_of(nruns, 256), 256, 0, st>>>(tmp, nruns, flag));
+  const uint32_t* dn = pl ? pl->n_runs : nullptr;
+  SEDEF_KERNEL(ctx, "k_chain_flags",
+               k_chain_flags<<<grid_of(nruns, 256), 256, 0, st>>>(tmp, nruns, flag, dn));
   SEDEF_TRY(scan_exclusive_u32(ctx, flag, pos, nruns, pos + nruns));
+  if (pl) {
+    pl->n_chains = pos + nruns;
+    SEDEF_TRY(plan_check(ctx, pl, pos + nruns, cap, 4));
+    *nchains = cap;
+    SEDEF_KERNEL(ctx, "k_chain_compact",
+                 k_chain_compact<<<grid_of(nruns, 256), 256, 0, st>>>(tmp, nruns, pos, chains, cap, dn));
+    return SEDEF_OK;
+  }
+  uint32_t* h_tot = (uint32_t*)ctx_host(ctx, 8);
+  if (!h_tot) return SEDEF_ERR_OOM;
   SEDEF_CUDA(cudaMemcpyAsync(h_tot, pos + nruns, 4, cudaMemcpyDeviceToHost, st));
   SEDEF_CUDA(cudaStreamSynchronize(st));
   *nchains = *h_tot;
   if (*nchains > cap) return fail(SEDEF_ERR_CAPACITY, "sedef_chain_t: chain buffer too small");
   SEDEF_KERNEL(ctx, "k_chain_compact",
-               k_chain_compact<<<grid_of(nruns, 256), 256, 0, st>>>(tmp, nruns, pos, chains, cap));
+               k_chain_compact<<<grid_of(nruns, 256), 256, 0, st>>>(tmp, nruns, pos, chains, cap,
+                                                                    nullptr));
   SEDEF_CUDA(cudaStreamSynchronize(st));
   return SEDEF_OK;
 }
 
 int run_merge(sedef_ctx* ctx, const sedef_chain_t* chains, int64_t n, const int64_t* h_qoff,
               int nqseq, const int64_t* h_toff, int ntseq, const Derived& D, sedef_cand_t* cands,
-              int64_t cap, int64_t* ncands) {
+              int64_t cap, int64_t* ncands, Planned* pl) {
   cudaStream_t st = ctx_stream(ctx);
   if (n >= (int64_t(1) << 31)) return fail(SEDEF_ERR_UNSUPPORTED, "too many chains");
+  const uint32_t* dn = pl ? pl->n_chains : nullptr;
   int64_t *dq = nullptr, *dt = nullptr;
-  SEDEF_TRY(upload_offsets(ctx, h_qoff, nqseq, h_toff, ntseq, &dq, &dt));
+  SEDEF_TRY(upload_offsets(ctx, pl, h_qoff, nqseq, h_toff, ntseq, &dq, &dt));
   uint64_t* key = (uint64_t*)ctx_alloc(ctx, (size_t)n * 8);
   uint64_t* skey = (uint64_t*)ctx_alloc(ctx, (size_t)n * 8);
   uint32_t* perm = (uint32_t*)ctx_alloc(ctx, (size_t)n * 4);
@@ -532,8 +613,8 @@ int run_merge(sedef_ctx* ctx, const sedef_chain_t* chains, int64_t n, const int6
   uint32_t* pos = (uint32_t*)ctx_alloc(ctx, (size_t)(n + 1) * 4);
   if (!key || !skey || !perm || !parent || !agg || !flag || !pos) return SEDEF_ERR_OOM;
   const int g = grid_of(n, 256);
-  SEDEF_KERNEL(ctx, "k_chain_keys", k_chain_keys<<<g, 256, 0, st>>>(chains, n, key));
-  SEDEF_TRY(radix_sort_u64(ctx, key, nullptr, skey, perm, n, 0, 33));
+  SEDEF_KERNEL(ctx, "k_chain_keys", k_chain_keys<<<g, 256, 0, st>>>(chains, n, key, dn));
+  SEDEF_TRY(radix_sort_u64(ctx, key, nullptr, skey, perm, n, 0, 33, dn));
   MergeArgs a;
   a.ch = chains;
   a.n = n;
@@ -541,29 +622,42 @@ int run_merge(sedef_ctx* ctx, const sedef_chain_t* chains, int64_t n, const int6
   a.parent = parent;
   a.diag_max = D.diag_max;
   a.delta_g = D.delta_g;
+  a.dn = dn;
   SEDEF_KERNEL(ctx, "k_merge_init", k_merge_init<<<g, 256, 0, st>>>(parent, n));
   SEDEF_KERNEL(ctx, "k_merge_link", k_merge_link<<<g, 256, 0, st>>>(a));
   SEDEF_KERNEL(ctx, "k_agg_init", k_agg_init<<<g, 256, 0, st>>>(agg, n));
   SEDEF_KERNEL(ctx, "k_merge_agg", k_merge_agg<<<g, 256, 0, st>>>(a, agg));
-  SEDEF_KERNEL(ctx, "k_root_flags", k_root_flags<<<g, 256, 0, st>>>(parent, n, flag));
+  SEDEF_KERNEL(ctx, "k_root_flags", k_root_flags<<<g, 256, 0, st>>>(parent, n, flag, dn));
   SEDEF_TRY(scan_exclusive_u32(ctx, flag, pos, n, pos + n));
-  uint32_t* h_tot = (uint32_t*)ctx_host(ctx, 8);
-  if (!h_tot) return SEDEF_ERR_OOM;
-  SEDEF_CUDA(cudaMemcpyAsync(h_tot, pos + n, 4, cudaMemcpyDeviceToHost, st));
-  SEDEF_CUDA(cudaStreamSynchronize(st));
-  const int64_t nc = *h_tot;
-  *ncands = nc;
-  if (nc > cap) return fail(SEDEF_ERR_CAPACITY, "sedef_merge: candidate buffer too small");
+  int64_t nc;
+  const uint32_t* dnc = nullptr;
+  if (pl) {
+    nc = cap;
+    dnc = pos + n;
+    pl->n_cands = dnc;
+    SEDEF_TRY(plan_check(ctx, pl, dnc, cap, 5));
+    *ncands = cap;
+  } else {
+    uint32_t* h_tot = (uint32_t*)ctx_host(ctx, 8);
+    if (!h_tot) return SEDEF_ERR_OOM;
+    SEDEF_CUDA(cudaMemcpyAsync(h_tot, pos + n, 4, cudaMemcpyDeviceToHost, st));
+    SEDEF_CUDA(cudaStreamSynchronize(st));
+    nc = *h_tot;
+    *ncands = nc;
+    if (nc > cap) return fail(SEDEF_ERR_CAPACITY, "sedef_merge: candidate buffer too small");
+  }
   if (nc == 0) return SEDEF_OK;
   sedef_cand_t* tmp = (sedef_cand_t*)ctx_alloc(ctx, (size_t)nc * sizeof(sedef_cand_t));
   uint64_t* ckey = (uint64_t*)ctx_alloc(ctx, (size_t)nc * 8);
   uint64_t* cskey = (uint64_t*)ctx_alloc(ctx, (size_t)nc * 8);
   uint32_t* cperm = (uint32_t*)ctx_alloc(ctx, (size_t)nc * 4);
   if (!tmp || !ckey || !cskey || !cperm) return SEDEF_ERR_OOM;
-  SEDEF_KERNEL(ctx, "k_cand_emit", k_cand_emit<<<g, 256, 0, st>>>(a, agg, pos, tmp, ckey));
-  SEDEF_TRY(radix_sort_u64(ctx, ckey, nullptr, cskey, cperm, nc, 0, 64));
+  SEDEF_KERNEL(ctx, "k_cand_emit", k_cand_emit<<<g, 256, 0, st>>>(a, agg, pos, tmp, ckey, nc));
+  SEDEF_TRY(radix_sort_u64(ctx, ckey, nullptr, cskey, cperm, nc, 0, 64, dnc));
   SEDEF_KERNEL(ctx, "k_cand_final",
-               k_cand_final<<<grid_of(nc, 256), 256, 0, st>>>(tmp, cperm, cskey, nc, dq, dt, cands));
+               k_cand_final<<<grid_of(nc, 256), 256, 0, st>>>(tmp, cperm, cskey, nc, dq, dt, cands,
+                                                              dnc));
+  if (pl) return SEDEF_OK;
   SEDEF_CUDA(cudaStreamSynchronize(st));
   return SEDEF_OK;
 }

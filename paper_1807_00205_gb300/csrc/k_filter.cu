@@ -631,9 +631,12 @@ __device__ void slow_hits(const FArgs& a, const SlowSmem& S, int s, int64_t i, F
   }
 }
 
-__global__ void __launch_bounds__(kSThreads) k_slow_count(FArgs a, int64_t nov,
-                                                          unsigned long long* counts, int32_t* s_out) {
+template <typename C>
+__global__ void __launch_bounds__(kSThreads) k_slow_count(FArgs a, int64_t nov, C* counts,
+                                                          int32_t* s_out, const uint32_t* dnov,
+                                                          unsigned long long* total) {
   __shared__ SlowSmem S;
+  nov = live_n(nov, dnov);
   for (int64_t v = blockIdx.x; v < nov; v += gridDim.x) {
     __syncthreads();
     const int64_t wdx = a.ov_list[v];
@@ -645,20 +648,26 @@ __global__ void __launch_bounds__(kSThreads) k_slow_count(FArgs a, int64_t nov,
     atomicAdd(&S.acc, mine);
     __syncthreads();
     if (threadIdx.x == 0) {
-      counts[v] = S.acc;
+      counts[v] = (C)S.acc;
       s_out[v] = s;
+      if (total) atomicAdd(total, S.acc);
     }
   }
 }
 
 // Writes keys (local window << 33 | o << 32 | t) and hash ids for windows
 // [v0, v1) of the overflow list at offsets base[v] - base[v0].
+// Windows whose hits would end past `hcap` are skipped (a planned pass
+// reports them as an overflow).
 __global__ void __launch_bounds__(kSThreads) k_slow_emit(FArgs a, int64_t v0, int64_t v1,
                                                          const unsigned long long* base,
-                                                         uint64_t* keys, uint32_t* vals) {
+                                                         uint64_t* keys, uint32_t* vals,
+                                                         const uint32_t* dnov, int64_t hcap) {
   __shared__ SlowSmem S;
   __shared__ unsigned long long cursor;
+  v1 = live_n(v1, dnov);
   for (int64_t v = v0 + blockIdx.x; v < v1; v += gridDim.x) {
+    if (base[v + 1] < base[v] || (int64_t)(base[v + 1] - base[v0]) > hcap) continue;
     __syncthreads();
     const int64_t wdx = a.ov_list[v];
     const int s = slow_wq(a, S, wdx);
@@ -693,12 +702,14 @@ __device__ __forceinline__ void slow_segment(const uint64_t* keys, int64_t lo, i
 
 __global__ void k_slow_groups(FArgs a, int64_t v0, int64_t v1, const unsigned long long* base,
                               const int32_t* s_of, const uint64_t* keys, SlowTask* tasks,
-                              unsigned long long* ntask, int64_t task_cap) {
+                              unsigned long long* ntask, int64_t task_cap, const uint32_t* dnov,
+                              int64_t hcap) {
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  v1 = live_n(v1, dnov);
   for (int64_t v = v0 + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < v1;
        v += nw) {
     const int s = s_of[v];
-    if (s == 0) continue;
+    if (s == 0 || base[v + 1] < base[v] || (int64_t)(base[v + 1] - base[v0]) > hcap) continue;
     const int m = a.mtab[s];
     const int64_t lo = (int64_t)(base[v] - base[v0]), hi = (int64_t)(base[v + 1] - base[v0]);
     int64_t split;
@@ -729,13 +740,13 @@ constexpr int kTaskWarps = 8;
 __global__ void __launch_bounds__(32 * kTaskWarps) k_slow_tasks(
     FArgs a, int64_t v0, const unsigned long long* base, const int32_t* s_of,
     const uint64_t* keys, const uint32_t* vals, const SlowTask* tasks,
-    const unsigned long long* ntask) {
+    const unsigned long long* ntask, int64_t task_cap) {
   __shared__ uint16_t cnt[kTaskWarps][kMaxWindowRecs];
   const int warp = threadIdx.x >> 5;
   for (int x = threadIdx.x & 31; x < kMaxWindowRecs; x += 32) cnt[warp][x] = 0;
   __syncwarp();
   if ((threadIdx.x & 31) != 0) return;
-  const int64_t nt = (int64_t)*ntask;
+  const int64_t nt = min((int64_t)*ntask, task_cap);
   for (int64_t t = (int64_t)blockIdx.x * kTaskWarps + warp; t < nt;
        t += (int64_t)gridDim.x * kTaskWarps) {
     const SlowTask task = tasks[t];
@@ -762,9 +773,11 @@ __global__ void __launch_bounds__(32 * kTaskWarps) k_slow_tasks(
 __global__ void k_windows(const uint64_t* __restrict__ qrec, int64_t nq,
                           const int64_t* __restrict__ qseq, int nqseq,
                           const int64_t* __restrict__ wbase, int64_t nwin, int step, int span,
-                          uint32_t* wi, uint32_t* wqa, uint32_t* wqb, int32_t* wseq) {
+                          uint32_t* wi, uint32_t* wqa, uint32_t* wqb, int32_t* wseq,
+                          const uint32_t* dnq) {
   const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= nwin) return;
+  nq = live_n(nq, dnq);
   int lo = 0, hi = nqseq;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
@@ -784,9 +797,10 @@ __global__ void k_windows(const uint64_t* __restrict__ qrec, int64_t nq,
 // when it fits 64 bits; part 1: j_a alone and part 2: (window, o), for a
 // two-pass stable sort otherwise.
 __global__ void k_run_keys(const sedef_run_t* runs, int64_t n, const int64_t* qseq, int nqseq,
-                           const int64_t* wbase, int step, int part, uint64_t* keys) {
+                           const int64_t* wbase, int step, int part, uint64_t* keys,
+                           const uint32_t* dn) {
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= n) return;
+  if (x >= live_n(n, dn)) return;
   const sedef_run_t r = runs[x];
   const int sq = seq_of(qseq, nqseq, r.i);
   const uint64_t widx = (uint64_t)(wbase[sq] + ((int64_t)r.i - qseq[sq]) / step);
@@ -795,20 +809,27 @@ __global__ void k_run_keys(const sedef_run_t* runs, int64_t n, const int64_t* qs
   else keys[x] = (widx << 1) | r.o;
 }
 
-__global__ void k_permute_u64(const uint64_t* in, const uint32_t* perm, int64_t n, uint64_t* out) {
+__global__ void k_permute_u64(const uint64_t* in, const uint32_t* perm, int64_t n, uint64_t* out,
+                              const uint32_t* dn) {
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x < n) out[x] = in[perm[x]];
+  if (x < live_n(n, dn)) out[x] = in[perm[x]];
 }
 
 __global__ void k_compose_perm(const uint32_t* first, const uint32_t* second, int64_t n,
-                               uint32_t* out) {
+                               uint32_t* out, const uint32_t* dn) {
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x < n) out[x] = first[second[x]];
+  if (x < live_n(n, dn)) out[x] = first[second[x]];
 }
 
-__global__ void k_gather_runs(const sedef_run_t* in, const uint32_t* perm, int64_t n, sedef_run_t* out) {
+__global__ void k_widen_u32(const uint32_t* in, int64_t n, unsigned long long* out) {
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x < n) out[x] = in[perm[x]];
+  if (x < n) out[x] = in[x];
+}
+
+__global__ void k_gather_runs(const sedef_run_t* in, const uint32_t* perm, int64_t n, sedef_run_t* out,
+                              const uint32_t* dn) {
+  const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x < live_n(n, dn)) out[x] = in[perm[x]];
 }
 
 // ----------------------------------------------------------------- refine --
@@ -917,6 +938,8 @@ struct RefineArgs {
   int64_t nq;
   const uint64_t* trec;
   int64_t nt;
+  const uint32_t* dnruns = nullptr;  // live counts of a planned pass
+  const uint32_t* dnt = nullptr;
   const uint32_t* toff;
   const int32_t* mtab;
   int span, max_occ, self_mode;
@@ -928,6 +951,8 @@ struct RefineArgs {
 
 template <int QC, int RC, bool kLean>
 __global__ void __launch_bounds__(32 * (kLean ? kRWarps : kRWarpsBig)) k_refine(RefineArgs a) {
+  a.nruns = live_n(a.nruns, a.dnruns);
+  a.nt = live_n(a.nt, a.dnt);
   using RW = RefineWarpT<QC, RC>;
   constexpr int DC = RW::DC;
   constexpr int NW = kLean ? kRWarps : kRWarpsBig;
@@ -1413,6 +1438,8 @@ __device__ __forceinline__ int lb_u32(const uint32_t* v, int n, uint32_t x) {
 }
 
 __global__ void __launch_bounds__(32 * kBWarps) k_refine_batch(RefineArgs a) {
+  a.nruns = live_n(a.nruns, a.dnruns);
+  a.nt = live_n(a.nt, a.dnt);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = lane_id();
   BatchWarp& B = reinterpret_cast<BatchWarp*>(smem_raw)[warp];
@@ -1646,9 +1673,10 @@ __global__ void __launch_bounds__(32 * kBWarps) k_refine_batch(RefineArgs a) {
 __global__ void k_run_ranges(const sedef_run_t* runs, int64_t n, const int64_t* qseq, int nqseq,
                              const int64_t* wbase, int step, const uint32_t* win_qa,
                              const uint32_t* win_qb, const uint64_t* trec, int64_t nt, int span,
-                             uint4* ranges) {
+                             uint4* ranges, const uint32_t* dn, const uint32_t* dnt) {
   const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= n) return;
+  if (x >= live_n(n, dn)) return;
+  nt = live_n(nt, dnt);
   const sedef_run_t r = runs[x];
   const int sq = seq_of(qseq, nqseq, r.i);
   const int64_t w = wbase[sq] + ((int64_t)r.i - qseq[sq]) / step;
@@ -1713,8 +1741,12 @@ int scan_exclusive_u32(sedef_ctx* ctx, const uint32_t* in, uint32_t* out, int64_
 int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* h_qoff, int nqseq,
                const uint64_t* trec, const uint64_t* tsorted, const uint32_t* toff, int64_t nt,
                const int64_t* h_toff, int ntseq, const Derived& D, const int32_t* h_mtab,
-               sedef_run_t* runs, int64_t cap, int64_t* nruns, int tune) {
+               sedef_run_t* runs, int64_t cap, int64_t* nruns, int tune, Planned* pl) {
   cudaStream_t st = ctx_stream(ctx);
+  if (pl && tune) return fail(SEDEF_ERR_INVALID, "sedef_filter: no autotuning inside a planned pass");
+  // live record counts of a planned pass (query and target are one sketch)
+  const uint32_t* dnq = pl ? pl->n_rec : nullptr;
+  const uint32_t* dnt = pl ? pl->n_rec : nullptr;
   // windows per query sequence
   std::vector<int64_t> wbase(nqseq + 1, 0);
   for (int s = 0; s < nqseq; ++s) {
@@ -1728,7 +1760,7 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   // uploads: query offsets, target offsets, window bases, m table
   const size_t up_bytes = (size_t)(nqseq + 1) * 8 * 2 + (size_t)(ntseq + 1) * 8 +
                           (size_t)(kMaxWindowRecs + 1) * 4;
-  char* h_up = (char*)ctx_host(ctx, up_bytes + 64);
+  char* h_up = (char*)host_buf(ctx, pl, up_bytes + 64);
   char* d_up = (char*)ctx_alloc(ctx, up_bytes + 64);
   if (!h_up || !d_up) return SEDEF_ERR_OOM;
   size_t o = 0;
@@ -1754,7 +1786,8 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   uint32_t* ovl1 = (uint32_t*)ctx_alloc(ctx, (size_t)nwin * 4);
   // [0] runs, [1] windows for the global path, [2] tier-1 work, [3] large
   // refine runs, [4] hits, [5] collected hits, [6]/[7] task and refine work,
-  // [8] tier-2 work, [9] windows tier 1 handed to tier 2, [10] sample size
+  // [8] tier-2 work, [9] windows tier 1 handed to tier 2, [10] sample size,
+  // [11] global-path hits (planned pass)
   unsigned long long* counters = (unsigned long long*)ctx_alloc(ctx, 128);
   sedef_run_t* raw = (sedef_run_t*)ctx_alloc(ctx, (size_t)(cap > 0 ? cap : 1) * sizeof(sedef_run_t));
   if (!wi || !wqa || !wqb || !wseq || !ovl || !ovl1 || !counters || !raw) return SEDEF_ERR_OOM;
@@ -1793,7 +1826,7 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   SEDEF_KERNEL(ctx, "k_windows",
                k_windows<<<(int)((nwin + 255) / 256), 256, 0, st>>>(
                    qrec, nq, a.qseq, nqseq, (const int64_t*)(d_up + ow), nwin, D.step, D.span, wi,
-                   wqa, wqb, wseq));
+                   wqa, wqb, wseq, dnq));
   static bool attr = false;
   if (!attr) {
     SEDEF_CUDA(cudaFuncSetAttribute(k_refine_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1856,11 +1889,57 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
     SEDEF_TRY(kTier2[v % kNumTier2](ctx, a, io2, nwin, "k_filter_mid"));
   }
 
-  unsigned long long* h_cnt = (unsigned long long*)ctx_host(ctx, 64);
-  if (!h_cnt) return SEDEF_ERR_OOM;
-  SEDEF_CUDA(cudaMemcpyAsync(h_cnt, counters, 16, cudaMemcpyDeviceToHost, st));
-  SEDEF_CUDA(cudaStreamSynchronize(st));
-  const int64_t nov = (int64_t)(h_cnt[1] & 0xFFFFFFFFull);
+  unsigned long long* h_cnt = nullptr;
+  int64_t nov = 0;
+  if (pl) {
+    // planned: the global path over the live overflow list in one batch of
+    // at most pl->slow_hits hits
+    const uint32_t* dnov = (const uint32_t*)(counters + 1);
+    const int64_t H = pl->slow_hits > 0 ? pl->slow_hits : 1;
+    uint32_t* cnt32 = (uint32_t*)ctx_alloc(ctx, (size_t)(nwin + 1) * 4);
+    uint32_t* base32 = (uint32_t*)ctx_alloc(ctx, (size_t)(nwin + 1) * 4);
+    unsigned long long* d_base = (unsigned long long*)ctx_alloc(ctx, (size_t)(nwin + 1) * 8);
+    int32_t* os = (int32_t*)ctx_alloc(ctx, (size_t)(nwin + 1) * 4);
+    uint64_t* keys = (uint64_t*)ctx_alloc(ctx, (size_t)H * 8);
+    uint32_t* vals = (uint32_t*)ctx_alloc(ctx, (size_t)H * 4);
+    uint64_t* skeys = (uint64_t*)ctx_alloc(ctx, (size_t)H * 8);
+    uint32_t* svals = (uint32_t*)ctx_alloc(ctx, (size_t)H * 4);
+    SlowTask* tasks = (SlowTask*)ctx_alloc(ctx, (size_t)H * sizeof(SlowTask));
+    if (!cnt32 || !base32 || !d_base || !os || !keys || !vals || !skeys || !svals || !tasks)
+      return SEDEF_ERR_OOM;
+    SEDEF_CUDA(cudaMemsetAsync(cnt32, 0, (size_t)(nwin + 1) * 4, st));
+    const int sgrid = (int)(nwin < (int64_t)ctx_sm_count(ctx) * 4 ? nwin : (int64_t)ctx_sm_count(ctx) * 4);
+    SEDEF_KERNEL(ctx, "k_slow_count",
+                 k_slow_count<uint32_t><<<sgrid, kSThreads, 0, st>>>(a, nwin, cnt32, os, dnov,
+                                                                     counters + 11));
+    // 32-bit offsets: a window whose range wraps is skipped; the exact
+    // 64-bit total (counters[11]) decides the overflow
+    SEDEF_TRY(scan_exclusive_u32(ctx, cnt32, base32, nwin, base32 + nwin));
+    SEDEF_KERNEL(ctx, "k_widen_u32",
+                 k_widen_u32<<<(int)((nwin + 256) / 256), 256, 0, st>>>(base32, nwin + 1, d_base));
+    const uint32_t* dhits = base32 + nwin;
+    SEDEF_TRY(plan_check64(ctx, pl, counters + 11, H, 1));
+    SEDEF_KERNEL(ctx, "k_slow_emit",
+                 k_slow_emit<<<sgrid, kSThreads, 0, st>>>(a, 0, nwin, d_base, keys, vals, dnov, H));
+    int wbits = 0;
+    while ((int64_t(1) << wbits) < nwin) ++wbits;
+    SEDEF_TRY(radix_sort_u64(ctx, keys, vals, skeys, svals, H, 0, 33 + wbits, dhits));
+    SEDEF_CUDA(cudaMemsetAsync(counters + 6, 0, 8, st));
+    const int64_t gw = (nwin + 7) / 8;
+    const int g2 = (int)(gw < (int64_t)ctx_sm_count(ctx) * 8 ? gw : (int64_t)ctx_sm_count(ctx) * 8);
+    SEDEF_KERNEL(ctx, "k_slow_groups",
+                 k_slow_groups<<<g2, 256, 0, st>>>(a, 0, nwin, d_base, os, skeys, tasks,
+                                                   counters + 6, H, dnov, H));
+    SEDEF_KERNEL(ctx, "k_slow_tasks",
+                 k_slow_tasks<<<ctx_sm_count(ctx) * 8, 32 * kTaskWarps, 0, st>>>(
+                     a, 0, d_base, os, skeys, svals, tasks, counters + 6, H));
+  } else {
+    h_cnt = (unsigned long long*)ctx_host(ctx, 64);
+    if (!h_cnt) return SEDEF_ERR_OOM;
+    SEDEF_CUDA(cudaMemcpyAsync(h_cnt, counters, 16, cudaMemcpyDeviceToHost, st));
+    SEDEF_CUDA(cudaStreamSynchronize(st));
+    nov = (int64_t)(h_cnt[1] & 0xFFFFFFFFull);
+  }
 
   if (nov > 0) {
     // slow path: count, then batches of emit -> sort -> sweep
@@ -1868,7 +1947,9 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
     int32_t* os = (int32_t*)ctx_alloc(ctx, (size_t)(nov + 1) * 4);
     if (!ocnt || !os) return SEDEF_ERR_OOM;
     int64_t sgrid = nov < (int64_t)ctx_sm_count(ctx) * 4 ? nov : (int64_t)ctx_sm_count(ctx) * 4;
-    SEDEF_KERNEL(ctx, "k_slow_count", k_slow_count<<<(int)sgrid, kSThreads, 0, st>>>(a, nov, ocnt, os));
+    SEDEF_KERNEL(ctx, "k_slow_count",
+                 k_slow_count<unsigned long long><<<(int)sgrid, kSThreads, 0, st>>>(a, nov, ocnt, os,
+                                                                                    nullptr, nullptr));
     std::vector<unsigned long long> hc(nov + 1, 0);
     SEDEF_CUDA(cudaMemcpyAsync(hc.data(), ocnt, (size_t)nov * 8, cudaMemcpyDeviceToHost, st));
     SEDEF_CUDA(cudaStreamSynchronize(st));
@@ -1883,6 +1964,8 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
       int64_t v1 = v0 + 1;
       while (v1 < nov && base[v1 + 1] - base[v0] <= budget && v1 - v0 < (1 << 20)) ++v1;
       const unsigned long long nh = base[v1] - base[v0];
+      // a batch's scratch goes back to the pool once the batch has run
+      const std::vector<char> used_before = ctx_pool_snapshot(ctx);
       if (nh > 0) {
         uint64_t* keys = (uint64_t*)ctx_alloc(ctx, (size_t)nh * 8);
         uint32_t* vals = (uint32_t*)ctx_alloc(ctx, (size_t)nh * 4);
@@ -1892,7 +1975,8 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
         const int64_t nb = v1 - v0;
         int g = (int)(nb < (int64_t)ctx_sm_count(ctx) * 4 ? nb : (int64_t)ctx_sm_count(ctx) * 4);
         SEDEF_KERNEL(ctx, "k_slow_emit",
-                     k_slow_emit<<<g, kSThreads, 0, st>>>(a, v0, v1, d_base, keys, vals));
+                     k_slow_emit<<<g, kSThreads, 0, st>>>(a, v0, v1, d_base, keys, vals, nullptr,
+                                                          (int64_t)nh));
         int wbits = 0;
         while ((int64_t(1) << wbits) < nb) ++wbits;
         SEDEF_TRY(radix_sort_u64(ctx, keys, vals, skeys, svals, (int64_t)nh, 0, 33 + wbits));
@@ -1903,21 +1987,36 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
         int g2 = (int)(gw < (int64_t)ctx_sm_count(ctx) * 8 ? gw : (int64_t)ctx_sm_count(ctx) * 8);
         SEDEF_KERNEL(ctx, "k_slow_groups",
                      k_slow_groups<<<g2, 256, 0, st>>>(a, v0, v1, d_base, os, skeys, tasks,
-                                                       counters + 6, (int64_t)nh));
+                                                       counters + 6, (int64_t)nh, nullptr,
+                                                       (int64_t)nh));
         SEDEF_KERNEL(ctx, "k_slow_tasks",
                      k_slow_tasks<<<ctx_sm_count(ctx) * 8, 32 * kTaskWarps, 0, st>>>(
-                         a, v0, d_base, os, skeys, svals, tasks, counters + 6));
+                         a, v0, d_base, os, skeys, svals, tasks, counters + 6, (int64_t)nh));
         SEDEF_CUDA(cudaStreamSynchronize(st));
       }
+      ctx_pool_restore(ctx, used_before);
       v0 = v1;
     }
     SEDEF_CUDA(cudaMemcpyAsync(h_cnt, counters, 8, cudaMemcpyDeviceToHost, st));
     SEDEF_CUDA(cudaStreamSynchronize(st));
   }
-  const int64_t total = (int64_t)h_cnt[0];
-  *nruns = total;
-  if (total > cap) return fail(SEDEF_ERR_CAPACITY, "sedef_filter: run buffer too small");
-  if (total == 0) return SEDEF_OK;
+  // runs: the exact count (eager) or the planned capacity with the live
+  // count on the device (the low word of counters[0])
+  const uint32_t* druns = nullptr;
+  int64_t total;
+  if (pl) {
+    total = cap;
+    druns = (const uint32_t*)counters;
+    pl->n_runs = druns;
+    SEDEF_TRY(plan_check(ctx, pl, druns, cap, 2));
+    *nruns = cap;
+    if (total == 0) return SEDEF_OK;
+  } else {
+    total = (int64_t)h_cnt[0];
+    *nruns = total;
+    if (total > cap) return fail(SEDEF_ERR_CAPACITY, "sedef_filter: run buffer too small");
+    if (total == 0) return SEDEF_OK;
+  }
   // order runs by (i, o); the sweep emits each window's runs in j order
   uint64_t* keys = (uint64_t*)ctx_alloc(ctx, (size_t)total * 8);
   uint64_t* skeys = (uint64_t*)ctx_alloc(ctx, (size_t)total * 8);
@@ -1929,8 +2028,9 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   const int64_t* d_wbase = (const int64_t*)(d_up + ow);
   if (33 + wb <= 64) {
     SEDEF_KERNEL(ctx, "k_run_keys",
-                 k_run_keys<<<tb, 256, 0, st>>>(raw, total, a.qseq, nqseq, d_wbase, D.step, 0, keys));
-    SEDEF_TRY(radix_sort_u64(ctx, keys, nullptr, skeys, perm, total, 0, 33 + wb));
+                 k_run_keys<<<tb, 256, 0, st>>>(raw, total, a.qseq, nqseq, d_wbase, D.step, 0, keys,
+                                                druns));
+    SEDEF_TRY(radix_sort_u64(ctx, keys, nullptr, skeys, perm, total, 0, 33 + wb, druns));
   } else {
     // stable two-pass order: by j_a, then by (window, o)
     uint32_t* perm1 = (uint32_t*)ctx_alloc(ctx, (size_t)total * 4);
@@ -1938,16 +2038,20 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
     uint64_t* k2 = (uint64_t*)ctx_alloc(ctx, (size_t)total * 8);
     if (!perm1 || !perm2 || !k2) return SEDEF_ERR_OOM;
     SEDEF_KERNEL(ctx, "k_run_keys",
-                 k_run_keys<<<tb, 256, 0, st>>>(raw, total, a.qseq, nqseq, d_wbase, D.step, 1, keys));
-    SEDEF_TRY(radix_sort_u64(ctx, keys, nullptr, skeys, perm1, total, 0, 32));
+                 k_run_keys<<<tb, 256, 0, st>>>(raw, total, a.qseq, nqseq, d_wbase, D.step, 1, keys,
+                                                druns));
+    SEDEF_TRY(radix_sort_u64(ctx, keys, nullptr, skeys, perm1, total, 0, 32, druns));
     SEDEF_KERNEL(ctx, "k_run_keys",
-                 k_run_keys<<<tb, 256, 0, st>>>(raw, total, a.qseq, nqseq, d_wbase, D.step, 2, keys));
-    SEDEF_KERNEL(ctx, "k_permute_u64", k_permute_u64<<<tb, 256, 0, st>>>(keys, perm1, total, k2));
-    SEDEF_TRY(radix_sort_u64(ctx, k2, nullptr, skeys, perm2, total, 0, wb + 1));
+                 k_run_keys<<<tb, 256, 0, st>>>(raw, total, a.qseq, nqseq, d_wbase, D.step, 2, keys,
+                                                druns));
+    SEDEF_KERNEL(ctx, "k_permute_u64",
+                 k_permute_u64<<<tb, 256, 0, st>>>(keys, perm1, total, k2, druns));
+    SEDEF_TRY(radix_sort_u64(ctx, k2, nullptr, skeys, perm2, total, 0, wb + 1, druns));
     SEDEF_KERNEL(ctx, "k_compose_perm",
-                 k_compose_perm<<<tb, 256, 0, st>>>(perm1, perm2, total, perm));
+                 k_compose_perm<<<tb, 256, 0, st>>>(perm1, perm2, total, perm, druns));
   }
-  SEDEF_KERNEL(ctx, "k_gather_runs", k_gather_runs<<<tb, 256, 0, st>>>(raw, perm, total, runs));
+  SEDEF_KERNEL(ctx, "k_gather_runs",
+               k_gather_runs<<<tb, 256, 0, st>>>(raw, perm, total, runs, druns));
   // refine: lean kernel over all runs, then the large kernel over the runs
   // it handed over (their count stays on the device)
   uint32_t* big = (uint32_t*)ctx_alloc(ctx, (size_t)total * 4);
@@ -1959,6 +2063,8 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   ra.nq = nq;
   ra.trec = trec;
   ra.nt = nt;
+  ra.dnruns = druns;
+  ra.dnt = dnt;
   ra.toff = toff;
   ra.mtab = a.mtab;
   ra.span = D.span;
@@ -1970,7 +2076,7 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   if (!ranges) return SEDEF_ERR_OOM;
   SEDEF_KERNEL(ctx, "k_run_ranges",
                k_run_ranges<<<tb, 256, 0, st>>>(runs, total, a.qseq, nqseq, d_wbase, D.step, wqa, wqb,
-                                                trec, nt, D.span, ranges));
+                                                trec, nt, D.span, ranges, druns, dnt));
   ra.ranges = ranges;
   ra.next = counters + 6;
   SEDEF_CUDA(cudaMemsetAsync(counters + 6, 0, 16, st));
@@ -1988,6 +2094,7 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   SEDEF_KERNEL(ctx, "k_refine_big",
                k_refine<kMaxWindowRecs, 1024, false><<<ctx_sm_count(ctx), 32 * kRWarpsBig, big_sm,
                                                        st>>>(ra));
+  if (pl) return SEDEF_OK;
   SEDEF_CUDA(cudaMemcpyAsync(h_cnt, counters, 64, cudaMemcpyDeviceToHost, st));
   SEDEF_CUDA(cudaStreamSynchronize(st));
   {

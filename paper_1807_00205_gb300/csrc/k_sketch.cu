@@ -13,6 +13,8 @@
 // argmin when it differs from the previous window's (winnowing argmins are
 // non-decreasing, so this emits each selected position once, in order).  A
 // count pass and a write pass bracket a device scan of the per-tile counts.
+#include <cstring>
+
 #include "common.cuh"
 
 namespace sedef {
@@ -284,7 +286,7 @@ int scan_exclusive_u32(sedef_ctx* ctx, const uint32_t* in, uint32_t* out, int64_
 
 int run_sketch(sedef_ctx* ctx, const uint32_t* packed, const uint32_t* mask, const uint32_t* nbits,
                const int64_t* h_off, int nseq, const Derived& D, uint64_t* rec, int64_t cap,
-               int64_t* nrec) {
+               int64_t* nrec, Planned* pl) {
   cudaStream_t st = ctx_stream(ctx);
   const int64_t N = h_off[nseq];
   SketchArgs a;
@@ -303,8 +305,15 @@ int run_sketch(sedef_ctx* ctx, const uint32_t* packed, const uint32_t* mask, con
   uint32_t* cnt = (uint32_t*)ctx_alloc(ctx, (size_t)(a.ntiles + 1) * 4);
   uint32_t* toff = (uint32_t*)ctx_alloc(ctx, (size_t)(a.ntiles + 1) * 4);
   if (!d_off || !cnt || !toff) return SEDEF_ERR_OOM;
-  SEDEF_CUDA(cudaMemcpyAsync(d_off, h_off, (size_t)(nseq + 1) * 8, cudaMemcpyHostToDevice, st));
-  SEDEF_CUDA(cudaStreamSynchronize(st));  // h_off is caller memory: copy before returning
+  if (pl) {
+    int64_t* h = (int64_t*)host_buf(ctx, pl, (size_t)(nseq + 1) * 8);
+    if (!h) return SEDEF_ERR_OOM;
+    std::memcpy(h, h_off, (size_t)(nseq + 1) * 8);
+    SEDEF_CUDA(cudaMemcpyAsync(d_off, h, (size_t)(nseq + 1) * 8, cudaMemcpyHostToDevice, st));
+  } else {
+    SEDEF_CUDA(cudaMemcpyAsync(d_off, h_off, (size_t)(nseq + 1) * 8, cudaMemcpyHostToDevice, st));
+    SEDEF_CUDA(cudaStreamSynchronize(st));  // h_off is caller memory: copy before returning
+  }
   a.off = d_off;
   int64_t grid = a.ntiles;
   const int64_t maxgrid = (int64_t)ctx_sm_count(ctx) * 8;
@@ -312,6 +321,16 @@ int run_sketch(sedef_ctx* ctx, const uint32_t* packed, const uint32_t* mask, con
   SEDEF_KERNEL(ctx, "k_sketch_count",
                k_sketch<false><<<(int)grid, kSkThreads, 0, st>>>(a, cnt, nullptr, nullptr, 0));
   SEDEF_TRY(scan_exclusive_u32(ctx, cnt, toff, a.ntiles, toff + a.ntiles));
+  if (pl) {
+    // the write pass stores the records below the capacity; the exact
+    // total stays on the device
+    pl->n_rec = toff + a.ntiles;
+    SEDEF_TRY(plan_check(ctx, pl, toff + a.ntiles, cap, 0));
+    *nrec = cap;
+    SEDEF_KERNEL(ctx, "k_sketch_write",
+                 k_sketch<true><<<(int)grid, kSkThreads, 0, st>>>(a, nullptr, toff, rec, cap));
+    return SEDEF_OK;
+  }
   uint32_t* h_total = (uint32_t*)ctx_host(ctx, 8);
   if (!h_total) return SEDEF_ERR_OOM;
   SEDEF_CUDA(cudaMemcpyAsync(h_total, toff + a.ntiles, 4, cudaMemcpyDeviceToHost, st));

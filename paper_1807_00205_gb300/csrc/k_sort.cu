@@ -80,8 +80,10 @@ __device__ __forceinline__ uint32_t digit_of(uint64_t key, int shift, uint32_t d
 
 __global__ void __launch_bounds__(kRsThreads) k_rs_hist(const uint64_t* __restrict__ keys, int64_t n,
                                                         int shift, uint32_t dmask, int64_t ntiles,
-                                                        uint32_t* __restrict__ hist) {
+                                                        uint32_t* __restrict__ hist,
+                                                        const uint32_t* __restrict__ dn) {
   __shared__ uint32_t h[256];
+  n = live_n(n, dn);
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     __syncthreads();
     h[threadIdx.x] = 0;
@@ -112,8 +114,10 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* __res
                                                            uint32_t* __restrict__ vout, int64_t n,
                                                            int shift, uint32_t dmask, int64_t ntiles,
                                                            const uint32_t* __restrict__ hoff,
-                                                           int iota_vals) {
+                                                           int iota_vals,
+                                                           const uint32_t* __restrict__ dn) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  n = live_n(n, dn);
   RsSmem& S = *reinterpret_cast<RsSmem*>(smem_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool has_vals = (vout != nullptr);
@@ -188,7 +192,9 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const uint64_t* __res
 constexpr int kOffChunk = 4096;
 
 __global__ void __launch_bounds__(256) k_offsets(const uint64_t* __restrict__ sorted, int64_t n,
-                                                 int64_t nhash, uint32_t* __restrict__ off) {
+                                                 int64_t nhash, uint32_t* __restrict__ off,
+                                                 const uint32_t* __restrict__ dn) {
+  n = live_n(n, dn);
   __shared__ uint32_t cnt[kOffChunk];
   __shared__ int64_t rng[2];
   __shared__ int tmp[33];
@@ -248,7 +254,8 @@ int scan_exclusive_u32(sedef_ctx* ctx, const uint32_t* in, uint32_t* out, int64_
 }
 
 int radix_sort_u64(sedef_ctx* ctx, const uint64_t* keys_in, const uint32_t* vals_in,
-                   uint64_t* keys_out, uint32_t* vals_out, int64_t n, int bit_lo, int bit_hi) {
+                   uint64_t* keys_out, uint32_t* vals_out, int64_t n, int bit_lo, int bit_hi,
+                   const uint32_t* dn) {
   cudaStream_t st = ctx_stream(ctx);
   if (n <= 0) return SEDEF_OK;
   const int passes = (bit_hi - bit_lo + 7) / 8;
@@ -284,23 +291,24 @@ int radix_sort_u64(sedef_ctx* ctx, const uint64_t* keys_in, const uint32_t* vals
     uint64_t* kdst = to_out ? keys_out : ktmp;
     uint32_t* vdst = vals_out ? (to_out ? vals_out : vtmp) : nullptr;
     SEDEF_KERNEL(ctx, "k_rs_hist",
-                 k_rs_hist<<<(int)hgrid, kRsThreads, 0, st>>>(ksrc, n, shift, dmask, ntiles, hist));
+                 k_rs_hist<<<(int)hgrid, kRsThreads, 0, st>>>(ksrc, n, shift, dmask, ntiles, hist, dn));
     SEDEF_TRY(scan_exclusive_u32(ctx, hist, hoff, ntiles * 256, nullptr));
     SEDEF_KERNEL(ctx, "k_rs_scatter",
                  k_rs_scatter<<<(int)grid, kRsThreads, smem, st>>>(ksrc, vsrc, kdst, vdst, n, shift,
                                                                    dmask, ntiles, hoff,
-                                                                   (p == 0 && iota) ? 1 : 0));
+                                                                   (p == 0 && iota) ? 1 : 0, dn));
     ksrc = kdst;
     vsrc = vdst;
   }
   return SEDEF_OK;
 }
 
-int build_offsets(sedef_ctx* ctx, const uint64_t* sorted, int64_t n, int k, uint32_t* off) {
+int build_offsets(sedef_ctx* ctx, const uint64_t* sorted, int64_t n, int k, uint32_t* off,
+                  const uint32_t* dn) {
   cudaStream_t st = ctx_stream(ctx);
   const int64_t nhash = int64_t(1) << (2 * k);
   const int64_t chunks = (nhash + kOffChunk - 1) / kOffChunk;
-  SEDEF_KERNEL(ctx, "k_offsets", k_offsets<<<(int)chunks, 256, 0, st>>>(sorted, n, nhash, off));
+  SEDEF_KERNEL(ctx, "k_offsets", k_offsets<<<(int)chunks, 256, 0, st>>>(sorted, n, nhash, off, dn));
   return SEDEF_OK;
 }
 

@@ -400,3 +400,15 @@ def test_filter_window_subset_equals_full_rows():
     sub = oracle.filter_runs(recs, g.offsets, recs, g.offsets, pd, windows=win)
     assert len(sub) > 0
     assert np.array_equal(sub, full[np.isin(full[:, 0], win)])
+
+
+def test_filter_threads_do_not_change_rows():
+    """Windows are filtered independently: any number of threads gives the
+    same rows in the same order."""
+    g = synth.small_case(43, lengths=(50_000, 20_000), n_sd=5, mask_frac=0.15)
+    pd = oracle.params()
+    recs = oracle.sketch(g.seq, g.offsets, pd)
+    one = oracle.filter_runs(recs, g.offsets, recs, g.offsets, pd)
+    assert len(one) > 0
+    for t in (2, 5, 16):
+        assert np.array_equal(oracle.filter_runs(recs, g.offsets, recs, g.offsets, pd, threads=t), one)
