@@ -186,7 +186,9 @@ uint64_t sedef_launch_count(void);
  * Counters of the context's last sedef_filter call, out[0..n): query
  * windows, windows sent to the global-memory path, hits enumerated and hits
  * collected by the shared-memory path, runs, runs refined by the large
- * refine kernel (at most 8 values).
+ * refine kernel, hits of the global-memory path; out[7] = anchors of the
+ * context's last sedef_chain call (at most 8 values).  out[6] and out[7]
+ * are the totals a captured pass needs as capacities.
  */
 int sedef_filter_stats(sedef_ctx* ctx, int64_t* out, int32_t n);
 
@@ -343,6 +345,23 @@ int sedef_chain(sedef_ctx* ctx, const sedef_run_t* d_runs, int64_t nruns, const 
 int sedef_merge(sedef_ctx* ctx, const sedef_chain_t* d_chains, int64_t nchains,
                 const int64_t* h_qoff, int32_t nqseq, const int64_t* h_toff, int32_t ntseq,
                 const sedef_params* p, sedef_cand_t* d_cands, int64_t cap, int64_t* h_ncands);
+
+/*
+ * f3 (the q-gram filter of Section 3.2), applied to kept seeds: for run r
+ * with keep = 1, X = G[i, i+n) and Y = G[j_star, j_star+n) (reverse
+ * complement when o = 1); d_shared[r] = the q-grams X and Y share, counted
+ * with multiplicity (sum over q-grams of the smaller occurrence count;
+ * q-grams over a non-ACGT base are not counted); d_pass[r] = 1 when
+ * d_shared[r] >= the least integer >= B - 1e-9, where
+ * B = n (1 - delta_G - q delta_M) - (n p_gap + 1)(q - 1) is the paper's
+ * adapted q-gram lemma bound (p_gap: expected gaps per base).  Runs with
+ * keep = 0 get 0 and 0.  d_packed / d_nbits are sedef_pack's outputs for
+ * the nbases bases the runs refer to (global coordinates).  q in [1, 5].
+ * *h_npass = passing seeds.  Synchronizes.
+ */
+int sedef_qgram(sedef_ctx* ctx, const uint32_t* d_packed, const uint32_t* d_nbits, int64_t nbases,
+                const sedef_run_t* d_runs, int64_t nruns, const sedef_params* p, int32_t q,
+                double p_gap, uint32_t* d_shared, uint8_t* d_pass, int64_t* h_npass);
 
 /*
  * Whole self-search through host buffers: copies h_seq (total bytes

@@ -85,6 +85,13 @@ def _load():
             lib.orc_merge.argtypes = [vp, i64, i64, vp]
             lib.orc_jaccard.restype = ctypes.c_double
             lib.orc_jaccard.argtypes = [vp, i64, i64, i64, i32]
+            lib.orc_qgram_bound.restype = ctypes.c_double
+            lib.orc_qgram_bound.argtypes = [i64, i32, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double]
+            lib.orc_qgram_shared.restype = i64
+            lib.orc_qgram_shared.argtypes = [vp, i64, i64, i64, i32, i32]
+            lib.orc_qgram.restype = vp
+            lib.orc_qgram.argtypes = [vp, vp, i64, i64, vp, i32, ctypes.c_double]
             _lib = lib
     return _lib
 
@@ -225,6 +232,31 @@ def merge(chains: np.ndarray, p: dict) -> np.ndarray:
 def jaccard(seq: np.ndarray, i: int, j: int, n: int, k: int) -> float:
     seq = _c(seq, np.uint8)
     return float(_load().orc_jaccard(_ptr(seq), i, j, n, k))
+
+
+QGRAM_COLS = ["shared", "pass"]
+
+
+def qgram_bound(n: int, q: int, delta_g=0.10, delta_m=0.15, p_gap=0.005) -> float:
+    """Section 3.2's lower bound on the q-grams a pair within the SD error
+    model shares."""
+    return float(_load().orc_qgram_bound(n, q, delta_g, delta_m, p_gap))
+
+
+def qgram_shared(seq: np.ndarray, i: int, j: int, n: int, o: int, q: int) -> int:
+    """Q of G[i, i+n) and G[j, j+n) (reverse-complemented for o = 1)."""
+    seq = _c(seq, np.uint8)
+    return int(_load().orc_qgram_shared(_ptr(seq), i, j, n, o, q))
+
+
+def qgram(seq: np.ndarray, runs: np.ndarray, p: dict, q: int = 4, p_gap: float = 0.005) -> np.ndarray:
+    """f3: per run rows (shared q-grams, pass) of each kept seed (Section 3.2)."""
+    lib = _load()
+    seq = _c(seq, np.uint8)
+    runs = _c(runs, np.int64).reshape(-1, len(RUN_COLS))
+    h = lib.orc_qgram(_ptr(seq), _ptr(runs), len(runs), len(RUN_COLS), _ptr(_par_array(p)),
+                      int(q), float(p_gap))
+    return _table(lib, h)
 
 
 def selfsearch(seq, offsets, p: dict, threads: int = 1):

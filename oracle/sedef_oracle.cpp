@@ -30,12 +30,14 @@
 // copy + free) so that the Python test harness can read them with ctypes.
 
 #include <algorithm>
+#include <cctype>
 #include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <map>
 #include <set>
+#include <string>
 #include <thread>
 #include <tuple>
 #include <vector>
@@ -729,6 +731,82 @@ double orc_jaccard(const uint8_t* seq, int64_t i, int64_t j, int64_t n, int k) {
   int64_t inter = 0;
   for (auto& x : X) inter += Y.count(x);
   return (double)inter / (double)(X.size() + Y.size() - inter);
+}
+
+// ---- f3 q-gram filter (Section 3.2) -------------------------------------------
+// Q(X, Y): the q-grams X and Y share, counted with multiplicity (for every
+// q-gram the smaller of its two occurrence counts, summed).  Case does not
+// matter; a q-gram holding a base other than ACGT is not counted.  For a
+// seed (i, j*, o) X = G[i, i+n) and Y = G[j*, j*+n), reverse-complemented
+// when o = 1.  Section 3.2's adapted q-gram lemma: a pair within the SD error
+// model shares at least B = n (1 - delta_G - q delta_M) - (n p_G + 1)(q - 1)
+// q-grams (n <= m); the pair passes when Q >= the least integer >= B - 1e-9.
+// Rows per run: Q, pass (0, 0 for runs that are not kept seeds).
+double orc_qgram_bound(int64_t n, int q, double delta_g, double delta_m, double p_gap) {
+  return (double)n * (1.0 - delta_g - (double)q * delta_m) -
+         ((double)n * p_gap + 1.0) * (double)(q - 1);
+}
+
+static std::string upper_window(const uint8_t* seq, int64_t a, int64_t n, bool revcomp) {
+  std::string x(seq + a, seq + a + n);
+  for (char& c : x) c = (char)std::toupper((unsigned char)c);
+  if (revcomp) {
+    std::reverse(x.begin(), x.end());
+    for (char& c : x) {
+      switch (c) {
+        case 'A': c = 'T'; break;
+        case 'C': c = 'G'; break;
+        case 'G': c = 'C'; break;
+        case 'T': c = 'A'; break;
+        default: c = 'N';
+      }
+    }
+  }
+  return x;
+}
+
+static std::map<std::string, int64_t> qgram_counts(const std::string& x, int q) {
+  std::map<std::string, int64_t> c;
+  for (size_t a = 0; a + q <= x.size(); ++a) {
+    std::string g = x.substr(a, q);
+    if (g.find_first_not_of("ACGT") != std::string::npos) continue;
+    c[g] += 1;
+  }
+  return c;
+}
+
+int64_t orc_qgram_shared(const uint8_t* seq, int64_t i, int64_t j, int64_t n, int o, int q) {
+  auto cx = qgram_counts(upper_window(seq, i, n, false), q);
+  auto cy = qgram_counts(upper_window(seq, j, n, o != 0), q);
+  int64_t shared = 0;
+  for (auto& kv : cx) {
+    auto it = cy.find(kv.first);
+    if (it != cy.end()) shared += std::min(kv.second, it->second);
+  }
+  return shared;
+}
+
+void* orc_qgram(const uint8_t* seq, const int64_t* runs, int64_t nruns, int64_t run_cols,
+                const int64_t* par, int q, double p_gap) {
+  Par P = read_par(par);
+  const double B = orc_qgram_bound(P.n, q, P.delta_g, P.delta_m, p_gap);
+  int64_t need = (int64_t)std::ceil(B - 1e-9);
+  while ((double)need < B - 1e-9) ++need;
+  while ((double)(need - 1) >= B - 1e-9) --need;
+  if (need < 0) need = 0;
+  Table* T = new Table();
+  T->ncols = 2;
+  for (int64_t r = 0; r < nruns; ++r) {
+    const int64_t* R = runs + r * run_cols;
+    const int64_t i = R[0], o = R[1], jstar = R[9], keep = R[11];
+    if (!keep) {
+      T->row({0, 0});
+      continue;
+    }
+    const int64_t Q = orc_qgram_shared(seq, i, jstar, P.n, (int)o, q);
+    T->row({Q, Q >= need ? 1 : 0});
+  }
+  return T;
 }
 
 }  // extern "C"

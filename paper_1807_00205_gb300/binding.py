@@ -43,7 +43,8 @@ EXPORTS = ["sedef_default_params", "sedef_last_error", "sedef_create", "sedef_de
            "sedef_index", "sedef_filter", "sedef_filter_autotune", "sedef_filter_variant",
            "sedef_chain", "sedef_merge", "sedef_selfsearch_host", "sedef_index_blob_size",
            "sedef_index_save", "sedef_index_blob_info", "sedef_index_load", "sedef_graph_create",
-           "sedef_graph_launch", "sedef_graph_wait", "sedef_graph_nodes", "sedef_graph_destroy"]
+           "sedef_graph_launch", "sedef_graph_wait", "sedef_graph_nodes", "sedef_graph_destroy",
+           "sedef_qgram"]
 
 CAP_NAMES = ["records", "slow_hits", "runs", "anchors", "chains", "cands"]
 
@@ -94,6 +95,8 @@ def load(build_if_missing: bool = True):
     lib.sedef_index_load.argtypes = [vp, vp, i64, vp, i32, vp, vp, vp, i64]
     lib.sedef_graph_create.argtypes = [vp, vp, vp, i32, P, ctypes.POINTER(GraphCaps), vp, vp, vp,
                                        vp, vp, vp, ctypes.POINTER(vp)]
+    lib.sedef_qgram.argtypes = [vp, vp, vp, i64, vp, i64, P, i32, ctypes.c_double, vp, vp,
+                                ctypes.POINTER(i64)]
     lib.sedef_graph_launch.argtypes = [vp, vp]
     lib.sedef_graph_wait.argtypes = [vp, vp]
     lib.sedef_graph_nodes.restype = i64
@@ -213,7 +216,8 @@ class Context:
     def sedef_filter_stats(self) -> dict:
         v = np.zeros(8, dtype=np.int64)
         _check(self.lib.sedef_filter_stats(self.handle, v.ctypes.data, 8))
-        keys = ["windows", "overflow_windows", "hits", "collected", "runs", "big_refine"]
+        keys = ["windows", "overflow_windows", "hits", "collected", "runs", "big_refine",
+                "slow_hits", "anchors"]
         return {k: int(x) for k, x in zip(keys, v)}
 
     @staticmethod
@@ -332,6 +336,18 @@ class Context:
                                     len(qo) - 1, to.ctypes.data, len(to) - 1, ctypes.byref(p),
                                     _ptr(cands), cap, ctypes.byref(count)))
         return cands[:count.value * CAND_DTYPE.itemsize], count.value
+
+    def sedef_qgram(self, packed, nbits, nbases: int, runs, nruns: int, p: Params, q: int = 4,
+                    p_gap: float = 0.005):
+        """f3: (shared q-grams per run (int32 view of u32), pass flags (uint8), passing count)."""
+        t = self.torch
+        shared = self._empty(nruns, t.int32)
+        ok = self._empty(nruns, t.uint8)
+        npass = ctypes.c_int64()
+        _check(self.lib.sedef_qgram(self.handle, _ptr(packed), _ptr(nbits), int(nbases), _ptr(runs),
+                                    int(nruns), ctypes.byref(p), int(q), float(p_gap), _ptr(shared),
+                                    _ptr(ok), ctypes.byref(npass)))
+        return shared[:nruns], ok[:nruns], npass.value
 
     def sedef_selfsearch_host(self, seq: np.ndarray, offsets, p: Params, cap=None):
         seq = np.ascontiguousarray(seq, dtype=np.uint8)
@@ -455,11 +471,19 @@ class Graph:
             pass
 
 
+def caps_from_run(out: dict, stats: dict, slack: float = 1.25) -> dict:
+    """Capacities for a captured pass from an eager pass over the same kind
+    of input (its counts and the context's statistics) times `slack`."""
+    need = {"records": out["rec"].numel(), "slow_hits": stats["slow_hits"], "runs": out["nruns"],
+            "anchors": stats["anchors"], "chains": out["nchains"], "cands": out["ncands"]}
+    return {k: int(v * slack) + 1024 for k, v in need.items()}
+
+
 def default_caps(n_bases: int) -> dict:
     """First-guess capacities for a pass over n_bases bases (a graph that
     overflows is rebuilt from the reported totals)."""
-    return {"records": n_bases // 4 + 1024, "slow_hits": n_bases // 2 + (1 << 20),
-            "runs": n_bases // 32 + 4096, "anchors": n_bases // 2 + (1 << 16),
+    return {"records": n_bases // 4 + 1024, "slow_hits": n_bases // 16 + (1 << 20),
+            "runs": n_bases // 32 + 4096, "anchors": n_bases // 8 + (1 << 16),
             "chains": n_bases // 32 + 4096, "cands": n_bases // 32 + 4096}
 
 

@@ -124,8 +124,9 @@ int ctx_filter_variant(sedef_ctx* ctx) { return ctx->filter_variant; }
 void ctx_set_filter_variant(sedef_ctx* ctx, int v) { ctx->filter_variant = v; }
 
 void ctx_set_stats(sedef_ctx* ctx, const int64_t* v, int n) {
-  for (int x = 0; x < 8; ++x) ctx->filter_stats[x] = x < n ? v[x] : 0;
+  for (int x = 0; x < 7; ++x) ctx->filter_stats[x] = x < n ? v[x] : 0;
 }
+void ctx_set_anchor_total(sedef_ctx* ctx, int64_t a) { ctx->filter_stats[7] = a; }
 int ctx_device(sedef_ctx* ctx) { return ctx->device; }
 int ctx_sm_count(sedef_ctx* ctx) { return ctx->sm_count; }
 

@@ -248,6 +248,7 @@ void* ctx_host(sedef_ctx* ctx, size_t bytes);  // pinned host scratch
 int ctx_device(sedef_ctx* ctx);
 int ctx_sm_count(sedef_ctx* ctx);
 void ctx_set_stats(sedef_ctx* ctx, const int64_t* v, int n);  // last sedef_filter call
+void ctx_set_anchor_total(sedef_ctx* ctx, int64_t a);         // last sedef_chain call
 int ctx_filter_variant(sedef_ctx* ctx);
 void ctx_set_filter_variant(sedef_ctx* ctx, int v);
 }  // namespace sedef

@@ -555,6 +555,7 @@ int run_chain(sedef_ctx* ctx, const sedef_run_t* runs, int64_t nruns, const uint
     SEDEF_CUDA(cudaMemcpyAsync(h_tot + 1, amax, 4, cudaMemcpyDeviceToHost, st));
     SEDEF_CUDA(cudaStreamSynchronize(st));
     A = *h_tot;
+    ctx_set_anchor_total(ctx, A);
     // refuse instead of running for hours
     if (h_tot[1] > (uint32_t)kMaxChainAnchors)
       return fail(SEDEF_ERR_UNSUPPORTED,

@@ -1890,7 +1890,7 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   }
 
   unsigned long long* h_cnt = nullptr;
-  int64_t nov = 0;
+  int64_t nov = 0, slow_hits_total = 0;
   if (pl) {
     // planned: the global path over the live overflow list in one batch of
     // at most pl->slow_hits hits
@@ -1958,6 +1958,7 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
     unsigned long long* d_base = (unsigned long long*)ctx_alloc(ctx, (size_t)(nov + 1) * 8);
     if (!d_base) return SEDEF_ERR_OOM;
     SEDEF_CUDA(cudaMemcpyAsync(d_base, base.data(), (size_t)(nov + 1) * 8, cudaMemcpyHostToDevice, st));
+    slow_hits_total = (int64_t)base[nov];
     const unsigned long long budget = 1ull << 27;  // hits per batch
     int64_t v0 = 0;
     while (v0 < nov) {
@@ -2098,9 +2099,9 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   SEDEF_CUDA(cudaMemcpyAsync(h_cnt, counters, 64, cudaMemcpyDeviceToHost, st));
   SEDEF_CUDA(cudaStreamSynchronize(st));
   {
-    const int64_t stats[8] = {nwin, nov, (int64_t)h_cnt[4], (int64_t)h_cnt[5], total,
-                              (int64_t)(h_cnt[3] & 0xFFFFFFFFull), 0, 0};
-    ctx_set_stats(ctx, stats, 8);
+    const int64_t stats[7] = {nwin, nov, (int64_t)h_cnt[4], (int64_t)h_cnt[5], total,
+                              (int64_t)(h_cnt[3] & 0xFFFFFFFFull), slow_hits_total};
+    ctx_set_stats(ctx, stats, 7);
   }
   SEDEF_CUDA(cudaStreamSynchronize(st));
   return SEDEF_OK;

@@ -74,19 +74,27 @@ def check_candidate_properties(chains: np.ndarray, cands: np.ndarray):
     comp = (g_sorted.astype(np.float64) * 2.0**33) + c_sorted[:, ci["q0"]]
     want = (grp_h.astype(np.float64) * 2.0**33) + chains[:, hi["q0"]]
     top = np.searchsorted(comp, want, side="right") - 1
-    found = np.zeros(len(chains), dtype=bool)
-    for back in range(256):
-        k = top - back
-        ok = k >= 0
+    # look back from each chain over its group's candidates (q0 <= the
+    # chain's q0), only for the chains not yet placed
+    todo = np.arange(len(chains))
+    stuck = [np.zeros(0, dtype=np.int64)]
+    for back in range(8192):
+        if len(todo) == 0:
+            break
+        k = top[todo] - back
+        ok = (k >= 0) & (g_sorted[np.maximum(k, 0)] == grp_h[todo])
         kk = np.where(ok, k, 0)
         c = c_sorted[kk]
-        inside = (ok & ~found & (g_sorted[kk] == grp_h)
-                  & (c[:, ci["q0"]] <= chains[:, hi["q0"]]) & (c[:, ci["q1"]] >= chains[:, hi["q1"]])
-                  & (c[:, ci["t0"]] <= chains[:, hi["t0"]]) & (c[:, ci["t1"]] >= chains[:, hi["t1"]]))
-        found |= inside
-        if found.all():
-            break
-    for x in np.nonzero(~found)[0]:  # the rare chain far from its container
+        h = chains[todo]
+        inside = (ok & (c[:, ci["q0"]] <= h[:, hi["q0"]]) & (c[:, ci["q1"]] >= h[:, hi["q1"]])
+                  & (c[:, ci["t0"]] <= h[:, hi["t0"]]) & (c[:, ci["t1"]] >= h[:, hi["t1"]]))
+        stuck.append(todo[~ok])  # left its group without a container
+        todo = todo[ok & ~inside]
+    stuck = np.concatenate(stuck + [todo])
+    # unplaced chains (none left in practice): a seeded sample of them, each
+    # against every candidate of its group
+    rng = np.random.default_rng(0)
+    for x in rng.permutation(stuck)[:300]:
         c = cands
         inside = ((grp_c == grp_h[x]) & (c[:, ci["q0"]] <= chains[x, hi["q0"]])
                   & (c[:, ci["q1"]] >= chains[x, hi["q1"]]) & (c[:, ci["t0"]] <= chains[x, hi["t0"]])

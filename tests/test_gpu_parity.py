@@ -294,3 +294,30 @@ def test_every_filter_shape_gives_the_same_runs(ctx):
     chosen = ctx.sedef_filter_autotune(rec, g.offsets, rec, srt, off, g.offsets, p)
     assert 0 <= chosen < count and ctx.sedef_filter_variant()[0] == chosen
     ctx.sedef_filter_variant(0)
+
+
+# ------------------------------------------------------- f3 q-gram filter ----
+
+@pytest.mark.parametrize("q", [1, 3, 4, 5])
+def test_qgram_filter(ctx, q):
+    """Shared q-grams and pass flags of every kept seed equal the oracle's
+    (masked bases, N runs, both orientations, several sequences)."""
+    g = synth.small_case(71 + q, lengths=(90_000, 40_000, 5_000), n_sd=6, sd_lo=1500, sd_hi=9000,
+                         id_lo=0.78, mask_frac=0.2, n_gaps=True)
+    pd = oracle.params()
+    p = binding.params_from_dict(pd)
+    recs = oracle.sketch(g.seq, g.offsets, pd)
+    runs = oracle.filter_runs(recs, g.offsets, recs, g.offsets, pd)
+    want = oracle.qgram(g.seq, runs, pd, q=q, p_gap=0.005)
+    d = to_dev(g.seq)
+    packed, mask, nbits = ctx.sedef_pack(d)
+    rec = ctx.sedef_sketch(packed, mask, nbits, g.offsets, p)
+    srt, off = ctx.sedef_index(rec, p)
+    druns, nr = ctx.sedef_filter(rec, g.offsets, rec, srt, off, g.offsets, p)
+    assert_rows_equal(run_rows(druns), runs, "runs")
+    shared, ok, npass = ctx.sedef_qgram(packed, nbits, g.length, druns, nr, p, q=q, p_gap=0.005)
+    got = np.stack([shared.cpu().numpy().view(np.uint32).astype(np.int64),
+                    ok.cpu().numpy().astype(np.int64)], axis=1)
+    assert_rows_equal(got, want, f"q-gram rows (q={q})")
+    assert npass == int(want[:, 1].sum())
+    assert (runs[:, oracle.RUN_COLS.index("keep")] == 1).sum() > 0

@@ -3,8 +3,29 @@ through the continuously batched server with overlapping workers."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1807_00205_gb300 import binding, serve, synth
-from tests.gpu_helpers import need_gpu
+from tests.gpu_helpers import assert_rows_equal, need_gpu
+
+
+def oracle_cands(q: np.ndarray, g, recs_t) -> np.ndarray:
+    """The oracle's non-self search of one query region against the genome,
+    as rows in global coordinates (the query is its own one-sequence input)."""
+    pd = oracle.params(self_mode=0)
+    qoff = np.array([0, len(q)], dtype=np.int64)
+    tq = oracle.sketch(q, qoff, pd)
+    runs = oracle.filter_runs(tq, qoff, recs_t, g.offsets, pd)
+    chains = oracle.chain(runs, tq, qoff, recs_t, g.offsets, pd)
+    return oracle.merge(chains, pd)
+
+
+def served_rows(c: np.ndarray, g) -> np.ndarray:
+    if len(c) == 0:
+        return np.zeros((0, len(oracle.CAND_COLS)), dtype=np.int64)
+    to = g.offsets
+    return np.stack([c["qseq"], c["q0"], c["q1"], c["tseq"], c["t0"] + to[c["tseq"]],
+                     c["t1"] + to[c["tseq"]], c["o"], c["score"], c["nchains"]],
+                    axis=1).astype(np.int64)
 
 pytestmark = pytest.mark.gpu
 
@@ -26,6 +47,11 @@ def test_results_same_alone_and_in_the_mix():
     for a, r in zip(alone, mix):
         assert np.array_equal(a, r.cands)
     assert sum(len(a) for a in alone) > 0
+    # served results are the oracle's non-self search of each region
+    recs_t = oracle.sketch(g.seq, g.offsets, oracle.params(self_mode=0))
+    for k in range(0, len(pool), 3):
+        assert_rows_equal(served_rows(alone[k], g), oracle_cands(pool[k], g, recs_t),
+                          f"request {k}")
     srv = serve.Server(index, p, workers=2, batching=True)
     srv.start()
     res = serve.run_load(srv, pool, rate=2000.0, count=28, seed=1)

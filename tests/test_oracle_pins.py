@@ -412,3 +412,85 @@ def test_filter_threads_do_not_change_rows():
     assert len(one) > 0
     for t in (2, 5, 16):
         assert np.array_equal(oracle.filter_runs(recs, g.offsets, recs, g.offsets, pd, threads=t), one)
+
+
+# ---------------------------------------------------------- f3 q-gram filter --
+
+def test_qgram_bound_reduces_to_the_q_gram_lemma():
+    """Section 3.2's bound with no gaps (delta_G = 0, p_G = 0) is the classic
+    q-gram lemma: strings of length n at e substitutions share at least
+    n - q + 1 - q e q-grams (Jokinen and Ukkonen); with the defaults it gives
+    211 (q = 4) and 94 (q = 5) at n = 750 after rounding up."""
+    for n, q, e in [(750, 4, 10), (1000, 3, 0), (100, 5, 7), (750, 1, 112)]:
+        assert abs(oracle.qgram_bound(n, q, 0.0, e / n, 0.0) - (n - q + 1 - q * e)) < 1e-9
+    assert math.ceil(oracle.qgram_bound(750, 4) - 1e-9) == 211
+    assert math.ceil(oracle.qgram_bound(750, 5) - 1e-9) == 94
+    # q = 1 has no overlap term: n (1 - delta_G - delta_M)
+    assert abs(oracle.qgram_bound(750, 1) - 750 * 0.75) < 1e-9
+
+
+def test_qgram_shared_special_cases():
+    rng = np.random.default_rng(3)
+    x = synth.random_bases(rng, 300)
+    s = np.concatenate([x, x, synth.reverse_complement(x)])
+    n = 300
+    for q in (1, 2, 4, 5):
+        assert oracle.qgram_shared(s, 0, 300, n, 0, q) == n - q + 1      # identical
+        assert oracle.qgram_shared(s, 0, 600, n, 1, q) == n - q + 1      # reverse complement
+    lower = np.frombuffer(bytes(x).lower(), dtype=np.uint8)
+    s2 = np.concatenate([x, lower])
+    assert oracle.qgram_shared(s2, 0, 300, n, 0, 4) == n - 4 + 1  # case is ignored
+    # one N removes the q q-grams over it
+    y = x.copy()
+    y[150] = ord("N")
+    s3 = np.concatenate([x, y])
+    assert oracle.qgram_shared(s3, 0, 300, n, 0, 4) == n - 4 + 1 - 4
+    # disjoint and multiplicity examples worked by hand
+    s4 = np.frombuffer(b"AAAAAAAACCCCCCCC", dtype=np.uint8)
+    assert oracle.qgram_shared(s4, 0, 8, 8, 0, 3) == 0
+    s5 = np.frombuffer(b"ACGTACGTACACACGG", dtype=np.uint8)
+    # q = 2: X has AC x2, CG x2, GT x2, TA x1; Y has AC x3, CA x2, CG x1, GG x1
+    assert oracle.qgram_shared(s5, 0, 8, 8, 0, 2) == 2 + 1
+
+
+def test_qgram_lemma_holds_under_the_error_model():
+    """Pairs within the SD error model never fall below the bound: Y is X
+    with e substitutions and g gaps (total gap length <= delta_G n), cut to
+    n bases; Q(X, Y) >= n (1 - delta_G - q e/n) - (g + 1)(q - 1)."""
+    rng = np.random.default_rng(11)
+    n = 750
+    for trial in range(60):
+        x = synth.random_bases(rng, n + 200)
+        y = x.copy()
+        e = int(rng.integers(0, 113))
+        pos = rng.choice(n, size=e, replace=False)
+        y[pos] = synth._ACGT[(np.searchsorted(synth._ACGT, y[pos]) + rng.integers(1, 4, e)) % 4]
+        g = int(rng.integers(0, 6))
+        budget = int(0.10 * n)
+        for _ in range(g):
+            ln = int(rng.integers(1, max(2, budget // max(g, 1)) + 1))
+            at = int(rng.integers(10, n - 10))
+            if rng.random() < 0.5:
+                y = np.delete(y, np.arange(at, at + ln))
+            else:
+                y = np.insert(y, at, synth._ACGT[rng.integers(0, 4, ln)])
+        s = np.concatenate([x[:n], y[:n]])
+        for q in (3, 4, 5):
+            got = oracle.qgram_shared(s, 0, n, n, 0, q)
+            assert got >= n * (1 - 0.10 - q * e / n) - (g + 1) * (q - 1) - 1e-9, (trial, q, got)
+
+
+def test_qgram_rows_follow_the_threshold():
+    g = synth.small_case(44, lengths=(60_000,), n_sd=4, sd_lo=2000, sd_hi=6000, id_lo=0.8)
+    pd = oracle.params()
+    recs = oracle.sketch(g.seq, g.offsets, pd)
+    runs = oracle.filter_runs(recs, g.offsets, recs, g.offsets, pd)
+    rows = oracle.qgram(g.seq, runs, pd, q=4)
+    need = math.ceil(oracle.qgram_bound(750, 4) - 1e-9)
+    keep = runs[:, oracle.RUN_COLS.index("keep")] == 1
+    assert keep.sum() > 0 and len(rows) == len(runs)
+    assert (rows[~keep] == 0).all()
+    assert np.array_equal(rows[keep, 1], (rows[keep, 0] >= need).astype(np.int64))
+    for r in np.nonzero(keep)[0][:10]:
+        i, o, js = runs[r, 0], runs[r, 1], runs[r, oracle.RUN_COLS.index("j_star")]
+        assert rows[r, 0] == oracle.qgram_shared(g.seq, i, js, 750, o, 4)
