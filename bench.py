@@ -365,7 +365,7 @@ def serve_arm(args):
         row = {"rate": rate}
         for mode, workers, batching in [("served", 2, True), ("plain", 1, False)]:
             srv = serve.Server(index, p, workers=workers, batching=batching, device=local)
-            srv.warm(pool[:2])
+            srv.warm(pool[:8])
             srv.start()
             row[mode] = serve.run_load(srv, pool, rate, args.requests, seed=int(rate))
             srv.close()

@@ -576,6 +576,276 @@ __global__ void __launch_bounds__(TPB) k_filter_fast(FArgs a, TierIO io) {
   }
 }
 
+// ------------------------------------------------------------- warp tier --
+//
+// Small windows (at most 128 query records, 4,096 hits, 256 collected hits
+// and 64 dense groups) take the same steps as k_filter_fast with one warp
+// per window and no block barriers: W_Q by a warp bitonic sort, hits by
+// binary search over the posting prefix sums, (bin, o) counters as the
+// prefilter, collected hits sorted per strand, dense groups found by the warp
+// and swept exactly by lane 0.  Windows past any limit go to the next tier.
+
+constexpr int kWQ = 128;        // query records
+constexpr int kWSlots = 1024;   // (bin, o) 16-bit counters (512 bins)
+constexpr int kWL = 256;        // collected hits
+constexpr int kWG = 64;         // dense groups
+constexpr int kWH = 4096;       // enumerated hits
+constexpr int kWWarps = 8;
+
+struct WarpSmem {
+  uint32_t qkey[kWQ];
+  uint32_t pst[kWQ];
+  uint32_t plen[kWQ];
+  uint32_t pre[kWQ + 1];
+  uint8_t dm[kWQ];
+  uint32_t slots[kWSlots / 2];
+  unsigned long long hits[kWL];
+  uint32_t glo[kWG];
+  uint32_t ghi[kWG];
+  uint16_t cnt[kWQ];
+  int nhit;
+};
+
+template <typename T>
+__device__ void warp_sort(T* v, int n) {  // n a power of two
+  const int lane = lane_id();
+  for (int size = 2; size <= n; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = lane; t < (n >> 1); t += 32) {
+        const int lo = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));
+        const int hi = lo + stride;
+        const bool asc = (lo & size) == 0;
+        const T x = v[lo], y = v[hi];
+        if ((x > y) == asc) {
+          v[lo] = y;
+          v[hi] = x;
+        }
+      }
+      __syncwarp();
+    }
+}
+
+__device__ __forceinline__ uint32_t wslot_of(uint32_t t, uint32_t o) {
+  return (((t >> kBinShift) << 1) | o) & (kWSlots - 1);
+}
+
+__global__ void __launch_bounds__(32 * kWWarps) k_filter_warp(FArgs a, TierIO io) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  WarpSmem& S = reinterpret_cast<WarpSmem*>(smem_raw)[warp];
+  for (int x = lane; x < kWQ; x += 32) S.cnt[x] = 0;
+  const int64_t count = io.in_list ? (int64_t)*io.in_count : a.nwin;
+  auto hand_over = [&](int64_t wdx) {
+    if (lane == 0) io.out_list[atomicAdd(io.out_count, 1u)] = (uint32_t)wdx;
+  };
+  while (true) {
+    int64_t k = 0;
+    if (lane == 0) k = (int64_t)atomicAdd(io.next, 1u);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    if (k >= count) break;
+    const int64_t wdx = io.in_list ? (int64_t)io.in_list[k] : k;
+    const int64_t i = a.win_i[wdx];
+    const uint32_t qa = a.win_qa[wdx], qb = a.win_qb[wdx];
+    const int c = (int)(qb - qa);
+    if (c == 0) continue;
+    if (c > kWQ) {
+      hand_over(wdx);
+      continue;
+    }
+    const int np = next_pow2(c < 2 ? 2 : c);
+    for (int x = lane; x < np; x += 32) {
+      uint32_t key = kNone;
+      if (x < c) {
+        const uint64_t r = __ldg(a.qrec + qa + x);
+        key = (rec_hash(r) << 1) | rec_strand(r);
+      }
+      S.qkey[x] = key;
+    }
+    __syncwarp();
+    warp_sort(S.qkey, np);
+    // distinct hashes in sorted order (the order build_wq gives)
+    int64_t seq_lo = 0, seq_hi = 0;
+    if (a.self_mode == 2) {
+      const int sq = a.win_seq[wdx];
+      seq_lo = a.tseq[sq];
+      seq_hi = a.tseq[sq + 1];
+    }
+    int s = 0;
+    for (int base = 0; base < c; base += 32) {
+      const int x = base + lane;
+      bool keep = false;
+      uint32_t st = 0, len = 0, mask = 0;
+      if (x < c) {
+        const uint32_t h = S.qkey[x] >> 1;
+        if (x == 0 || (S.qkey[x - 1] >> 1) != h) {
+          for (int y = x; y < c && (S.qkey[y] >> 1) == h; ++y) mask |= 1u << (S.qkey[y] & 1u);
+          st = a.toff[h];
+          len = a.toff[h + 1] - st;
+          keep = !(a.max_occ > 0 && (int)len > a.max_occ);
+          if (keep && a.self_mode == 2) posting_window(a.tsorted, &st, &len, seq_lo, seq_hi);
+        }
+      }
+      const unsigned km = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        const int d = s + __popc(km & lanemask_lt());
+        S.pst[d] = st;
+        S.plen[d] = len;
+        S.dm[d] = (uint8_t)mask;
+      }
+      s += __popc(km);
+    }
+    __syncwarp();
+    if (s == 0) continue;
+    // prefix sums of the posting lengths
+    uint32_t run = 0;
+    for (int base = 0; base < s; base += 32) {
+      const int x = base + lane;
+      const uint32_t v = x < s ? S.plen[x] : 0u;
+      const uint32_t inc = warp_inclusive_sum(v);
+      if (x < s) S.pre[x] = run + inc - v;
+      run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) S.pre[s] = run;
+    const uint32_t H = run;
+    if (H == 0) continue;
+    if (H > (uint32_t)kWH) {
+      hand_over(wdx);
+      continue;
+    }
+    const int m = a.mtab[s];
+    for (int x = lane; x < kWSlots / 2; x += 32) S.slots[x] = 0;
+    if (lane == 0) S.nhit = 0;
+    __syncwarp();
+    auto each_hit = [&](auto f) {
+      for (int e = lane; e < (int)H; e += 32) {
+        int lo = 0, hi = s;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if ((int)S.pre[mid] <= e) lo = mid; else hi = mid;
+        }
+        const uint64_t r = __ldg(a.tsorted + S.pst[lo] + (uint32_t)(e - (int)S.pre[lo]));
+        const uint32_t t = rec_pos(r), st = rec_strand(r);
+        if (a.self_mode && (int64_t)t >= i && (int64_t)t <= i + a.span) continue;
+        const uint32_t qm = S.dm[lo];
+        if ((qm >> st) & 1u) f(t, (uint32_t)lo, 0u);
+        if ((qm >> (st ^ 1u)) & 1u) f(t, (uint32_t)lo, 1u);
+      }
+    };
+    each_hit([&](uint32_t t, uint32_t, uint32_t o) {
+      const uint32_t sl = wslot_of(t, o);
+      atomicAdd(&S.slots[sl >> 1], 1u << ((sl & 1) * 16));
+    });
+    __syncwarp();
+    each_hit([&](uint32_t t, uint32_t hid, uint32_t o) {
+      const uint32_t b = t >> kBinShift;
+      const uint32_t c0 = slot_count(S.slots, wslot_of(t, o));
+      const uint32_t cn = slot_count(S.slots, (((b + 1) << 1) | o) & (kWSlots - 1));
+      bool need = c0 + cn >= (uint32_t)m;
+      if (!need && b > 0) {
+        const uint32_t cp = slot_count(S.slots, (((b - 1) << 1) | o) & (kWSlots - 1));
+        need = cp + c0 >= (uint32_t)m;
+      }
+      if (need) {
+        const int at = atomicAdd(&S.nhit, 1);
+        if (at < kWL)
+          S.hits[at] = ((unsigned long long)o << 63) | ((unsigned long long)t << 20) | hid;
+      }
+    });
+    __syncwarp();
+    const int L = S.nhit;
+    if (L > kWL) {
+      hand_over(wdx);
+      continue;
+    }
+    if (L < m) {
+      if (io.stats && lane == 0) {
+        atomicAdd(a.stats + 0, (unsigned long long)H);
+        atomicAdd(a.stats + 1, (unsigned long long)L);
+      }
+      continue;
+    }
+    const int nh = next_pow2(L < 2 ? 2 : L);
+    for (int x = L + lane; x < nh; x += 32) S.hits[x] = ~0ull;
+    __syncwarp();
+    warp_sort(S.hits, nh);
+    int split;
+    {
+      int lo2 = 0, hi2 = L;  // first hit with o = 1
+      while (lo2 < hi2) {
+        const int mid = (lo2 + hi2) >> 1;
+        if ((S.hits[mid] >> 63) == 0) lo2 = mid + 1; else hi2 = mid;
+      }
+      split = lo2;
+    }
+    int ng = 0, ng0 = 0;
+    for (int o = 0; o < 2; ++o) {
+      const unsigned long long* base = S.hits + (o ? split : 0);
+      const int64_t cnt = o ? L - split : split;
+      find_groups(
+          [&](int64_t x) {
+            const unsigned long long h = base[x];
+            return make_uint2((uint32_t)(h >> 20), (uint32_t)(h & 0xFFFFFu));
+          },
+          cnt, m, a.span, [&](int64_t lo, int64_t hi) {
+            if (lane == 0 && ng < kWG) {
+              S.glo[ng] = (uint32_t)(lo < 0 ? 0 : lo);
+              S.ghi[ng] = (uint32_t)hi;
+            }
+            ++ng;
+          });
+      if (o == 0) ng0 = ng;
+    }
+    __syncwarp();
+    if (ng > kWG) {
+      hand_over(wdx);
+      continue;
+    }
+    if (io.stats && lane == 0) {
+      atomicAdd(a.stats + 0, (unsigned long long)H);
+      atomicAdd(a.stats + 1, (unsigned long long)L);
+    }
+    if (lane == 0) {
+      WinInfo w;
+      w.i = i;
+      w.qseq = a.win_seq[wdx];
+      w.s = s;
+      w.m = m;
+      for (int g = 0; g < ng; ++g) {
+        w.o = g < ng0 ? 0 : 1;
+        const unsigned long long* base = S.hits + (w.o ? split : 0);
+        const int64_t cnt = w.o ? L - split : split;
+        sweep_group(a, w,
+                    [&](int64_t x) {
+                      const unsigned long long h = base[x];
+                      return make_uint2((uint32_t)(h >> 20), (uint32_t)(h & 0xFFFFFu));
+                    },
+                    cnt, S.cnt, (int64_t)S.glo[g], (int64_t)S.ghi[g]);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+int launch_warp_tier(sedef_ctx* ctx, const FArgs& a, const TierIO& io, int64_t max_windows,
+                     const char* name) {
+  const size_t sm = sizeof(WarpSmem) * kWWarps;
+  static bool attr = false;
+  if (!attr) {
+    SEDEF_CUDA(cudaFuncSetAttribute(k_filter_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sm));
+    attr = true;
+  }
+  int per_sm = 0;
+  SEDEF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_warp, 32 * kWWarps, sm));
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)ctx_sm_count(ctx) * per_sm;
+  const int64_t need = (max_windows + kWWarps - 1) / kWWarps;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  SEDEF_KERNEL(ctx, name, k_filter_warp<<<(int)grid, 32 * kWWarps, sm, ctx_stream(ctx)>>>(a, io));
+  return SEDEF_OK;
+}
+
 // ------------------------------------------------------------- slow path --
 
 constexpr int kSThreads = 256;
@@ -1729,7 +1999,9 @@ constexpr int kNumTier1 = 4;
 const FastLaunch kTier2[] = {launch_fast<256, 8192, 2048>, launch_fast<256, 4096, 1024>,
                              launch_fast<512, 8192, 2048>};
 constexpr int kNumTier2 = 3;
-constexpr int kNumVariants = kNumTier1 * kNumTier2;  // variant = t1 * kNumTier2 + t2
+// variant = (warp tier off) * 12 + t1 * kNumTier2 + t2
+constexpr int kNumShapes = kNumTier1 * kNumTier2;
+constexpr int kNumVariants = 2 * kNumShapes;
 
 }  // namespace
 
@@ -1784,6 +2056,8 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   int32_t* wseq = (int32_t*)ctx_alloc(ctx, (size_t)nwin * 4);
   uint32_t* ovl = (uint32_t*)ctx_alloc(ctx, (size_t)nwin * 4);
   uint32_t* ovl1 = (uint32_t*)ctx_alloc(ctx, (size_t)nwin * 4);
+  uint32_t* ovl0 = (uint32_t*)ctx_alloc(ctx, (size_t)nwin * 4);
+  if (!ovl0) return SEDEF_ERR_OOM;
   // [0] runs, [1] windows for the global path, [2] tier-1 work, [3] large
   // refine runs, [4] hits, [5] collected hits, [6]/[7] task and refine work,
   // [8] tier-2 work, [9] windows tier 1 handed to tier 2, [10] sample size,
@@ -1853,15 +2127,22 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
     float best_ms = 1e30f;
     for (int v = 0; v < kNumVariants; ++v) {
       float ms = 0.f;
+      const int sh = v % kNumShapes;
+      const bool warp_tier = v < kNumShapes;
       for (int rep = 0; rep < 2; ++rep) {  // the first repetition warms up
         SEDEF_CUDA(cudaMemsetAsync(counters, 0, 80, st));
-        TierIO io{d_sample, (const unsigned int*)(counters + 10), ovl1,
+        SEDEF_CUDA(cudaMemsetAsync(counters + 12, 0, 16, st));
+        TierIO io0{d_sample, (const unsigned int*)(counters + 10), ovl0,
+                   (unsigned int*)(counters + 12), (unsigned int*)(counters + 13), 0};
+        TierIO io{warp_tier ? ovl0 : d_sample,
+                  (const unsigned int*)(counters + (warp_tier ? 12 : 10)), ovl1,
                   (unsigned int*)(counters + 9), (unsigned int*)(counters + 2), 0};
         TierIO io2{ovl1, (const unsigned int*)(counters + 9), ovl, (unsigned int*)(counters + 1),
                    (unsigned int*)(counters + 8), 0};
         SEDEF_CUDA(cudaEventRecord(e0, st));
-        SEDEF_TRY(kTier1[v / kNumTier2](ctx, a, io, ns, "k_filter_tune"));
-        SEDEF_TRY(kTier2[v % kNumTier2](ctx, a, io2, ns, "k_filter_tune"));
+        if (warp_tier) SEDEF_TRY(launch_warp_tier(ctx, a, io0, ns, "k_filter_tune"));
+        SEDEF_TRY(kTier1[sh / kNumTier2](ctx, a, io, ns, "k_filter_tune"));
+        SEDEF_TRY(kTier2[sh % kNumTier2](ctx, a, io2, ns, "k_filter_tune"));
         SEDEF_CUDA(cudaEventRecord(e1, st));
         SEDEF_CUDA(cudaEventSynchronize(e1));
         SEDEF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
@@ -1878,15 +2159,25 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
     return SEDEF_OK;
   }
   {
-    // tier 1 (autotuned shape) over all windows, tier 2 (8,192 hits in
-    // shared memory) over what tier 1 could not hold, the global path after
+    // the warp tier over all windows (unless the autotuned variant leaves it
+    // out), tier 1 (autotuned shape) over what it could not hold, tier 2
+    // (4,096-8,192 hits in shared memory) after that, the global path last
     int v = ctx_filter_variant(ctx);
     if (v < 0 || v >= kNumVariants) v = 0;
-    TierIO io1{nullptr, nullptr, ovl1, (unsigned int*)(counters + 9), (unsigned int*)(counters + 2), 1};
-    SEDEF_TRY(kTier1[v / kNumTier2](ctx, a, io1, nwin, "k_filter_fast"));
+    const int sh = v % kNumShapes;
+    const bool warp_tier = v < kNumShapes;
+    if (warp_tier) {
+      TierIO io0{nullptr, nullptr, ovl0, (unsigned int*)(counters + 12),
+                 (unsigned int*)(counters + 13), 1};
+      SEDEF_TRY(launch_warp_tier(ctx, a, io0, nwin, "k_filter_warp"));
+    }
+    TierIO io1{warp_tier ? ovl0 : nullptr,
+               warp_tier ? (const unsigned int*)(counters + 12) : nullptr, ovl1,
+               (unsigned int*)(counters + 9), (unsigned int*)(counters + 2), 1};
+    SEDEF_TRY(kTier1[sh / kNumTier2](ctx, a, io1, nwin, "k_filter_fast"));
     TierIO io2{ovl1, (const unsigned int*)(counters + 9), ovl, (unsigned int*)(counters + 1),
                (unsigned int*)(counters + 8), 0};
-    SEDEF_TRY(kTier2[v % kNumTier2](ctx, a, io2, nwin, "k_filter_mid"));
+    SEDEF_TRY(kTier2[sh % kNumTier2](ctx, a, io2, nwin, "k_filter_mid"));
   }
 
   unsigned long long* h_cnt = nullptr;

@@ -148,8 +148,24 @@ class Server:
                         for c in self.ctxs]
         self.batches = 0
 
-    def warm(self, seqs: list):
-        """One untimed pass per worker over these query sequences."""
+    def warm(self, seqs: list, autotune: bool = True):
+        """Picks the filter shape on these query sequences against the
+        resident index (autotuner, first worker's context; every worker takes
+        the result), then one untimed pass per worker over them."""
+        if autotune and seqs:
+            import torch
+            c0 = self.ctxs[0]
+            q = binding.params_from_struct(self.p, self_mode=0)
+            offs = np.zeros(len(seqs) + 1, dtype=np.int64)
+            offs[1:] = np.cumsum([len(x) for x in seqs])
+            with torch.cuda.stream(c0.stream):
+                d = torch.from_numpy(np.concatenate(seqs)).to(c0.device)
+                packed, mask, nbits = c0.sedef_pack(d)
+                qrec = c0.sedef_sketch(packed, mask, nbits, offs, q)
+                v = c0.sedef_filter_autotune(qrec, offs, self.index.trec, self.index.tsorted,
+                                             self.index.toff, self.index.offsets, q)
+            for c in self.ctxs:
+                c.sedef_filter_variant(v)
         for c in self.ctxs:
             search(c, self.index, [Request(rid=-1, seq=q) for q in seqs], self.p)
 
