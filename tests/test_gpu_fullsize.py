@@ -78,7 +78,7 @@ def check_candidate_properties(chains: np.ndarray, cands: np.ndarray):
     # chain's q0), only for the chains not yet placed
     todo = np.arange(len(chains))
     stuck = [np.zeros(0, dtype=np.int64)]
-    for back in range(8192):
+    for back in range(64):
         if len(todo) == 0:
             break
         k = top[todo] - back
@@ -91,7 +91,7 @@ def check_candidate_properties(chains: np.ndarray, cands: np.ndarray):
         stuck.append(todo[~ok])  # left its group without a container
         todo = todo[ok & ~inside]
     stuck = np.concatenate(stuck + [todo])
-    # unplaced chains (none left in practice): a seeded sample of them, each
+    # chains not placed within 64 candidates: a seeded sample of them, each
     # against every candidate of its group
     rng = np.random.default_rng(0)
     for x in rng.permutation(stuck)[:300]:
