@@ -188,9 +188,10 @@ def algorithmic_bytes(seq, offsets, rec_rows, sorted_rows, runs, k, n, step):
     }
 
 
-def measured_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None
-    when there is none or the kernel's source changed since it was taken."""
+def measured_traffic(kernel: str, field: str = "bytes_per_launch"):
+    """DRAM bytes (or another counter) per launch of `kernel` from the committed
+    ncu capture, or None when there is none or the kernel's source changed
+    since it was taken."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     if not os.path.exists(path):
@@ -206,7 +207,7 @@ def measured_traffic(kernel: str):
     with open(src, "rb") as f:
         if hashlib.sha256(f.read()).hexdigest() != e["sha256"]:
             return None
-    return int(e["bytes_per_launch"])
+    return int(e[field]) if e.get(field) is not None else None
 
 
 def run_cpu_oracle_sample(seq, bases=CPU_SAMPLE_BASES, threads=1):
@@ -580,6 +581,18 @@ def main():
                      "launch_ms": per_launch_ms})
     else:
         roof.update({"achieved": None, "frac": None, "launch_ms": per_launch_ms})
+    # the bound that holds for a latency/issue-bound kernel: warp instructions
+    # issued (ncu count of the committed capture) per live launch time against
+    # one instruction per scheduler per cycle (4 per SM) at the top SM clock
+    inst = measured_traffic(dname, "warp_instructions_per_launch")
+    if inst:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        ghz = (clk.get("sm_max_mhz") or 2070.0) / 1000.0
+        ipeak = sms * 4 * ghz
+        iach = inst / (per_launch_ms / 1000) / 1e9
+        roof["issue"] = {"achieved": iach, "peak": ipeak, "unit": "G warp-instructions/s",
+                         "frac": iach / ipeak, "instructions_per_launch": inst,
+                         "peak_from": f"{sms} SMs x 4 schedulers x {ghz:.3f} GHz"}
     kernels = {k: {"launches_per_step": c / args.steps, "ms_per_step": t / args.steps}
                for k, (c, t) in sorted(trace.items(), key=lambda kv: -kv[1][1])}
     for k, v in kernels.items():
