@@ -584,15 +584,18 @@ def main():
     # the bound that holds for a latency/issue-bound kernel: warp instructions
     # issued (ncu count of the committed capture) per live launch time against
     # one instruction per scheduler per cycle (4 per SM) at the top SM clock
-    inst = measured_traffic(dname, "warp_instructions_per_launch")
-    if inst:
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        ghz = (clk.get("sm_max_mhz") or 2070.0) / 1000.0
-        ipeak = sms * 4 * ghz
-        iach = inst / (per_launch_ms / 1000) / 1e9
-        roof["issue"] = {"achieved": iach, "peak": ipeak, "unit": "G warp-instructions/s",
-                         "frac": iach / ipeak, "instructions_per_launch": inst,
-                         "peak_from": f"{sms} SMs x 4 schedulers x {ghz:.3f} GHz"}
+    try:
+        inst = measured_traffic(dname, "warp_instructions_per_launch")
+        if inst:
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            ghz = float(clk.get("sm_max_mhz") or 2070.0) / 1000.0
+            ipeak = sms * 4 * ghz
+            iach = inst / (per_launch_ms / 1000) / 1e9
+            roof["issue"] = {"achieved": iach, "peak": ipeak, "unit": "G warp-instructions/s",
+                             "frac": iach / ipeak, "instructions_per_launch": inst,
+                             "peak_from": f"{sms} SMs x 4 schedulers x {ghz:.3f} GHz"}
+    except Exception as e:  # a missing counter must not cost the line
+        roof["issue"] = {"error": str(e)}
     kernels = {k: {"launches_per_step": c / args.steps, "ms_per_step": t / args.steps}
                for k, (c, t) in sorted(trace.items(), key=lambda kv: -kv[1][1])}
     for k, v in kernels.items():
