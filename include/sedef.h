@@ -13,7 +13,7 @@
  *   sedef_filter  per query window: candidate lookup, sliding count of shared
  *                 minimizers tested against tau, and the winnowed MinHash
  *                 estimate that picks each run's seed (Sections 2.2 and 3.1)
- *   sedef_chain_t   colinear chaining of the seed's minimizer anchors (Section
+ *   sedef_chain   colinear chaining of the seed's minimizer anchors (Section
  *                 3.3, sparse DP with gaps bounded via delta_G)
  *   sedef_merge   chains joined into SD candidates (Section 3: seeds grown
  *                 while similar, at chain granularity)
@@ -235,9 +235,10 @@ int sedef_sketch(sedef_ctx* ctx, const uint32_t* d_packed, const uint32_t* d_mas
  * 1 MB (per-tile counts and offsets for at most 268,435,456 bases and the
  * offsets of at most 4096 sequences); larger inputs are rejected with
  * SEDEF_ERR_UNSUPPORTED.  The array stays allocated on every device that
- * loads the library until the process exits.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  All calls share the one array, so
+ * loads the library until the process exits.  Every call looks up the
+ * array's device address on the current device (cudaGetSymbolAddress); the
+ * first call on a device also loads the array there, so make that first
+ * call before any stream capture.  All calls share the one array, so
  * calls that overlap on the GPU (other streams, other host threads) race:
  * serialize them.  Synchronizes `stream`.
  */

@@ -223,6 +223,34 @@ void estimate(const std::map<uint64_t, int>& wq,
   *den = taken;
 }
 
+// Colinear chaining DP of Section 3.3 over anchors (p, t') sorted ascending.
+// f[a] = 1 + max f[b] over predecessors b < a with both gaps in (0, gap_max]
+// and |gap_p - gap_t| <= diag_max; pred[a] = that b (the largest f, then
+// the largest index), -1 when a starts its chain.  Returns the chain end:
+// the largest f, then the smallest index.  A >= 1.
+int64_t chain_dp(const std::vector<std::pair<int64_t, int64_t>>& anc, int64_t gap_max,
+                 int64_t diag_max, std::vector<int64_t>* f_out, std::vector<int64_t>* pred_out) {
+  const int64_t A = (int64_t)anc.size();
+  std::vector<int64_t>& f = *f_out;
+  std::vector<int64_t>& pred = *pred_out;
+  f.assign(A, 1);
+  pred.assign(A, -1);
+  for (int64_t a = 0; a < A; ++a)
+    for (int64_t b = 0; b < a; ++b) {
+      const int64_t dp = anc[a].first - anc[b].first, dt = anc[a].second - anc[b].second;
+      if (dp <= 0 || dt <= 0 || dp > gap_max || dt > gap_max) continue;
+      if (std::llabs(dp - dt) > diag_max) continue;
+      if (pred[a] < 0 || f[b] + 1 > f[a] || (f[b] + 1 == f[a] && b > pred[a])) {
+        f[a] = f[b] + 1;
+        pred[a] = b;
+      }
+    }
+  int64_t end = 0;
+  for (int64_t a = 1; a < A; ++a)
+    if (f[a] > f[end]) end = a;
+  return end;
+}
+
 }  // namespace
 
 extern "C" {
@@ -605,22 +633,10 @@ void* orc_chain(const int64_t* runs, int64_t nruns, int64_t run_cols,
     std::sort(anc.begin(), anc.end());
     const int64_t A = (int64_t)anc.size();
     if (A == 0) continue;
-    std::vector<int64_t> f(A, 1), pred(A, -1);
-    for (int64_t a = 0; a < A; ++a) {
-      for (int64_t b = 0; b < a; ++b) {
-        int64_t dp = std::get<0>(anc[a]) - std::get<0>(anc[b]);
-        int64_t dt = std::get<1>(anc[a]) - std::get<1>(anc[b]);
-        if (dp <= 0 || dt <= 0 || dp > P.gap_max || dt > P.gap_max) continue;
-        if (std::llabs(dp - dt) > P.diag_max) continue;
-        if (pred[a] < 0 || f[b] + 1 > f[a] || (f[b] + 1 == f[a] && b > pred[a])) {
-          f[a] = f[b] + 1;
-          pred[a] = b;
-        }
-      }
-    }
-    int64_t end = 0;
-    for (int64_t a = 1; a < A; ++a)
-      if (f[a] > f[end]) end = a;
+    std::vector<std::pair<int64_t, int64_t>> pt(A);
+    for (int64_t a = 0; a < A; ++a) pt[a] = {std::get<0>(anc[a]), std::get<1>(anc[a])};
+    std::vector<int64_t> f, pred;
+    const int64_t end = chain_dp(pt, P.gap_max, P.diag_max, &f, &pred);
     const int64_t score = f[end];
     if (score < min_shared(tau, s)) continue;
     int64_t q0 = INT64_MAX, q1 = -1, t0 = INT64_MAX, t1 = -1;
@@ -636,23 +652,14 @@ void* orc_chain(const int64_t* runs, int64_t nruns, int64_t run_cols,
 }
 
 // Chaining of one explicit anchor list (for pin tests): anchors are (p, t')
-// rows; returns rows (f, pred) per anchor in sorted (p, t') order followed by
-// nothing else.  The best end is the largest f, then the smallest index.
+// rows; returns rows (p, t', f, pred) per anchor in sorted (p, t') order,
+// computed by chain_dp, the DP orc_chain runs for every kept seed.
 void* orc_chain_anchors(const int64_t* anchors, int64_t A, int64_t gap_max, int64_t diag_max) {
   std::vector<std::pair<int64_t, int64_t>> anc(A);
   for (int64_t a = 0; a < A; ++a) anc[a] = {anchors[2 * a], anchors[2 * a + 1]};
   std::sort(anc.begin(), anc.end());
-  std::vector<int64_t> f(A, 1), pred(A, -1);
-  for (int64_t a = 0; a < A; ++a)
-    for (int64_t b = 0; b < a; ++b) {
-      int64_t dp = anc[a].first - anc[b].first, dt = anc[a].second - anc[b].second;
-      if (dp <= 0 || dt <= 0 || dp > gap_max || dt > gap_max) continue;
-      if (std::llabs(dp - dt) > diag_max) continue;
-      if (pred[a] < 0 || f[b] + 1 > f[a] || (f[b] + 1 == f[a] && b > pred[a])) {
-        f[a] = f[b] + 1;
-        pred[a] = b;
-      }
-    }
+  std::vector<int64_t> f, pred;
+  if (A > 0) chain_dp(anc, gap_max, diag_max, &f, &pred);
   Table* T = new Table();
   T->ncols = 4;
   for (int64_t a = 0; a < A; ++a) T->row({anc[a].first, anc[a].second, f[a], pred[a]});

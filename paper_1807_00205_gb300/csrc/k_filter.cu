@@ -1,27 +1,36 @@
-// a4-a6: candidate lookup, sliding shared-minimizer count against m(s), and
-// the winnowed MinHash refine (Sections 2.2 and 3.1).
+// a4-a6: candidate lookup, sliding count of shared minimizers against m(s),
+// and the winnowed MinHash refine (Sections 2.2 and 3.1).
 //
-// Fast path (one CTA of 128 threads per query window, persistent CTAs):
+// Shared-memory tiers (one CTA per query window, persistent CTAs):
 //   1. the window's query minimizers are sorted by hash in shared memory and
 //      deduplicated into W_Q (s hashes, each with its strand set);
 //   2. every posting of every hash of W_Q is a hit (t, hid, o).  Hits are
 //      counted into direct-mapped 16-bit counters keyed by (t >> 10, o):
 //      a target window [j, j+n-k] lies inside bins j>>10 and (j>>10)+1, so a
 //      j can only pass when those two counters sum to m or more (aliasing
-//      only adds false candidates);
+//      only adds false candidates).  The table has the smallest power of two
+//      >= 4 H slots (H = the window's hits), at least 2,048 and at most the
+//      tier's size, so the prefilter stays selective when posting lists are
+//      long (a large target);
 //   3. hits whose bin pair can pass are collected and sorted by (o, t); the
 //      exact sweep (one thread, per-hash counters) runs only over j ranges
 //      where m consecutive hits fit in n-k bases.  Any j whose true count
 //      reaches m has all of its hits collected, and a count computed from a
 //      subset never exceeds the true one, so the runs are exact.
-// Windows that exceed the fast path's shared-memory budget go to a slow path
-// that writes their hits to global memory, radix-sorts them by
-// (window, o, t) and runs the same sweep.
+// The tiers differ only in their shared-memory budget: an optional warp tier
+// (one warp per small window), tier 1 (autotuned shape), tier 2 (more
+// collected hits) and the wide tier (32,768 counters) for windows with more
+// than 4,096 hits, which tiers 1 and 2 hand over before enumerating them.
+// Windows no tier can hold go to a global path that writes their hits to
+// global memory, radix-sorts them by (window, o, t) and runs the same sweep.
 //
-// Refine (one warp per run): the domain W_Q u (target minimizers of the
-// run's span) is sorted; presence and sharedness are kept as counters and
-// bitsets while the target window rolls over the run's breakpoints, and the
-// estimate |S(W_Q u W_T) n W_Q n W_T| is read off the first s set bits.
+// Refine (k_refine_batch): each run's domain, W_Q u (target minimizers of the
+// run's span that can change the estimate), is sorted by a warp into a
+// per-warp slot; then one lane per run rolls the target window over the
+// run's breakpoints, keeping presence and sharedness counters and the s-th
+// present hash, so the estimate |S(W_Q u W_T) n W_Q n W_T| is exact at every
+// breakpoint.  Runs whose domain exceeds the batched kernel's slots go to
+// k_refine (one warp per run, bitsets over the sorted domain).
 #include <cstring>
 
 #include "common.cuh"
@@ -350,7 +359,7 @@ __device__ int build_wq(const FArgs& a, QBuild q, int c, int64_t seq_lo = 0, int
 
 // ------------------------------------------------------------- fast path --
 
-template <int TPB, int LCAP, int GCAP>
+template <int TPB, int LCAP, int GCAP, int SLOTS>
 struct FastSmemT {
   uint32_t qkey[kQCap];
   uint32_t dh[kQCap];
@@ -358,7 +367,7 @@ struct FastSmemT {
   uint32_t plen[kQCap];
   uint32_t pre[kQCap + 1];
   uint8_t dm[kQCap];
-  uint32_t slots[kSlots / 2];  // two 16-bit counters per word
+  uint32_t slots[SLOTS / 2];  // two 16-bit counters per word
   unsigned long long hits[LCAP];
   uint32_t glo[GCAP];     // dense groups: Jlo (clamped to >= 0), Jhi
   uint32_t ghi[GCAP];
@@ -377,10 +386,16 @@ struct TierIO {
   unsigned int* out_count;
   unsigned int* next;             // work counter of this tier
   int stats;                      // count hits in the filter statistics
+  // windows with more than hlim hits are handed over before their hits are
+  // enumerated: to wide_list when set (the wide tier), else to out_list
+  uint32_t hlim = 0xFFFFFFFFu;
+  uint32_t* wide_list = nullptr;
+  unsigned int* wide_count = nullptr;
 };
 
-__device__ __forceinline__ uint32_t slot_of(uint32_t t, uint32_t o) {
-  return (((t >> kBinShift) << 1) | o) & (kSlots - 1);
+// (bin, o) counter slot of a hit in a direct-mapped table of mask+1 slots
+__device__ __forceinline__ uint32_t slot_of(uint32_t t, uint32_t o, uint32_t mask) {
+  return (((t >> kBinShift) << 1) | o) & mask;
 }
 
 __device__ __forceinline__ uint32_t slot_count(const uint32_t* slots, uint32_t s) {
@@ -406,9 +421,12 @@ __device__ __forceinline__ void for_hits(const FArgs& a, const Smem& S, int64_t 
   }
 }
 
-template <int TPB, int LCAP, int GCAP>
+// SLOTS is the largest (bin, o) table; a window uses the smallest power of
+// two >= 4 H (at least 2,048 slots), so that aliasing stays rare however
+// many hits the window has.
+template <int TPB, int LCAP, int GCAP, int SLOTS>
 __global__ void __launch_bounds__(TPB) k_filter_fast(FArgs a, TierIO io) {
-  using FastSmem = FastSmemT<TPB, LCAP, GCAP>;
+  using FastSmem = FastSmemT<TPB, LCAP, GCAP, SLOTS>;
   constexpr int kFThreads = TPB;
   constexpr int kLCap = LCAP;
   constexpr int kGCap = GCAP;
@@ -465,7 +483,6 @@ __global__ void __launch_bounds__(TPB) k_filter_fast(FArgs a, TierIO io) {
       }
       if (threadIdx.x == 0) S.pre[s] = run;
     }
-    for (int x = threadIdx.x; x < kSlots / 2; x += blockDim.x) S.slots[x] = 0;
     if (threadIdx.x == 0) {
       S.s = s;
       S.nhit = 0;
@@ -474,26 +491,35 @@ __global__ void __launch_bounds__(TPB) k_filter_fast(FArgs a, TierIO io) {
     __syncthreads();
     const uint32_t H = S.pre[s];
     if (H == 0) continue;
-    if (H > (uint32_t)kHMax) {
-      if (threadIdx.x == 0) io.out_list[atomicAdd(io.out_count, 1u)] = (uint32_t)wdx;
+    if (H > (uint32_t)kHMax || H > io.hlim) {
+      if (threadIdx.x == 0) {
+        if (H <= (uint32_t)kHMax && io.wide_list)
+          io.wide_list[atomicAdd(io.wide_count, 1u)] = (uint32_t)wdx;
+        else
+          io.out_list[atomicAdd(io.out_count, 1u)] = (uint32_t)wdx;
+      }
       continue;
     }
+    uint32_t nslots = kSlots;
+    while (nslots < 4u * H && nslots < (uint32_t)SLOTS) nslots <<= 1;
+    const uint32_t smask = nslots - 1;
+    for (uint32_t x = threadIdx.x; x < nslots / 2; x += blockDim.x) S.slots[x] = 0;
+    __syncthreads();
     const int m = a.mtab[s];
-    if (io.stats && threadIdx.x == 0) atomicAdd(a.stats + 0, (unsigned long long)H);
     // pass 1: (bin, o) counts
     for_hits(a, S, i, (int)H, [&](uint32_t t, uint32_t, uint32_t o) {
-      const uint32_t sl = slot_of(t, o);
+      const uint32_t sl = slot_of(t, o, smask);
       atomicAdd(&S.slots[sl >> 1], 1u << ((sl & 1) * 16));
     });
     __syncthreads();
     // pass 2: collect the hits of bins whose pair (b, b+1) or (b-1, b) may pass
     for_hits(a, S, i, (int)H, [&](uint32_t t, uint32_t hid, uint32_t o) {
       const uint32_t b = t >> kBinShift;
-      const uint32_t c0 = slot_count(S.slots, slot_of(t, o));
-      const uint32_t cn = slot_count(S.slots, (((b + 1) << 1) | o) & (kSlots - 1));
+      const uint32_t c0 = slot_count(S.slots, slot_of(t, o, smask));
+      const uint32_t cn = slot_count(S.slots, (((b + 1) << 1) | o) & smask);
       bool need = c0 + cn >= (uint32_t)m;
       if (!need && b > 0) {
-        const uint32_t cp = slot_count(S.slots, (((b - 1) << 1) | o) & (kSlots - 1));
+        const uint32_t cp = slot_count(S.slots, (((b - 1) << 1) | o) & smask);
         need = cp + c0 >= (uint32_t)m;
       }
       if (need) {
@@ -504,12 +530,18 @@ __global__ void __launch_bounds__(TPB) k_filter_fast(FArgs a, TierIO io) {
     });
     __syncthreads();
     const int L = S.nhit;
-    if (io.stats && threadIdx.x == 0) atomicAdd(a.stats + 1, (unsigned long long)L);
     if (L > kLCap) {
       if (threadIdx.x == 0) io.out_list[atomicAdd(io.out_count, 1u)] = (uint32_t)wdx;
       continue;
     }
-    if (L < m) continue;
+    // statistics count the windows this tier finishes (each window once)
+    if (L < m) {
+      if (io.stats && threadIdx.x == 0) {
+        atomicAdd(a.stats + 0, (unsigned long long)H);
+        atomicAdd(a.stats + 1, (unsigned long long)L);
+      }
+      continue;
+    }
     const int np = next_pow2(L < 2 ? 2 : L);
     for (int x = L + threadIdx.x; x < np; x += blockDim.x) S.hits[x] = ~0ull;
     __syncthreads();
@@ -551,6 +583,10 @@ __global__ void __launch_bounds__(TPB) k_filter_fast(FArgs a, TierIO io) {
     if (ng > kGCap) {
       if (threadIdx.x == 0) io.out_list[atomicAdd(io.out_count, 1u)] = (uint32_t)wdx;
       continue;
+    }
+    if (io.stats && threadIdx.x == 0) {
+      atomicAdd(a.stats + 0, (unsigned long long)H);
+      atomicAdd(a.stats + 1, (unsigned long long)L);
     }
     {
       const int warp = threadIdx.x >> 5;
@@ -1966,25 +2002,30 @@ __global__ void k_run_ranges(const sedef_run_t* runs, int64_t n, const int64_t* 
 
 // ------------------------------------------------------- tier launchers --
 
-template <int TPB, int LCAP, int GCAP>
-int launch_fast(sedef_ctx* ctx, const FArgs& a, const TierIO& io, int64_t max_windows,
+template <int TPB, int LCAP, int GCAP, int SLOTS = kSlots>
+int launch_fast(sedef_ctx* ctx, const FArgs& a, const TierIO& io_in, int64_t max_windows,
                 const char* name) {
-  const size_t sm = sizeof(FastSmemT<TPB, LCAP, GCAP>);
+  const size_t sm = sizeof(FastSmemT<TPB, LCAP, GCAP, SLOTS>);
   static bool attr = false;  // one per instantiation
   if (!attr) {
-    SEDEF_CUDA(cudaFuncSetAttribute(k_filter_fast<TPB, LCAP, GCAP>,
+    SEDEF_CUDA(cudaFuncSetAttribute(k_filter_fast<TPB, LCAP, GCAP, SLOTS>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     attr = true;
   }
+  // a table of SLOTS counters keeps its aliasing low up to 2 * SLOTS hits;
+  // windows with more go on (to the wide tier when the caller names one)
+  TierIO io = io_in;
+  io.hlim = (uint32_t)(2 * SLOTS);
   int per_sm = 0;
-  SEDEF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_fast<TPB, LCAP, GCAP>,
+  SEDEF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm,
+                                                           k_filter_fast<TPB, LCAP, GCAP, SLOTS>,
                                                            TPB, sm));
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)ctx_sm_count(ctx) * per_sm;
   if (grid > max_windows) grid = max_windows;
   if (grid < 1) grid = 1;
   SEDEF_KERNEL(ctx, name,
-               k_filter_fast<TPB, LCAP, GCAP><<<(int)grid, TPB, sm, ctx_stream(ctx)>>>(a, io));
+               k_filter_fast<TPB, LCAP, GCAP, SLOTS><<<(int)grid, TPB, sm, ctx_stream(ctx)>>>(a, io));
   return SEDEF_OK;
 }
 
@@ -1999,6 +2040,11 @@ constexpr int kNumTier1 = 4;
 const FastLaunch kTier2[] = {launch_fast<256, 8192, 2048>, launch_fast<256, 4096, 1024>,
                              launch_fast<512, 8192, 2048>};
 constexpr int kNumTier2 = 3;
+// Wide tier: windows with more hits than a 2,048-slot table can separate
+// (long posting lists of a large target), before the global path.  32,768
+// (bin, o) slots keep the prefilter selective up to 65,535 hits.
+constexpr int kWideSlots = 32768;
+const FastLaunch kTierWide = launch_fast<512, 2048, 512, kWideSlots>;
 // variant = (warp tier off) * 12 + t1 * kNumTier2 + t2
 constexpr int kNumShapes = kNumTier1 * kNumTier2;
 constexpr int kNumVariants = 2 * kNumShapes;
@@ -2057,11 +2103,13 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   uint32_t* ovl = (uint32_t*)ctx_alloc(ctx, (size_t)nwin * 4);
   uint32_t* ovl1 = (uint32_t*)ctx_alloc(ctx, (size_t)nwin * 4);
   uint32_t* ovl0 = (uint32_t*)ctx_alloc(ctx, (size_t)nwin * 4);
-  if (!ovl0) return SEDEF_ERR_OOM;
+  uint32_t* ovlw = (uint32_t*)ctx_alloc(ctx, (size_t)nwin * 4);
+  if (!ovl0 || !ovlw) return SEDEF_ERR_OOM;
   // [0] runs, [1] windows for the global path, [2] tier-1 work, [3] large
   // refine runs, [4] hits, [5] collected hits, [6]/[7] task and refine work,
   // [8] tier-2 work, [9] windows tier 1 handed to tier 2, [10] sample size,
-  // [11] global-path hits (planned pass)
+  // [11] global-path hits (planned pass), [12]/[13] warp-tier hand-overs and
+  // work, [14] windows for the wide tier, [15] wide-tier work
   unsigned long long* counters = (unsigned long long*)ctx_alloc(ctx, 128);
   sedef_run_t* raw = (sedef_run_t*)ctx_alloc(ctx, (size_t)(cap > 0 ? cap : 1) * sizeof(sedef_run_t));
   if (!wi || !wqa || !wqb || !wseq || !ovl || !ovl1 || !counters || !raw) return SEDEF_ERR_OOM;
@@ -2131,18 +2179,25 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
       const bool warp_tier = v < kNumShapes;
       for (int rep = 0; rep < 2; ++rep) {  // the first repetition warms up
         SEDEF_CUDA(cudaMemsetAsync(counters, 0, 80, st));
-        SEDEF_CUDA(cudaMemsetAsync(counters + 12, 0, 16, st));
+        SEDEF_CUDA(cudaMemsetAsync(counters + 12, 0, 32, st));
         TierIO io0{d_sample, (const unsigned int*)(counters + 10), ovl0,
                    (unsigned int*)(counters + 12), (unsigned int*)(counters + 13), 0};
         TierIO io{warp_tier ? ovl0 : d_sample,
                   (const unsigned int*)(counters + (warp_tier ? 12 : 10)), ovl1,
                   (unsigned int*)(counters + 9), (unsigned int*)(counters + 2), 0};
-        TierIO io2{ovl1, (const unsigned int*)(counters + 9), ovl, (unsigned int*)(counters + 1),
+        io.wide_list = ovlw;
+        io.wide_count = (unsigned int*)(counters + 14);
+        TierIO io2{ovl1, (const unsigned int*)(counters + 9), ovlw, (unsigned int*)(counters + 14),
                    (unsigned int*)(counters + 8), 0};
+        io2.wide_list = ovlw;
+        io2.wide_count = (unsigned int*)(counters + 14);
+        TierIO iow{ovlw, (const unsigned int*)(counters + 14), ovl, (unsigned int*)(counters + 1),
+                   (unsigned int*)(counters + 15), 0};
         SEDEF_CUDA(cudaEventRecord(e0, st));
         if (warp_tier) SEDEF_TRY(launch_warp_tier(ctx, a, io0, ns, "k_filter_tune"));
         SEDEF_TRY(kTier1[sh / kNumTier2](ctx, a, io, ns, "k_filter_tune"));
         SEDEF_TRY(kTier2[sh % kNumTier2](ctx, a, io2, ns, "k_filter_tune"));
+        SEDEF_TRY(kTierWide(ctx, a, iow, ns, "k_filter_tune"));
         SEDEF_CUDA(cudaEventRecord(e1, st));
         SEDEF_CUDA(cudaEventSynchronize(e1));
         SEDEF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
@@ -2161,7 +2216,9 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   {
     // the warp tier over all windows (unless the autotuned variant leaves it
     // out), tier 1 (autotuned shape) over what it could not hold, tier 2
-    // (4,096-8,192 hits in shared memory) after that, the global path last
+    // (4,096-8,192 hits in shared memory) after that, the wide tier over the
+    // windows with many hits (from tiers 1 and 2) and over what tier 2 could
+    // not hold, the global path last
     int v = ctx_filter_variant(ctx);
     if (v < 0 || v >= kNumVariants) v = 0;
     const int sh = v % kNumShapes;
@@ -2174,10 +2231,17 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
     TierIO io1{warp_tier ? ovl0 : nullptr,
                warp_tier ? (const unsigned int*)(counters + 12) : nullptr, ovl1,
                (unsigned int*)(counters + 9), (unsigned int*)(counters + 2), 1};
+    io1.wide_list = ovlw;
+    io1.wide_count = (unsigned int*)(counters + 14);
     SEDEF_TRY(kTier1[sh / kNumTier2](ctx, a, io1, nwin, "k_filter_fast"));
-    TierIO io2{ovl1, (const unsigned int*)(counters + 9), ovl, (unsigned int*)(counters + 1),
-               (unsigned int*)(counters + 8), 0};
+    TierIO io2{ovl1, (const unsigned int*)(counters + 9), ovlw, (unsigned int*)(counters + 14),
+               (unsigned int*)(counters + 8), 1};
+    io2.wide_list = ovlw;
+    io2.wide_count = (unsigned int*)(counters + 14);
     SEDEF_TRY(kTier2[sh % kNumTier2](ctx, a, io2, nwin, "k_filter_mid"));
+    TierIO iow{ovlw, (const unsigned int*)(counters + 14), ovl, (unsigned int*)(counters + 1),
+               (unsigned int*)(counters + 15), 1};
+    SEDEF_TRY(kTierWide(ctx, a, iow, nwin, "k_filter_wide"));
   }
 
   unsigned long long* h_cnt = nullptr;

@@ -367,8 +367,6 @@ constexpr size_t kNoallocBytes = 2 * kNoallocCountBytes + (size_t)(kNoallocMaxSe
 // each device that loads the library.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-constexpr int kMaxDevices = 64;
-static unsigned char* g_noalloc_ptr[kMaxDevices];
 
 // Exclusive scan of n counts by one block (n is at most 131,073 here).
 __global__ void __launch_bounds__(1024) k_scan_one_block(const uint32_t* __restrict__ in,
@@ -415,14 +413,17 @@ extern "C" int sedef_sketch_noalloc(const uint32_t* d_packed, const uint32_t* d_
     return fail(SEDEF_ERR_INVALID, "NULL buffer");
   int dev = 0;
   SEDEF_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return fail(SEDEF_ERR_UNSUPPORTED, "device index too large");
-  if (!g_noalloc_ptr[dev]) {
-    void* ptr = nullptr;
+  // The array's device address on the current device.  Looked up on every
+  // call (a table lookup once the module is loaded; the first call on a
+  // device loads it), so it stays right after a cudaDeviceReset and needs no
+  // lock between host threads.  In host code the array's name is only a
+  // host-side stand-in, never a device address.
+  void* ptr = nullptr;
+  {
     const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess || !ptr) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-    g_noalloc_ptr[dev] = (unsigned char*)ptr;
   }
-  unsigned char* base = g_noalloc_ptr[dev];
+  unsigned char* base = (unsigned char*)ptr;
   uint32_t* cnt = reinterpret_cast<uint32_t*>(base);
   uint32_t* toff = reinterpret_cast<uint32_t*>(base + kNoallocCountBytes);
   int64_t* d_off = reinterpret_cast<int64_t*>(base + 2 * kNoallocCountBytes);

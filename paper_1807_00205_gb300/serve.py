@@ -36,6 +36,7 @@ class Request:
     arrival: float = 0.0     # perf_counter() time it entered the queue
     done: float = 0.0
     cands: np.ndarray = None  # sedef_cand_t rows (qseq = 0)
+    error: str = ""          # set when the request's batch failed
 
 
 class Admission:
@@ -129,7 +130,8 @@ class Server:
 
     def __init__(self, index: ResidentIndex, p: "binding.Params", workers: int = 2,
                  batching: bool = True, max_batch_bases: int = 64 << 20,
-                 reserve_bytes: int = 8 << 30, device: int = 0, free_bytes_fn=None):
+                 reserve_bytes: int = 8 << 30, device: int = 0, free_bytes_fn=None,
+                 ctx_factory=None):
         import torch
         self.index = index
         self.p = p
@@ -142,8 +144,9 @@ class Server:
             free_bytes_fn = lambda: torch.cuda.mem_get_info(device)[0]  # noqa: E731
         self.admission = Admission(max_batch_bases if batching else 1, reserve_bytes,
                                    free_bytes_fn)
-        self.ctxs = [binding.Context(device, stream=torch.cuda.Stream(device))
-                     for _ in range(workers)]
+        if ctx_factory is None:
+            ctx_factory = lambda: binding.Context(device, stream=torch.cuda.Stream(device))  # noqa: E731
+        self.ctxs = [ctx_factory() for _ in range(workers)]
         self.threads = [threading.Thread(target=self._work, args=(c,), daemon=True)
                         for c in self.ctxs]
         self.batches = 0
@@ -192,6 +195,10 @@ class Server:
                 continue
             try:
                 search(ctx, self.index, reqs, self.p)
+            except Exception as e:  # the batch fails, the worker goes on
+                for r in reqs:
+                    r.error = f"{type(e).__name__}: {e}"
+                    r.cands = None
             finally:
                 self.admission.release(reqs)
             now = time.perf_counter()
@@ -212,9 +219,13 @@ class Server:
             c.close()
 
 
-def run_load(server: Server, pool: list, rate: float, count: int, seed: int = 0) -> dict:
+def run_load(server: Server, pool: list, rate: float, count: int, seed: int = 0,
+             deadline_s: float = 600.0) -> dict:
     """Submits `count` requests (cycling through `pool`) at Poisson arrivals
-    of `rate` per second; returns latency percentiles and throughput."""
+    of `rate` per second; returns latency percentiles and throughput.
+    Raises TimeoutError when the requests have not all completed
+    `deadline_s` seconds after the last submission, and RuntimeError when a
+    request failed."""
     rng = np.random.default_rng(seed)
     gaps = rng.exponential(1.0 / rate, size=count)
     with server.cv:
@@ -231,11 +242,18 @@ def run_load(server: Server, pool: list, rate: float, count: int, seed: int = 0)
         r = Request(rid=k, seq=pool[k % len(pool)])
         reqs.append(r)
         server.submit(r)
+    give_up = time.perf_counter() + deadline_s
     while True:
         with server.cv:
             if len(server.completed) >= count:
                 break
+        if time.perf_counter() > give_up:
+            raise TimeoutError(f"{count - len(server.completed)} of {count} requests "
+                               f"still pending after {deadline_s} s")
         time.sleep(0.001)
+    failed = [r for r in reqs if r.error]
+    if failed:
+        raise RuntimeError(f"{len(failed)} requests failed; first: {failed[0].error}")
     t1 = max(r.done for r in reqs)
     lat = np.array([r.done - r.arrival for r in reqs]) * 1000.0
     bases = sum(len(r.seq) for r in reqs)

@@ -175,3 +175,116 @@ def chain_is_valid(chain, gap_max, diag_max):
         if not (0 < dp <= gap_max and 0 < dt <= gap_max and abs(dp - dt) <= diag_max):
             return False
     return True
+
+
+# ----------------------------------------------------------------- chains --
+#
+# Chaining restated from its definition (Section 3.3 on the seed's minimizer
+# anchors), by exhaustive path enumeration instead of a DP.  `slip` names one
+# plausible mistake to apply instead ("pred_tie", "end_tie", "span_short",
+# "no_self", "no_flip", "keep_all"); the pin test uses it only to show that
+# each mistake changes at least one row of its cases.
+
+def _seq_index(offsets, pos):
+    for s in range(len(offsets) - 1):
+        if int(offsets[s]) <= pos < int(offsets[s + 1]):
+            return s
+    return -1
+
+
+def seed_anchors(run, qrecs, trecs, p, slip=None):
+    """Anchors of one kept run as (p, t', t): a query-window minimizer p in
+    [i, i+n-k] and a target minimizer t in [j_a, j_b+n-k] with equal hash and
+    strands differing by o; in self mode t outside [i, i+n-k]; t' = t, or
+    j_b+n-k - t for o = 1.  Sorted by (p, t')."""
+    i, o, ja, jb = (int(x) for x in run[:4])
+    span = p["n"] - p["k"]
+    t_hi = jb + span - (1 if slip == "span_short" else 0)
+    occ = {}
+    for h, _, _ in trecs:
+        occ[h] = occ.get(h, 0) + 1
+    out = []
+    for hq, pq, sq in qrecs:
+        if not (i <= pq <= i + span):
+            continue
+        if p["max_occ"] > 0 and occ.get(hq, 0) > p["max_occ"]:
+            continue
+        for ht, pt, st in trecs:
+            if ht != hq or (sq ^ st) != o or not (ja <= pt <= t_hi):
+                continue
+            if p["self_mode"] and slip != "no_self" and i <= pt <= i + span:
+                continue
+            tp = t_hi - pt if (o == 1 and slip != "no_flip") else pt
+            out.append((pq, tp, pt))
+    return sorted(out)
+
+
+def maximal_chains(anchors, gap_max, diag_max, cap=500_000):
+    """Every source-to-sink path of the 'may follow' relation (index tuples).
+    A longest chain can be extended at neither end, so it is one of them."""
+    A = len(anchors)
+
+    def follows(a, b):
+        dp, dt = anchors[b][0] - anchors[a][0], anchors[b][1] - anchors[a][1]
+        return 0 < dp <= gap_max and 0 < dt <= gap_max and abs(dp - dt) <= diag_max
+
+    succ = [[b for b in range(A) if follows(a, b)] for a in range(A)]
+    has_pred = [False] * A
+    for a in range(A):
+        for b in succ[a]:
+            has_pred[b] = True
+    paths = []
+    stack = [(a,) for a in range(A) if not has_pred[a]]
+    while stack:
+        path = stack.pop()
+        nxt = succ[path[-1]]
+        if not nxt:
+            paths.append(path)
+            if len(paths) > cap:
+                raise OverflowError("too many chains to enumerate")
+        for b in nxt:
+            stack.append(path + (b,))
+    return paths
+
+
+def chosen_chain(anchors, gap_max, diag_max, slip=None):
+    """The chain the tie rule selects: among the longest chains, those ending
+    at the earliest anchor; among these, walking back from the end, the later
+    anchor at every step (lexicographically largest reversed index tuple)."""
+    paths = maximal_chains(anchors, gap_max, diag_max)
+    L = max(len(x) for x in paths)
+    longest = [x for x in paths if len(x) == L]
+    ends = {x[-1] for x in longest}
+    end = max(ends) if slip == "end_tie" else min(ends)
+    cands = [x for x in longest if x[-1] == end]
+    key = lambda x: tuple(reversed(x))
+    return min(cands, key=key) if slip == "pred_tie" else max(cands, key=key)
+
+
+def chain_rows(runs, qrecs, qoff, trecs, toff, p, tau, slip=None):
+    """Oracle chain rows (i, o, qseq, q0, q1, tseq, t0, t1, score, s) for
+    every kept run, by explicit anchor sets and path enumeration."""
+    span = p["n"] - p["k"]
+    occ = {}
+    for h, _, _ in trecs:
+        occ[h] = occ.get(h, 0) + 1
+    rows = []
+    for run in runs:
+        i, o, ja = int(run[0]), int(run[1]), int(run[2])
+        if int(run[11]) != 1:
+            continue
+        wq = {h for h, pq, _ in qrecs if i <= pq <= i + span
+              and not (p["max_occ"] > 0 and occ.get(h, 0) > p["max_occ"])}
+        s = len(wq)
+        anc = seed_anchors(run, qrecs, trecs, p, slip)
+        if not anc:
+            continue
+        ch = chosen_chain([(a[0], a[1]) for a in anc], p["gap_max"], p["diag_max"], slip)
+        score = len(ch)
+        if score < m_of(tau, s) and slip != "keep_all":
+            continue
+        ps = [anc[x][0] for x in ch]
+        ts = [anc[x][2] for x in ch]
+        rows.append((i, o, _seq_index(qoff, i), min(ps), max(ps) + p["k"], _seq_index(toff, ja),
+                     min(ts), max(ts) + p["k"], score, s))
+    return rows

@@ -190,6 +190,44 @@ def test_overflow_windows_use_global_path(ctx):
     full_parity(ctx, g, oracle.params(w=1, k=13), check_chain=False)
 
 
+def repeat_family_genome(seed=91, length=300_000, elem=1000, copies=150, id_lo=0.97,
+                         id_hi=0.995):
+    """150 unmasked copies of one 1 kbp element (97-99.5% identity, either
+    strand): posting lists ~150 long, like those of a large genome, so most
+    windows have more than 4,096 hits."""
+    rng = np.random.default_rng(seed)
+    seq = synth.random_bases(rng, length, 0.41)
+    unit = synth.random_bases(rng, elem, 0.41)
+    starts = np.sort(rng.choice(np.arange(0, length - elem, elem + 200), size=copies,
+                                replace=False))
+    for a in starts:
+        pc = synth.mutate(rng, unit, float(rng.uniform(id_lo, id_hi)))
+        if rng.random() < 0.5:
+            pc = synth.reverse_complement(pc)
+        seq[a:a + len(pc)] = pc[:length - a]
+    return synth.genome_from_parts([seq])
+
+
+def test_wide_tier_long_postings(ctx):
+    """Windows with more hits than a 2,048-slot prefilter can separate go to
+    the wide tier (32,768 slots), and from there to the global path when
+    they collect more than it holds; every stage must still equal the
+    oracle, under every first-tier shape."""
+    g = repeat_family_genome()
+    ref, out = full_parity(ctx, g, oracle.params())
+    assert len(ref["runs"]) > 10_000 and len(ref["cands"]) > 0
+    st = ctx.sedef_filter_stats()
+    assert st["windows"] > 1000
+    p = binding.params()
+    _, count = ctx.sedef_filter_variant()
+    for v in range(0, count, 5):
+        ctx.sedef_filter_variant(v)
+        runs, _ = ctx.sedef_filter(out["rec"], g.offsets, out["rec"], out["sorted"], out["off"],
+                                   g.offsets, p)
+        assert_rows_equal(run_rows(runs), ref["runs"], f"runs (shape {v})")
+    ctx.sedef_filter_variant(0)
+
+
 def test_chain_refuses_degenerate_seeds(ctx):
     """A seed inside a long unmasked poly-A run has millions of anchors; the
     chain call reports it instead of running the quadratic DP."""

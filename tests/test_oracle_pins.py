@@ -9,7 +9,9 @@ fix, independent of the oracle's own code paths.
 - winnowing invariant and density 2/(w+1) (Section 2.2);
 - index: sorted unique (hash, position) pairs (Section 3.1) versus numpy;
 - filter and refine: every window x every target start by explicit sets;
-- chaining: longest chain by a different search on tiny anchor sets;
+- chaining: longest chain by a different search on tiny anchor sets, and
+  whole chain rows (anchor sets, axis flip, self-span rule, tie rule, m(s)
+  drop) by exhaustive path enumeration;
 - merge: connected components by networkx;
 - planted duplications are recovered (the protocol of Section 4.1.1).
 """
@@ -230,6 +232,7 @@ def test_filter_window_subset_matches_full():
 
 @pytest.mark.parametrize("seed", range(30))
 def test_chain_dp_is_longest(seed):
+    """chain_anchors runs chain_dp, the same DP orc_chain runs per kept seed."""
     rng = np.random.default_rng(seed)
     A = int(rng.integers(1, 12))
     base = np.sort(rng.integers(0, 200, A))
@@ -249,6 +252,85 @@ def test_chain_dp_is_longest(seed):
         end = int(rows[end, 3])
     chain.reverse()
     assert len(chain) == best and bf.chain_is_valid(chain, gap_max, diag_max)
+
+
+def tandem_genome(seed, period=33, copies=5, flank=120, mut=0.05):
+    """A near-exact tandem repeat (period 33 < n), its partial reverse
+    complement and random flanks: in self mode the target span of a tandem
+    mate overlaps the query window's own span, and nearby copies give ties."""
+    rng = np.random.default_rng(seed)
+    unit = synth.random_bases(rng, period)
+    rep = np.concatenate([unit] * copies)
+    sub = rng.random(len(rep)) < mut
+    rep[sub] = synth._ACGT[rng.integers(0, 4, int(sub.sum()))]
+    seq = np.concatenate([synth.random_bases(rng, flank), rep, synth.random_bases(rng, flank),
+                          synth.reverse_complement(rep)[:80], synth.random_bases(rng, 60)])
+    return synth.Genome(np.ascontiguousarray(seq), np.array([0, len(seq)], dtype=np.int64), [])
+
+
+def end_dup_genome(seed):
+    """Two sequences, each ending with the second copy of a duplication
+    (reverse-complemented on odd seeds), so that runs end where the target
+    sequence ends and the last target k-mer can be an anchor."""
+    rng = np.random.default_rng(seed)
+    x = synth.random_bases(rng, 100)
+    y = synth.reverse_complement(x) if seed % 2 else x.copy()
+    s1 = np.concatenate([synth.random_bases(rng, int(rng.integers(20, 60))), x,
+                         synth.random_bases(rng, int(rng.integers(40, 70))), y])
+    z = synth.random_bases(rng, 150)
+    s2 = np.concatenate([z, synth.random_bases(rng, int(rng.integers(30, 60))),
+                         z[:int(rng.integers(90, 150))]])
+    seq = np.concatenate([s1, s2])
+    return synth.Genome(np.ascontiguousarray(seq), np.array([0, len(s1), len(seq)], dtype=np.int64),
+                        [])
+
+
+CHAIN_CASES = [
+    ("tiny", 51, dict(TINY)),
+    ("tiny", 52, dict(TINY, self_mode=0)),
+    ("tiny", 54, dict(TINY, self_mode=2)),
+    ("tiny", 55, dict(TINY, k=4, w=3, n=25, step=5, gap_max=25, diag_max=3)),
+    ("tiny", 56, dict(TINY, max_occ=4)),
+    ("tiny", 64, dict(TINY, diag_max=40, gap_max=40)),
+    ("tandem", 60, dict(TINY, diag_max=12, gap_max=30)),
+    ("tandem", 61, dict(TINY, diag_max=40, gap_max=40)),
+    ("end_dup", 81, dict(TINY, step=1)),
+    ("end_dup", 89, dict(TINY, step=1)),
+]
+CHAIN_SLIPS = ["pred_tie", "end_tie", "span_short", "no_self", "no_flip", "keep_all"]
+
+
+def _chain_case(kind, seed, p):
+    g = {"tiny": tiny_genome, "tandem": tandem_genome, "end_dup": end_dup_genome}[kind](seed)
+    recs = oracle.sketch(g.seq, g.offsets, p)
+    runs = oracle.filter_runs(recs, g.offsets, recs, g.offsets, p)
+    got = [tuple(map(int, r)) for r in oracle.chain(runs, recs, g.offsets, recs, g.offsets, p).tolist()]
+    R = [tuple(r) for r in recs.tolist()]
+    tau = oracle.tau(p["k"], p["delta_m"], p["delta_g"])
+    return got, lambda slip=None: bf.chain_rows(runs.tolist(), R, g.offsets, R, g.offsets, p,
+                                                tau, slip)
+
+
+@pytest.mark.parametrize("kind,seed,p", CHAIN_CASES)
+def test_chain_rows_match_bruteforce(kind, seed, p):
+    """orc_chain as the self-search calls it, against Section 3.3 restated by
+    exhaustive path enumeration: anchor sets rebuilt from the raw records
+    (target span [j_a, j_b+n-k], self-span exclusion, o = 1 axis flip), every
+    maximal chain enumerated, the tie rule applied to the longest ones
+    (chain end: the earliest anchor; then the later predecessor at every
+    step), and chains below m(s) dropped.  Whole rows must match."""
+    got, want = _chain_case(kind, seed, p)
+    assert len(got) > 0
+    assert got == want()
+
+
+def test_chain_pin_detects_each_slip():
+    """Every plausible slip (predecessor or end tie reversed, target span one
+    short, self-span rule dropped, no o = 1 axis flip, no m(s) drop) changes
+    at least one row of the cases above, so the pin would catch it."""
+    cases = [_chain_case(*c) for c in CHAIN_CASES]
+    for slip in CHAIN_SLIPS:
+        assert any(got != want(slip) for got, want in cases), slip
 
 
 def test_chain_rows_are_colinear_boxes():

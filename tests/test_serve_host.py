@@ -39,3 +39,54 @@ def test_plain_mode_takes_one_request():
     adm = Admission(max_batch_bases=1, reserve_bytes=0, free_bytes_fn=lambda: 1 << 40)
     q = reqs([5000, 10, 10])
     assert len(adm.take(q)) == 1 and len(adm.take(q)) == 1 and len(adm.take(q)) == 1
+
+
+def test_failed_batch_does_not_stall_the_server(monkeypatch):
+    """A batch whose search raises (an allocation failure, say) marks its
+    requests failed; the worker keeps serving and run_load reports the
+    failure instead of waiting forever."""
+    import pytest
+
+    from paper_1807_00205_gb300 import serve
+
+    class FakeCtx:
+        def close(self):
+            pass
+
+    def fake_search(ctx, index, reqs, p):
+        if any(r.rid == 3 for r in reqs):
+            raise MemoryError("device allocation failed")
+        for r in reqs:
+            r.cands = np.zeros(0)
+
+    monkeypatch.setattr(serve, "search", fake_search)
+    srv = serve.Server(None, None, workers=2, batching=False, free_bytes_fn=lambda: 1 << 40,
+                       reserve_bytes=0, ctx_factory=FakeCtx)
+    srv.start()
+    pool = [np.zeros(100, dtype=np.uint8)]
+    with pytest.raises(RuntimeError, match="1 requests failed"):
+        serve.run_load(srv, pool, rate=5000.0, count=8, seed=1, deadline_s=30)
+    assert len(srv.completed) == 8
+    assert all(r.cands is not None for r in srv.completed if r.rid != 3)
+    srv.close()
+
+
+def test_run_load_deadline(monkeypatch):
+    """A request that never completes ends run_load with a TimeoutError."""
+    import pytest
+
+    from paper_1807_00205_gb300 import serve
+
+    class FakeCtx:
+        def close(self):
+            pass
+
+    srv = serve.Server(None, None, workers=1, batching=False, free_bytes_fn=lambda: 0,
+                       reserve_bytes=1, ctx_factory=FakeCtx)  # nothing is ever admitted
+    srv.start()
+    with pytest.raises(TimeoutError):
+        serve.run_load(srv, [np.zeros(10, dtype=np.uint8)], rate=1000.0, count=2, seed=0,
+                       deadline_s=0.5)
+    with srv.cv:
+        srv.queue.clear()
+    srv.close()
