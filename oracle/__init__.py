@@ -92,6 +92,9 @@ def _load():
             lib.orc_qgram_shared.argtypes = [vp, i64, i64, i64, i32, i32]
             lib.orc_qgram.restype = vp
             lib.orc_qgram.argtypes = [vp, vp, i64, i64, vp, i32, ctypes.c_double]
+            lib.orc_extend.restype = vp
+            lib.orc_extend.argtypes = [vp, i64, i64, vp, i64, vp, i32, vp, i64, vp, i32, vp, i64,
+                                       i32]
             _lib = lib
     return _lib
 
@@ -256,6 +259,26 @@ def qgram(seq: np.ndarray, runs: np.ndarray, p: dict, q: int = 4, p_gap: float =
     runs = _c(runs, np.int64).reshape(-1, len(RUN_COLS))
     h = lib.orc_qgram(_ptr(seq), _ptr(runs), len(runs), len(RUN_COLS), _ptr(_par_array(p)),
                       int(q), float(p_gap))
+    return _table(lib, h)
+
+
+EXTEND_COLS = ["i", "o", "j_star", "qa", "qb", "ta", "tb", "est", "den"]
+MAX_SD_LENGTH = 1_000_000  # Section 3.2: potential SDs of at most 1 Mbp
+
+
+def extend(runs, qrecs_all, qoff, trecs_all, toff, p: dict, max_len: int = MAX_SD_LENGTH,
+           threads: int = 1) -> np.ndarray:
+    """f1 (Section 3.2): one potential SD region per kept seed, in run order
+    (see EXTEND_COLS; global coordinates).  qrecs_all / trecs_all are the
+    extension sketches: all k-mers, masked ones included (sketch with
+    min_unmasked = 0).  `threads` > 1 shares the seeds out to threads."""
+    lib = _load()
+    runs = _c(runs, np.int64).reshape(-1, len(RUN_COLS))
+    qrecs_all, trecs_all = _c(qrecs_all, np.int64), _c(trecs_all, np.int64)
+    qoff, toff = _c(qoff, np.int64), _c(toff, np.int64)
+    h = lib.orc_extend(_ptr(runs), len(runs), runs.shape[1], _ptr(qrecs_all), len(qrecs_all),
+                       _ptr(qoff), len(qoff) - 1, _ptr(trecs_all), len(trecs_all), _ptr(toff),
+                       len(toff) - 1, _ptr(_par_array(p)), int(max_len), int(threads))
     return _table(lib, h)
 
 

@@ -22,6 +22,8 @@
 //   merge     Section 3 (seeds grown into larger regions while similar),
 //             restated at chain granularity
 //   tau       Section 3.1 closed form tau >= (1-dG)/(1+dG) / (2 e^{k dM} - 1)
+//   extend    Section 3.2 (seeds grown into potential SD regions while the
+//             winnowed MinHash estimate stays >= tau; all k-mers)
 //
 // Readings where the paper is silent are listed in the design notes; the code
 // below states each one where it is used.
@@ -813,6 +815,176 @@ void* orc_qgram(const uint8_t* seq, const int64_t* runs, int64_t nruns, int64_t 
     const int64_t Q = orc_qgram_shared(seq, i, jstar, P.n, (int)o, q);
     T->row({Q, Q >= need ? 1 : 0});
   }
+  return T;
+}
+
+}  // extern "C"
+
+// ---- f1 SD extension: seeds grown into potential SD regions (Section 3.2) --
+// For every kept seed (i, j*, o) the query region starts as [i, i+n) and the
+// target region as [j*, j*+n).  W_Q and W_T are the minimizers of the
+// extension sketch (all k-mers, masked ones included: Section 3.2, last
+// paragraph) whose k-mer span lies inside the region.  The regions grow by
+// one base per step on each side (n and m increase together); for o = 1 the
+// target grows at the opposite end, since its copy is reverse-complemented.
+// After every step the winnowed MinHash estimate is taken as in Section 2.2,
+// with s = |W_Q| (distinct hashes): U = the s smallest hashes of W_Q u W_T,
+// est = hashes of U in W_Q and in W_T with relative strand o; the step is
+// kept while est >= m(s) = the least integer >= tau*s - 1e-9.  Growth stops
+// at the first step whose estimate falls below, that would leave a
+// sequence, that would make a region longer than max_len, or (query and
+// target on one sequence of a self search) that would make the two regions
+// overlap more than they already do.  Forward growth (right ends) runs first,
+// then backward growth (left ends) from its result.  In a self search a
+// target minimizer inside the query region's own k-mer span is the same
+// genome position, so it joins the union but is never shared.
+// Rows per kept run (global coordinates):
+//   i, o, j_star, qa, qb, ta, tb, est, den
+namespace {
+
+struct ExtState {
+  std::map<uint64_t, int> q;                    // hash -> query strand mask
+  std::map<uint64_t, std::pair<int, int>> t;    // hash -> (target records, shareable strand mask)
+};
+
+// est and den of the current regions (Section 2.2 estimator, s = |W_Q|).
+void ext_estimate(const ExtState& S, int o, int64_t* est, int64_t* den) {
+  const int64_t s = (int64_t)S.q.size();
+  auto a = S.q.begin();
+  auto b = S.t.begin();
+  int64_t taken = 0, e = 0;
+  while (taken < s && (a != S.q.end() || b != S.t.end())) {
+    uint64_t h;
+    if (b == S.t.end() || (a != S.q.end() && a->first <= b->first)) h = a->first;
+    else h = b->first;
+    const bool in_q = a != S.q.end() && a->first == h;
+    const bool in_t = b != S.t.end() && b->first == h;
+    if (in_q && in_t) {
+      const int qm = a->second, tm = b->second.second;
+      // some query strand sq and target strand st with sq ^ st == o
+      const int tm_o = o ? (((tm & 1) << 1) | ((tm >> 1) & 1)) : tm;
+      if (qm & tm_o) ++e;
+    }
+    ++taken;
+    if (in_q) ++a;
+    if (in_t) ++b;
+  }
+  *est = e;
+  *den = taken;
+}
+
+// The record starting at `pos`, if the extension sketch has one there.
+const Rec* rec_at(const std::vector<Rec>& recs, int64_t pos) {
+  auto it = std::lower_bound(recs.begin(), recs.end(), pos,
+                             [](const Rec& r, int64_t p) { return r.pos < p; });
+  return (it != recs.end() && it->pos == pos) ? &*it : nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+void* orc_extend(const int64_t* runs, int64_t nruns, int64_t run_cols, const int64_t* qrows,
+                 int64_t nq, const int64_t* qoff, int nqseq, const int64_t* trows, int64_t nt,
+                 const int64_t* toff, int ntseq, const int64_t* par, int64_t max_len,
+                 int nthreads) {
+  Par P = read_par(par);
+  std::vector<Rec> qrecs = rows_to_recs(qrows, nq);
+  std::vector<Rec> trecs = rows_to_recs(trows, nt);
+  auto qr = seq_ranges(qoff, nqseq);
+  auto tr = seq_ranges(toff, ntseq);
+  const double tau = tau_of(P.k, P.delta_m, P.delta_g);
+  const int64_t k = P.k;
+  std::vector<int64_t> kept;
+  for (int64_t r = 0; r < nruns; ++r)
+    if (runs[r * run_cols + 11]) kept.push_back(r);
+  const int64_t nk = (int64_t)kept.size();
+  std::vector<std::vector<int64_t>> out(nk);
+
+  auto one = [&](int64_t x) {
+    const int64_t* R = runs + kept[x] * run_cols;
+    const int64_t i = R[0], o = R[1], js = R[9];
+    const int qs = seq_of(qr, i), ts = seq_of(tr, js);
+    const int64_t qlo = qr[qs].first, qhi = qr[qs].second;
+    const int64_t tlo = tr[ts].first, thi = tr[ts].second;
+    const bool same = P.self_mode && qs == ts;
+    int64_t qa = i, qb = i + P.n, ta = js, tb = js + P.n;
+    ExtState S;
+    // a target record is shareable unless, in a self search, it lies in the
+    // query region's own k-mer span
+    auto add_q = [&](const Rec& r) { S.q[r.h] |= 1 << r.sigma; };
+    auto add_t = [&](const Rec& r, int64_t qa_, int64_t qb_) {
+      auto& c = S.t[r.h];
+      c.first += 1;
+      if (!(P.self_mode && r.pos >= qa_ && r.pos <= qb_ - k)) c.second |= 1 << r.sigma;
+    };
+    auto overlap = [&](int64_t a0, int64_t a1, int64_t b0, int64_t b1) -> int64_t {
+      return std::max<int64_t>(0, std::min(a1, b1) - std::max(a0, b0));
+    };
+    {
+      auto rq = pos_range(qrecs, qa, qb - k);
+      for (size_t y = rq.first; y < rq.second; ++y) add_q(qrecs[y]);
+      auto rt = pos_range(trecs, ta, tb - k);
+      for (size_t y = rt.first; y < rt.second; ++y) add_t(trecs[y], qa, qb);
+    }
+    int64_t est = 0, den = 0;
+    ext_estimate(S, (int)o, &est, &den);
+    const bool start_ok = est >= min_shared(tau, den);
+    for (int dir = 0; dir < 2 && start_ok; ++dir) {  // 0: right ends, 1: left ends
+      while (true) {
+        int64_t nqa = qa, nqb = qb, nta = ta, ntb = tb;
+        if (dir == 0) {
+          nqb = qb + 1;
+          if (o == 0) ntb = tb + 1; else nta = ta - 1;
+        } else {
+          nqa = qa - 1;
+          if (o == 0) nta = ta - 1; else ntb = tb + 1;
+        }
+        if (nqa < qlo || nqb > qhi || nta < tlo || ntb > thi) break;
+        if (nqb - nqa > max_len || ntb - nta > max_len) break;
+        if (same && overlap(nqa, nqb, nta, ntb) > overlap(qa, qb, ta, tb)) break;
+        // the k-mers that now fit in each region; their old entries are kept
+        // so that a failed step can be taken back
+        const Rec* nqr = dir == 0 ? rec_at(qrecs, nqb - k) : rec_at(qrecs, nqa);
+        if (!(nqr && nqr->pos >= nqa && nqr->pos <= nqb - k)) nqr = nullptr;
+        const Rec* ntr = (ntb != tb) ? rec_at(trecs, ntb - k) : rec_at(trecs, nta);
+        if (!(ntr && ntr->pos >= nta && ntr->pos <= ntb - k)) ntr = nullptr;
+        const bool q_had = nqr && S.q.count(nqr->h);
+        const int q_old = q_had ? S.q[nqr->h] : 0;
+        const bool t_had = ntr && S.t.count(ntr->h);
+        const std::pair<int, int> t_old = t_had ? S.t[ntr->h] : std::pair<int, int>(0, 0);
+        if (nqr) add_q(*nqr);
+        if (ntr) add_t(*ntr, nqa, nqb);
+        // the estimate changes only when a minimizer joined a region
+        int64_t e2 = est, d2 = den;
+        if (nqr || ntr) ext_estimate(S, (int)o, &e2, &d2);
+        if (e2 < min_shared(tau, d2)) {  // back to the last good state
+          if (nqr) {
+            if (q_had) S.q[nqr->h] = q_old; else S.q.erase(nqr->h);
+          }
+          if (ntr) {
+            if (t_had) S.t[ntr->h] = t_old; else S.t.erase(ntr->h);
+          }
+          break;
+        }
+        qa = nqa, qb = nqb, ta = nta, tb = ntb;
+        est = e2, den = d2;
+      }
+    }
+    out[x] = {i, o, js, qa, qb, ta, tb, est, den};
+  };
+  if (nthreads < 1) nthreads = 1;
+  std::atomic<int64_t> next(0);
+  auto work = [&]() {
+    for (int64_t x; (x = next.fetch_add(1)) < nk;) one(x);
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nthreads; ++t) th.emplace_back(work);
+  work();
+  for (auto& t : th) t.join();
+  Table* T = new Table();
+  T->ncols = 9;
+  for (auto& row : out) T->v.insert(T->v.end(), row.begin(), row.end());
   return T;
 }
 

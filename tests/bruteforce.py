@@ -288,3 +288,76 @@ def chain_rows(runs, qrecs, qoff, trecs, toff, p, tau, slip=None):
         rows.append((i, o, _seq_index(qoff, i), min(ps), max(ps) + p["k"], _seq_index(toff, ja),
                      min(ts), max(ts) + p["k"], score, s))
     return rows
+
+
+# -------------------------------------------------------------- extension --
+
+def _region_estimate(qrecs, trecs, qa, qb, ta, tb, p, o):
+    """Section 2.2 estimate of two regions from explicit sets: W_Q, W_T the
+    minimizers whose k-mer lies in each region; s = |W_Q|; U = the s smallest
+    of W_Q u W_T; est = hashes of U shared with relative strand o (in a self
+    search a target minimizer inside the query's k-mer span is not shared)."""
+    k = p["k"]
+    Q = {}
+    for h, pos, sg in qrecs:
+        if qa <= pos <= qb - k:
+            Q.setdefault(h, set()).add(sg)
+    T_all, T_sh = set(), {}
+    for h, pos, sg in trecs:
+        if ta <= pos <= tb - k:
+            T_all.add(h)
+            if not (p["self_mode"] and qa <= pos <= qb - k):
+                T_sh.setdefault(h, set()).add(sg)
+    s = len(Q)
+    U = sorted(set(Q) | T_all)[:s]
+    est = sum(1 for h in U if h in Q and h in T_sh
+              and any((a ^ b) == o for a in Q[h] for b in T_sh[h]))
+    return est, len(U)
+
+
+def extend_rows(runs, qrecs, qoff, trecs, toff, p, tau, max_len, slip=None):
+    """Section 3.2 restated: every kept seed's regions grown one base per
+    side per step, forward then backward, while the estimate of the grown
+    regions (recomputed from scratch) stays >= m(s), inside the sequences,
+    within max_len, and (self search, one sequence) without the regions
+    overlapping more than before the step.  Rows (i, o, j*, qa, qb, ta, tb,
+    est, den).  `slip` ("no_mirror": o = 1 targets grow like o = 0 ones) is
+    used only to show that the pin sees such a mistake."""
+    n = p["n"]
+    rows = []
+    for run in runs:
+        if int(run[11]) != 1:
+            continue
+        i, o, js = int(run[0]), int(run[1]), int(run[9])
+        qs, ts = _seq_index(qoff, i), _seq_index(toff, js)
+        qlo, qhi = int(qoff[qs]), int(qoff[qs + 1])
+        tlo, thi = int(toff[ts]), int(toff[ts + 1])
+        same = p["self_mode"] and qs == ts
+        qa, qb, ta, tb = i, i + n, js, js + n
+        est, den = _region_estimate(qrecs, trecs, qa, qb, ta, tb, p, o)
+
+        def ovl(a0, a1, b0, b1):
+            return max(0, min(a1, b1) - max(a0, b0))
+
+        if est >= m_of(tau, den):
+            mirror = o == 1 and slip != "no_mirror"
+            for direction in (0, 1):
+                while True:
+                    if direction == 0:
+                        nqa, nqb = qa, qb + 1
+                        nta, ntb = (ta - 1, tb) if mirror else (ta, tb + 1)
+                    else:
+                        nqa, nqb = qa - 1, qb
+                        nta, ntb = (ta, tb + 1) if mirror else (ta - 1, tb)
+                    if nqa < qlo or nqb > qhi or nta < tlo or ntb > thi:
+                        break
+                    if nqb - nqa > max_len:
+                        break
+                    if same and ovl(nqa, nqb, nta, ntb) > ovl(qa, qb, ta, tb):
+                        break
+                    e2, d2 = _region_estimate(qrecs, trecs, nqa, nqb, nta, ntb, p, o)
+                    if e2 < m_of(tau, d2):
+                        break
+                    qa, qb, ta, tb, est, den = nqa, nqb, nta, ntb, e2, d2
+        rows.append((i, o, js, qa, qb, ta, tb, est, den))
+    return rows

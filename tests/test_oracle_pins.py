@@ -576,3 +576,88 @@ def test_qgram_rows_follow_the_threshold():
     for r in np.nonzero(keep)[0][:10]:
         i, o, js = runs[r, 0], runs[r, 1], runs[r, oracle.RUN_COLS.index("j_star")]
         assert rows[r, 0] == oracle.qgram_shared(g.seq, i, js, 750, o, 4)
+
+
+# ------------------------------------------------------- f1 SD extension ----
+
+EXTEND_CASES = [
+    ("tiny", 51, dict(TINY), 400),
+    ("tiny", 52, dict(TINY, self_mode=0), 400),
+    ("tiny", 54, dict(TINY, self_mode=2), 400),
+    ("tiny", 57, dict(TINY), 120),                 # the length cap binds
+    ("tiny", 58, dict(TINY, min_unmasked=2), 400),
+    ("tandem", 60, dict(TINY), 400),               # overlapping mates
+    ("end_dup", 81, dict(TINY, step=1), 400),      # regions reach sequence ends
+    ("end_dup", 89, dict(TINY, step=1), 400),
+]
+
+
+def _extend_case(kind, seed, p, max_len):
+    g = {"tiny": tiny_genome, "tandem": tandem_genome, "end_dup": end_dup_genome}[kind](seed)
+    recs = oracle.sketch(g.seq, g.offsets, p)
+    runs = oracle.filter_runs(recs, g.offsets, recs, g.offsets, p)
+    allk = oracle.sketch(g.seq, g.offsets, dict(p, min_unmasked=0))  # Section 3.2: any k-mer
+    got = [tuple(map(int, r)) for r in
+           oracle.extend(runs, allk, g.offsets, allk, g.offsets, p, max_len=max_len).tolist()]
+    R = [tuple(r) for r in allk.tolist()]
+    tau = oracle.tau(p["k"], p["delta_m"], p["delta_g"])
+    return g, got, lambda slip=None: bf.extend_rows(runs.tolist(), R, g.offsets, R, g.offsets,
+                                                    p, tau, max_len, slip)
+
+
+@pytest.mark.parametrize("kind,seed,p,max_len", EXTEND_CASES)
+def test_extend_matches_bruteforce(kind, seed, p, max_len):
+    """Section 3.2 restated step by step: the grown regions' estimate is
+    recomputed from explicit sets after every one-base step on each side;
+    the oracle's incremental growth must stop at the same regions."""
+    g, got, want = _extend_case(kind, seed, p, max_len)
+    assert len(got) > 0 and any(r[4] - r[3] > p["n"] for r in got)
+    assert got == want()
+
+
+def test_extend_mirror_is_pinned():
+    """For o = 1 the target grows at the opposite end; growing it like o = 0
+    changes rows of the cases above."""
+    cases = [_extend_case(*c) for c in EXTEND_CASES]
+    assert any(got != want("no_mirror") for _, got, want in cases)
+
+
+def test_extend_limits_hold():
+    """Regions grow in lockstep (equal lengths), stay inside their sequences,
+    never exceed max_len, never overlap more than their seed did, and every
+    grown region still passes the threshold."""
+    tau = oracle.tau()
+    for kind, seed, p, max_len in EXTEND_CASES:
+        g, got, _ = _extend_case(kind, seed, p, max_len)
+        m = oracle.mtable(p["k"], p["delta_m"], p["delta_g"], smax=4096)
+        for i, o, js, qa, qb, ta, tb, est, den in got:
+            assert qb - qa == tb - ta <= max(max_len, p["n"])
+            qs = np.searchsorted(g.offsets, i, side="right") - 1
+            ts = np.searchsorted(g.offsets, js, side="right") - 1
+            assert g.offsets[qs] <= qa <= i and i + p["n"] <= qb <= g.offsets[qs + 1]
+            assert g.offsets[ts] <= ta and tb <= g.offsets[ts + 1]
+            if p["self_mode"] and qs == ts:
+                ov = max(0, min(qb, tb) - max(qa, ta))
+                assert ov <= max(0, min(i + p["n"], js + p["n"]) - max(i, js))
+            if qb - qa > p["n"]:
+                assert est >= m[den] and est >= tau * den - 1e-9
+
+
+def test_extension_contains_planted_duplications():
+    """The purpose of Section 3.2: seeds (750 bp) grown until the estimate
+    drops find the boundaries of the duplications.  For every planted pair
+    (2-8 kbp, 90-99.5% identity) one potential SD region holds both whole
+    mates, which no single seed window can."""
+    g = synth.small_case(41, lengths=(400_000,), n_sd=8, sd_lo=2000, sd_hi=8000,
+                         id_lo=0.90, id_hi=0.995)
+    p = oracle.params()
+    r = oracle.selfsearch(g.seq, g.offsets, p, threads=8)
+    allk = oracle.sketch(g.seq, g.offsets, oracle.params(min_unmasked=0))
+    ext = oracle.extend(r["runs"], allk, g.offsets, allk, g.offsets, p, threads=8)
+    assert len(g.planted) >= 6
+    for sd in g.planted:
+        a, b = (sd.src, sd.src + sd.length), (sd.dst, sd.dst + sd.copy_length)
+        first, second = (a, b) if a[0] < b[0] else (b, a)
+        o = 1 if sd.reverse else 0
+        assert any(row[1] == o and row[3] <= first[0] and row[4] >= first[1]
+                   and row[5] <= second[0] and row[6] >= second[1] for row in ext.tolist()), sd
