@@ -1,18 +1,21 @@
 #!/usr/bin/env python
 """Throughput of the SEDEF seeding filter on one GB300 (or N replicas).
 
-A step is one pass of the whole path over a device-resident genome: pack,
+A step is one pass of the whole path over a device-resident input: pack,
 sketch, index, filter (candidate lookup, sliding count, refine), chain and
-merge, through the C ABI.  The default workload is the chromosome-scale
-self-search: 100 Mbp at 41% GC, ~40% soft-masked repeats (300 bp and 6 kbp
-families), N-gaps every ~10 Mbp and 2,000 planted duplications of 1-200 kbp
-at 75-99.5% identity in both orientations (synthetic, seeded).
+merge, as one call of the C ABI (sedef_selfsearch).  The default workload is
+the batch: 200 independent synthetic genomes of 1-20 Mbp (log-uniform, 1.43
+Gbp in all; 41% GC, 30% soft-masked repeats, 50-500 planted duplications of
+1-50 kbp at 75-99% identity), self-searched in one persistent pass
+(self_mode 2), beside the plain form (one pass per genome).  Other
+workloads: the 100 Mbp chromosome, the 2 Mbp plain genome, the 3.1 Gbp
+human-scale assembly (self-search) and serving against its resident index.
 
 Prints one JSON line (rank 0).  `value` is query Mbp/s of the whole job (all
 ranks); `e2e` repeats the measurement through sedef_selfsearch_host with the
-genome in pinned host memory and the candidates copied back; `roofline`
-relates the dominant kernel's algorithmic bytes to the measured HBM peak;
-`cpu_baseline` times the CPU oracle on a bounded sample.
+input in pinned host memory and the candidates copied back; `roofline`
+relates the dominant kernel family's algorithmic bytes (or instructions) to
+the measured peak; `cpu_baseline` times the CPU oracle on a bounded sample.
 
 --impl reference times the CPU oracle (the reference arm of this build) on a
 bounded sample of the same workload.
@@ -20,6 +23,7 @@ bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -34,23 +38,45 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "query Mbp/s through sketch+Jaccard filter+chain (batched/served vs plain), p99 latency, HBM %"
-WORKLOAD = "chromosome-100Mbp self-search (41% GC, 40% soft-masked repeats, N-gaps, 2000 planted SDs 1-200 kbp)"
 WORKLOADS = {
-    "chromosome": WORKLOAD,
+    "batch": "batch of 200 independent genomes, 1-20 Mbp log-uniform (1.43 Gbp), 41% GC, 30% "
+             "soft-masked repeats, 50-500 planted SDs of 1-50 kbp at 75-99% identity; one "
+             "persistent pass (self_mode 2) vs one pass per genome",
+    "chromosome": "chromosome-100Mbp self-search (41% GC, 40% soft-masked repeats, N-gaps, 2000 "
+                  "planted SDs 1-200 kbp)",
     "plain": "plain-2Mbp self-search (i.i.d. ACGT, 20 planted SDs 1-20 kbp)",
-    "human": "human-scale 3.1 Gbp self-search (24 chromosomes of 50-250 Mbp, 41% GC, 50% soft-masked "
-             "repeats, N-gaps, 20000 planted SDs 1-300 kbp intra- and inter-chromosomal)",
+    "human": "human-scale 3.1 Gbp self-search (24 chromosomes of 50-250 Mbp, 41% GC, 50% "
+             "soft-masked repeats, N-gaps, 20000 planted SDs 1-300 kbp intra- and "
+             "inter-chromosomal)",
 }
-
-
-def make_genome(name: str):
-    from paper_1807_00205_gb300 import synth
-    return {"chromosome": synth.chromosome_100mbp, "plain": synth.plain_2mbp,
-            "human": synth.human_3gbp}[name]()
-
-
-CPU_SAMPLE_BASES = 10_000_000
 FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 256 << 20
+COUNTERS = os.path.join(ROOT, "profiles", "roofline_counters.json")
+
+# kernel families (trace stage labels) and the bound that holds for each
+HBM_FAMILIES = ("pack", "sketch", "index", "filter")
+ISSUE_FAMILIES = ("refine", "runsort", "chain", "merge")
+
+
+class Workload:
+    def __init__(self, name, seq, offsets, self_mode, genomes=None):
+        self.name, self.seq, self.offsets, self.self_mode = name, seq, offsets, self_mode
+        self.genomes = genomes
+
+    @property
+    def length(self) -> int:
+        return int(self.offsets[-1])
+
+
+def make_workload(name: str, max_genomes=None) -> Workload:
+    from paper_1807_00205_gb300 import batch, synth
+    if name == "batch":
+        gs = synth.batch_genomes(max_genomes=max_genomes)
+        seq, offs = batch.concatenate(gs)
+        return Workload(name, seq, offs, 2, gs)
+    g = {"chromosome": synth.chromosome_100mbp, "plain": synth.plain_2mbp,
+         "human": synth.human_3gbp}[name]()
+    return Workload(name, g.seq, g.offsets, 1)
 
 
 def peaks():
@@ -135,233 +161,201 @@ def dist_info():
     return ws, rank, local
 
 
-def algorithmic_bytes(seq, offsets, rec_rows, sorted_rows, runs, k, n, step):
-    """Minimum bytes each kernel family must move per launch (see the
-    design notes).  Records are 8 bytes."""
-    N = int(offsets[-1])
-    nrec = len(rec_rows)
+# ------------------------------------------------------------ accounting --
+
+def family_of(key: str) -> str:
+    """Trace key "stage:kernel" -> kernel family (the stage label)."""
+    return key.split(":", 1)[0] if ":" in key else "other"
+
+
+def filter_algorithmic_bytes(rec, offsets, k, n, step, self_mode, nruns) -> dict:
+    """The filter's algorithmic bytes for one pass, counted on the device:
+    per query window, its query records (8 B each), one offset pair per
+    distinct hash of W_Q (8 B) and every posting of those hashes (4 B: the
+    position and strand a posting must carry; in self_mode 2 the postings
+    of the window's own genome), plus the runs written (32 B each)."""
+    import torch
+    dev = rec.device
+    r = rec.view(torch.int64)
+    h = r >> 33
+    pos = (r >> 1) & 0xFFFFFFFF
+    off = torch.as_tensor(np.asarray(offsets, dtype=np.int64), device=dev)
+    seq = torch.searchsorted(off, pos, right=True) - 1
+    local = pos - off[seq]
+    lens = off[1:] - off[:-1]
+    nwin = torch.clamp((lens - n) // step + 1, min=0)
+    wbase = torch.zeros(len(nwin) + 1, dtype=torch.int64, device=dev)
+    wbase[1:] = torch.cumsum(nwin, 0)
     span = n - k
-    # filter: every window reads its query records, one offset pair per
-    # distinct query hash and every posting of those hashes once
-    pos, hsh = rec_rows[:, 1], rec_rows[:, 0]
-    occ = np.bincount(hsh, minlength=1 << (2 * k)).astype(np.int64)
-    # windows start at each sequence start, then every `step`, and end
-    # inside the sequence; number them globally
-    off = np.asarray(offsets, dtype=np.int64)
-    nwin = np.maximum(0, (np.diff(off) - n) // step + 1)
-    wbase = np.concatenate([[0], np.cumsum(nwin)])
-    sq = np.searchsorted(off, pos, side="right") - 1
-    local = pos - off[sq]
-    w_lo = np.ceil((local - span) / step).clip(min=0).astype(np.int64)
-    w_hi = np.minimum(local // step, nwin[sq] - 1).astype(np.int64)
-    filt_q = 0
-    pairs = []
-    for d in range(0, span // step + 2):
+    w_lo = torch.clamp(torch.div(local - span + step - 1, step, rounding_mode="floor"), min=0)
+    w_hi = torch.minimum(local // step, nwin[seq] - 1)
+    keys, nq = [], 0
+    for d in range(span // step + 2):
         w = w_lo + d
         ok = w <= w_hi
-        filt_q += int(ok.sum())
-        pairs.append(((wbase[sq[ok]] + w[ok]) << 32) | hsh[ok])
-    pairs = np.unique(np.concatenate(pairs))
-    hashes = (pairs & 0xFFFFFFFF).astype(np.int64)
-    filt = 8 * filt_q + 8 * len(pairs) + 8 * int(occ[hashes].sum())
-    # refine: per run the query records of its window and the target records
-    # of its span
-    ref = 0
-    if len(runs):
-        ja = runs["j_a"].astype(np.int64)
-        jb = runs["j_b"].astype(np.int64)
-        i = runs["i"].astype(np.int64)
-        a = np.searchsorted(pos, ja)
-        b = np.searchsorted(pos, jb + span, side="right")
-        qa = np.searchsorted(pos, i)
-        qb = np.searchsorted(pos, i + span, side="right")
-        ref = int(8 * ((b - a).sum() + (qb - qa).sum()) + 32 * len(runs))
-    return {
-        "k_pack": int(1.5 * N),
-        "k_sketch_count": int(0.5 * N),
-        "k_sketch_write": int(0.5 * N + 8 * nrec),
-        "k_rs_scatter": 16 * nrec,
-        "k_rs_hist": 8 * nrec,
-        "k_offsets": 8 * nrec + 4 * ((1 << (2 * k)) + 1),
-        "k_filter_fast": filt,
-        "k_refine": ref,
-    }
+        nq += int(ok.sum())
+        keys.append(((wbase[seq[ok]] + w[ok]) << 32) | h[ok])
+    pairs = torch.unique(torch.cat(keys))
+    del keys
+    ph = pairs & 0xFFFFFFFF
+    if self_mode == 2:
+        wid = pairs >> 32
+        wseq = torch.searchsorted(wbase, wid, right=True) - 1
+        rk, rc = torch.unique((seq << 32) | h, return_counts=True)
+        occ = rc[torch.searchsorted(rk, (wseq << 32) | ph)]
+    else:
+        occ = torch.bincount(h, minlength=1 << (2 * k))[ph]
+    postings = int(occ.sum())
+    return {"bytes": 4 * postings + 8 * int(pairs.numel()) + 8 * nq + 32 * int(nruns),
+            "postings": postings, "distinct_query_hashes": int(pairs.numel()),
+            "query_records": nq, "windows": int(wbase[-1])}
 
 
-def measured_traffic(kernel: str, field: str = "bytes_per_launch"):
-    """DRAM bytes (or another counter) per launch of `kernel` from the committed
-    ncu capture, or None when there is none or the kernel's source changed
-    since it was taken."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
-    if not os.path.exists(path):
+def algorithmic_bytes(N: int, nrec: int, k: int, filt: dict) -> dict:
+    """Minimum bytes each HBM-bound family must move per pass: pack 1.5 B
+    per base; sketch the packed input once (0.5 B per base) and 8 B per
+    record written; index one read and one write of every record (the
+    single-pass lower bound of a sort) and the 4^k + 1 offsets; filter as
+    counted by filter_algorithmic_bytes."""
+    return {"pack": int(1.5 * N), "sketch": int(0.5 * N + 8 * nrec),
+            "index": 16 * nrec + 4 * ((1 << (2 * k)) + 1), "filter": filt["bytes"]}
+
+
+def counters_entry(kernel: str, workload: str, variant: int):
+    """Per-unit ncu counters of `kernel` captured on this workload with this
+    filter shape, while its source file is unchanged; None otherwise."""
+    if not os.path.exists(COUNTERS):
         return None
-    with open(path) as f:
+    with open(COUNTERS) as f:
         d = json.load(f)
-    e = d.get(kernel)
-    if not e or not e.get("sha256"):
-        return None
-    src = os.path.join(ROOT, e["source"])
-    if not os.path.exists(src):
-        return None
-    with open(src, "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != e["sha256"]:
+    for e in d.get("entries", []):
+        if e.get("kernel") != kernel or e.get("workload") != workload:
+            continue
+        if e.get("filter_shape") is not None and e["filter_shape"] != variant:
+            continue
+        src = os.path.join(ROOT, e["source"])
+        if not os.path.exists(src):
             return None
-    return int(e[field]) if e.get(field) is not None else None
+        with open(src, "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != e["sha256"]:
+                return None
+        return e
+    return None
 
 
-def run_cpu_oracle_sample(seq, bases=CPU_SAMPLE_BASES, threads=1):
-    """The oracle self-searching a prefix of the workload: (Mbp/s, s, bases)."""
+# ---------------------------------------------------------- CPU baseline --
+
+def oracle_selfsearch_rate(W: Workload, min_bases: int, threads: int):
+    """The oracle self-searching a bounded sample of the workload: whole
+    leading genomes of a batch (they are independent), or a prefix of one
+    genome.  Returns (Mbp/s, seconds, bases, description)."""
     import oracle
-    X = min(bases, len(seq))
-    s = np.ascontiguousarray(seq[:X])
-    off = np.array([0, X], dtype=np.int64)
     oracle.build()
+    if W.genomes is not None:
+        take, tot = [], 0
+        for g in W.genomes:
+            take.append(g)
+            tot += g.length
+            if tot >= min_bases:
+                break
+        from paper_1807_00205_gb300 import batch
+        s, off = batch.concatenate(take)
+        pd = oracle.params(self_mode=2)
+        desc = f"self-search (self_mode 2) of the first {len(take)} genomes ({tot} bases)"
+    else:
+        X = min(min_bases, W.length)
+        s, off = np.ascontiguousarray(W.seq[:X]), np.array([0, X], dtype=np.int64)
+        pd = oracle.params()
+        desc = f"self-search of the first {X} bases"
     t = time.perf_counter()
-    oracle.selfsearch(s, off, oracle.params(), threads=threads)
+    oracle.selfsearch(s, off, pd, threads=threads)
     dt = time.perf_counter() - t
-    return X / dt / 1e6, dt, X
+    bases = int(off[-1])
+    return bases / dt / 1e6, dt, bases, desc
 
 
-def cpu_baseline_line(seq) -> dict:
-    """The oracle on all host cores (threads over windows) on a 30 Mbp
-    prefix, and on one core on a 10 Mbp prefix."""
+def cpu_baseline_line(W: Workload) -> dict:
     cores = os.cpu_count() or 1
-    v, dt, X = run_cpu_oracle_sample(seq, 3 * CPU_SAMPLE_BASES, threads=cores)
-    v1, dt1, X1 = run_cpu_oracle_sample(seq, CPU_SAMPLE_BASES, threads=1)
+    if W.name == "human":
+        return cpu_baseline_windows(W, cores)
+    v, dt, X, desc = oracle_selfsearch_rate(W, 30_000_000, cores)
     return {"value": v, "unit": "Mbp/s", "cores": cores, "kind": "oracle",
-            "sample": f"self-search of the first {X} bases of the workload ({dt:.1f} s wall, "
-                      f"threads over windows)",
-            "single_thread": {"value": v1, "unit": "Mbp/s", "cores": 1,
-                              "sample": f"first {X1} bases ({dt1:.1f} s)"}}
+            "sample": f"{desc}, threads over windows, {dt:.1f} s wall"}
+
+
+def cpu_baseline_windows(W: Workload, cores: int, nwin: int = 2000) -> dict:
+    """Human scale: the oracle's sketch of the whole genome, then the filter
+    over `nwin` evenly spaced query windows against the whole genome; Mbp/s
+    counts query_step bases per window (each window stands for that much of
+    the self-search)."""
+    import oracle
+    oracle.build()
+    pd = oracle.params()
+    t = time.perf_counter()
+    recs = oracle.sketch(W.seq, W.offsets, pd, threads=cores)
+    t_sk = time.perf_counter() - t
+    wins = []
+    for s in range(len(W.offsets) - 1):
+        st, en = int(W.offsets[s]), int(W.offsets[s + 1])
+        wins.extend(range(st, en - pd["n"] + 1, pd["step"]))
+    wins = np.asarray(wins, dtype=np.int64)
+    pick = wins[np.linspace(0, len(wins) - 1, nwin).astype(np.int64)]
+    t = time.perf_counter()
+    oracle.filter_runs(recs, W.offsets, recs, W.offsets, pd, windows=pick, threads=cores)
+    t_f = time.perf_counter() - t
+    per_win = t_f / nwin + t_sk / len(wins)
+    return {"value": pd["step"] / per_win / 1e6, "unit": "Mbp/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"sketch of all {W.length} bases ({t_sk:.0f} s) and filter of {nwin} "
+                      f"evenly spaced of {len(wins)} query windows ({t_f:.0f} s), extrapolated "
+                      f"at {pd['step']} query bases per window; threads on all cores"}
 
 
 def reference_arm(args):
     ws, rank, local = dist_info()
     if rank != 0:
         return
-    from paper_1807_00205_gb300 import synth
-    g = synth.chromosome_100mbp()
-    import oracle
-    oracle.build()
-    X = 10_000_000
+    if args.workload in ("serve", "human"):
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the CPU oracle cannot serve or self-search 3.1 Gbp within the bench's "
+                          "time; its sampled rate is the cpu_baseline of --workload human"}))
+        return
     cores = os.cpu_count() or 1
-    s = np.ascontiguousarray(g.seq[:X])
-    off = np.array([0, X], dtype=np.int64)
+    W = make_workload(args.workload, max_genomes=12 if args.workload == "batch" else None)
+    sample = 10_000_000
     for _ in range(args.warmup):
-        oracle.selfsearch(s, off, oracle.params(), threads=cores)
-    times = []
+        oracle_selfsearch_rate(W, sample, cores)
+    times, desc, bases = [], "", 0
     for _ in range(args.steps):
-        t = time.perf_counter()
-        oracle.selfsearch(s, off, oracle.params(), threads=cores)
-        times.append(time.perf_counter() - t)
+        _, dt, bases, desc = oracle_selfsearch_rate(W, sample, cores)
+        times.append(dt)
     ms = 1000 * sum(times) / len(times)
-    value = X / (ms / 1000) / 1e6
+    value = bases / (ms / 1000) / 1e6
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Mbp/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"self-search of the first {X} bases",
-                   "l2": "n/a (CPU)"},
+        "config": {"workload": WORKLOADS[args.workload], "sample": desc, "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": value, "unit": "Mbp/s", "cores": cores, "kind": "oracle",
-                         "sample": f"self-search of the first {X} bases of the workload, "
-                                   f"threads over windows"},
+                         "sample": f"{desc} of the workload, threads over windows"},
         "e2e": {"value": value, "unit": "Mbp/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def batch_arm(args):
-    """Many independent genomes: one pass over the whole batch (self_mode 2)
-    against one pass per genome, both on device-resident inputs."""
-    import torch
-    from paper_1807_00205_gb300 import batch, binding, synth
-    ws, rank, local = dist_info()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    t0 = time.time()
-    all_gs = synth.batch_genomes(count=args.batch_count)
-    gen_s = time.time() - t0
-    N_total = sum(g.length for g in all_gs)
-    gs = batch.shard(all_gs, rank, ws)  # each rank takes a length-balanced block of genomes
-    seq, offs = batch.concatenate(gs)
-    N = int(offs[-1])
-    stream = torch.cuda.Stream(dev)
-    ctx = binding.Context(local, stream=stream)
-    p = binding.params()
-    with torch.cuda.stream(stream):
-        d_all = torch.from_numpy(seq).to(dev)
-        d_each = [d_all[int(offs[g]):int(offs[g + 1])] for g in range(len(gs))]
-        offs_each = [np.array([0, len(g.seq)], dtype=np.int64) for g in gs]
-        flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)
-
-    def timed(fn):
-        with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
-                fn()
-                flush.fill_(1)
-            ms = []
-            for _ in range(args.steps):
-                flush.fill_(1)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                fn()
-                e1.record(stream)
-                e1.synchronize()
-                ms.append(e0.elapsed_time(e1))
-        return sum(ms) / len(ms)
-
-    with torch.cuda.stream(stream):
-        # the filter shape is autotuned once on the batch, before any timing
-        ctx.selfsearch(d_all, offs, binding.params_from_struct(p, self_mode=2), autotune=True)
-    launches0 = binding.Context.sedef_launch_count()
-    ms_b = timed(lambda: batch.batched(ctx, d_all, offs, p))
-    launches_b = (binding.Context.sedef_launch_count() - launches0) // (args.warmup + args.steps)
-    launches0 = binding.Context.sedef_launch_count()
-    ms_p = timed(lambda: batch.plain(ctx, d_each, offs_each, p))
-    launches_p = (binding.Context.sedef_launch_count() - launches0) // (args.warmup + args.steps)
-    out = batch.batched(ctx, d_all, offs, p)
-    ms_b = aggregate_max_ms(ms_b, ws, dev)
-    ms_p = aggregate_max_ms(ms_p, ws, dev)
-    if rank != 0:
-        ctx.close()
-        torch.distributed.destroy_process_group()
-        return
-    N = N_total
-    line = {
-        "metric": METRIC, "value": N / (ms_b / 1000) / 1e6, "unit": "Mbp/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
-        "scaling": "strong", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": f"batch of {len(gs)} independent genomes, 1-20 Mbp log-uniform, "
-                               f"41% GC, 30% soft-masked, 50-500 SDs of 1-50 kbp",
-                   "genome_bases": N, "generation_s": gen_s, "mode": "one pass, self_mode 2",
-                   "runs": int(out["nruns"]), "candidates": int(out["ncands"]),
-                   "l2": "inputs larger than L2 and a 256 MB L2 flush between steps"},
-        "gpu_launches": int(launches_b),
-        "plain": {"value": N / (ms_p / 1000) / 1e6, "unit": "Mbp/s", "ms_per_step": ms_p,
-                  "mode": "one pass per genome, self_mode 1", "gpu_launches": int(launches_p)},
-    }
-    print(json.dumps(line), flush=True)
-    ctx.close()
-    if ws > 1:
-        torch.distributed.destroy_process_group()
-
+# ---------------------------------------------------------------- serving --
 
 def serve_arm(args):
     """Resident index of the 3.1 Gbp human-scale workload (or the 100 Mbp
     chromosome); Poisson streams of query regions (10 kbp-5 Mbp, 0-25%
-    mutation) at each rate, served by two continuously batching workers and
+    mutation) at each rate, served by the continuously batching server and
     by the plain one-request-per-pass form."""
     import torch
     from paper_1807_00205_gb300 import binding, serve, synth
     ws, rank, local = dist_info()
     torch.cuda.set_device(local)
-    g = make_genome(args.serve_genome)
+    g = {"human": synth.human_3gbp, "chromosome": synth.chromosome_100mbp}[args.serve_genome]()
     pool = synth.query_regions(g, 48)
     p = binding.params()
     ctx = binding.Context(local)
@@ -377,12 +371,13 @@ def serve_arm(args):
             srv.close()
         results.append(row)
     top = results[-1]
+    name = "human" if args.serve_genome == "human" else "chromosome"
     line = {
         "metric": METRIC, "value": top["served"]["mbp_s"], "unit": "Mbp/s", "n_gpus": 1,
         "steps": args.requests, "warmup": 2, "ms_per_step": top["served"]["mean_ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": f"serving: resident index of the {WORKLOADS[args.serve_genome]}; "
+        "config": {"workload": f"serving: resident index of the {WORKLOADS[name]}; "
                                "Poisson query regions 10 kbp-5 Mbp log-uniform cut from it "
                                "with 0-25% mutation",
                    "served": "2 workers (own streams), continuous batching, admission by free HBM",
@@ -393,37 +388,32 @@ def serve_arm(args):
     ctx.close()
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="chromosome",
-                    choices=["chromosome", "plain", "human", "batch", "serve"])
-    ap.add_argument("--serve-genome", default="human", choices=["human", "chromosome"],
-                    help="serving: the genome whose index stays resident")
-    ap.add_argument("--batch-count", type=int, default=200,
-                    help="genomes in the batch workload")
-    ap.add_argument("--rates", default="50,200,1000", help="serving: request rates per second")
-    ap.add_argument("--requests", type=int, default=200, help="serving: requests per rate")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
-    ap.add_argument("--no-graph", action="store_true", help="skip the captured-graph measurement")
-    ap.add_argument("--trace", action="store_true", help="print the per-kernel table to stderr")
-    args = ap.parse_args()
-    if args.impl == "reference":
-        reference_arm(args)
-        return
-    if args.workload == "batch":
-        batch_arm(args)
-        return
-    if args.workload == "serve":
-        serve_arm(args)
-        return
+# ------------------------------------------------------------- main arm --
 
+def timed_steps(stream, flush, steps, warmup, fn):
+    """Mean ms of `steps` calls of fn on `stream` (CUDA events, an L2 flush
+    outside the events before each), after `warmup` untimed calls."""
     import torch
-    from paper_1807_00205_gb300 import binding, synth
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            fn()
+            flush.fill_(1)
+        ms = []
+        for _ in range(steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    return sum(ms) / len(ms)
+
+
+def run_workload(args):
+    import torch
+    from paper_1807_00205_gb300 import binding
 
     ws, rank, local = dist_info()
     if ws > 1:
@@ -431,33 +421,38 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    g = make_genome(args.workload)
-    N = g.length
-    p = binding.params()
+    t0 = time.time()
+    W = make_workload(args.workload)
+    gen_s = time.time() - t0
+    N = W.length
+    p = binding.params(self_mode=W.self_mode)
     stream = torch.cuda.Stream(dev)
     ctx = binding.Context(local, stream=stream)
     with torch.cuda.stream(stream):
-        d_seq = torch.from_numpy(g.seq).to(dev)
-        flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)  # 256 MB > L2
-    stream.synchronize()
-
-    def step():
-        return ctx.selfsearch(d_seq, g.offsets, p)
-
-    with torch.cuda.stream(stream):
-        # the filter's first-tier shape is autotuned once, before any timing
-        out = ctx.selfsearch(d_seq, g.offsets, p, autotune=True)
-        variant = ctx.sedef_filter_variant()[0]
-        for _ in range(args.warmup):
-            out = step()
-            flush.fill_(1)
+        d_seq = torch.from_numpy(W.seq).to(dev)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     stream.synchronize()
 
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
 
-    # ---- timed region: device-resident input
+    # the filter's first-tier shape is autotuned once, then one pass stage by
+    # stage keeps every intermediate for the accounting below (untimed)
+    with torch.cuda.stream(stream):
+        out = ctx.selfsearch(d_seq, W.offsets, p, autotune=True)
+        variant = ctx.sedef_filter_variant()[0]
+        out = ctx.selfsearch(d_seq, W.offsets, p)
+    fstats = ctx.sedef_filter_stats()
+
+    def step():
+        return ctx.sedef_selfsearch(d_seq, W.offsets, p)
+
+    with torch.cuda.stream(stream):
+        cands, ncands = step()  # sizes the context's buffers
+    stream.synchronize()
+
+    # ---- timed region: device-resident input, one C call per step
     barrier()
     torch.cuda.synchronize()
     clocks = Clocks(local)
@@ -465,28 +460,41 @@ def main():
     ctx.sedef_trace_report(reset=True)
     ctx.sedef_trace_enable(True)
     launches0 = binding.Context.sedef_launch_count()
-    step_ms = []
-    with torch.cuda.stream(stream):
-        for _ in range(args.steps):
-            flush.fill_(1)  # L2 flush between steps, outside the step's events
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            out = step()
-            e1.record(stream)
-            e1.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
-    launches = binding.Context.sedef_launch_count() - launches0
-    trace = ctx.sedef_trace_report(reset=True)
-    fstats = ctx.sedef_filter_stats()
+    ms = timed_steps(stream, flush, args.steps, args.warmup, step)
+    launches = (binding.Context.sedef_launch_count() - launches0) * args.steps // \
+        (args.steps + args.warmup)
     ctx.sedef_trace_enable(False)
+    trace = ctx.sedef_trace_report(reset=True)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = aggregate_max_ms(sum(step_ms) / len(step_ms), ws, dev)
+    # the trace covers warm-up and timed steps alike: per-step figures divide
+    # by their sum
+    nsteps = args.steps + args.warmup
+    ms = aggregate_max_ms(ms, ws, dev)
     value = ws * N / (ms / 1000) / 1e6
 
-    # ---- the q-gram filter (Section 3.2) on the step's kept seeds, timed alone
+    # ---- plain form of the batch: one pass per genome (self_mode 1)
+    plain = None
+    if W.genomes is not None:
+        pp = binding.params(self_mode=1)
+        views = [d_seq[int(W.offsets[g]):int(W.offsets[g + 1])] for g in range(len(W.genomes))]
+        offs1 = [np.array([0, int(W.offsets[g + 1] - W.offsets[g])], dtype=np.int64)
+                 for g in range(len(W.genomes))]
+
+        def plain_step():
+            for v, o in zip(views, offs1):
+                ctx.sedef_selfsearch(v, o, pp)
+
+        l0 = binding.Context.sedef_launch_count()
+        ms_p = timed_steps(stream, flush, args.steps, args.warmup, plain_step)
+        lp = (binding.Context.sedef_launch_count() - l0) * args.steps // nsteps
+        ms_p = aggregate_max_ms(ms_p, ws, dev)
+        plain = {"value": ws * N / (ms_p / 1000) / 1e6, "unit": "Mbp/s", "ms_per_step": ms_p,
+                 "mode": "one sedef_selfsearch call per genome (self_mode 1)",
+                 "gpu_launches": int(lp), "batched_over_plain": ms_p / ms}
+
+    # ---- the q-gram filter (Section 3.2) on the pass's kept seeds, timed alone
     with torch.cuda.stream(stream):
         qms = []
         for it in range(args.warmup + args.steps):
@@ -503,127 +511,122 @@ def main():
     qgram_info = {"q": 4, "p_gap": 0.005, "ms": sum(qms) / len(qms), "kept_seeds": kept,
                   "passed": int(npass), "bytes_per_seed": 2 * p.n // 4}
 
-    # ---- the same step as one captured graph (sedef_graph_*): built once,
-    # outside the timing, then replayed
+    # ---- the same pass as one captured graph (sedef_graph_*)
     graph_info = None
     try:
         if args.no_graph:
             raise RuntimeError("skipped (--no-graph)")
         with torch.cuda.stream(stream):
-            # capacities from the eager step's counts (x 1.25)
             caps = binding.caps_from_run(out, fstats)
-            graph = ctx.selfsearch_graph(d_seq, g.offsets, p, caps=caps)
-            for _ in range(args.warmup):
-                graph.launch(stream)
-                graph.wait()
-                flush.fill_(1)
-        barrier()
-        torch.cuda.synchronize()
-        g_ms = []
-        with torch.cuda.stream(stream):
-            for _ in range(args.steps):
-                flush.fill_(1)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                graph.launch(stream)
-                e1.record(stream)
-                e1.synchronize()
-                graph.wait()
-                g_ms.append(e0.elapsed_time(e1))
-        graph_ms = aggregate_max_ms(sum(g_ms) / len(g_ms), ws, dev)
+            graph = ctx.selfsearch_graph(d_seq, W.offsets, p, caps=caps)
+
+        def replay():
+            graph.launch(stream)
+
+        g_ms = timed_steps(stream, flush, args.steps, args.warmup, replay)
+        graph.wait()
+        graph_ms = aggregate_max_ms(g_ms, ws, dev)
         graph_info = {"value": ws * N / (graph_ms / 1000) / 1e6, "unit": "Mbp/s",
                       "ms_per_step": graph_ms, "kernel_nodes": graph.nodes,
-                      "capacities": graph.caps,
-                      "same_candidates": bool(graph.need["cands"] == int(out["ncands"]))}
+                      "same_candidates": bool(graph.need["cands"] == int(ncands))}
         graph.close()
     except (binding.SedefError, RuntimeError) as e:
         graph_info = {"error": str(e)}
 
     # ---- end to end through the host-buffer entry point
-    host_seq = torch.from_numpy(g.seq).pin_memory().numpy()
-    e2e_times = []
-    ncand = 0
+    host_seq = torch.from_numpy(W.seq).pin_memory().numpy()
+    e2e_times, nc_host = [], 0
     for it in range(0 if args.no_e2e else args.warmup + args.steps):
         barrier()
-        t0 = time.perf_counter()
-        cands = ctx.sedef_selfsearch_host(host_seq, g.offsets, p)
-        dt = time.perf_counter() - t0
-        ncand = len(cands)
+        t = time.perf_counter()
+        hc = ctx.sedef_selfsearch_host(host_seq, W.offsets, p)
+        dt = time.perf_counter() - t
+        nc_host = len(hc)
         if it >= args.warmup:
             e2e_times.append(dt)
     e2e_ms = 1000 * sum(e2e_times) / len(e2e_times) if e2e_times else float("nan")
     e2e_ms = aggregate_max_ms(e2e_ms, ws, dev)
-    e2e_value = ws * N / (e2e_ms / 1000) / 1e6
 
     if rank != 0:
+        ctx.close()
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
 
-    # ---- roofline of the dominant kernel
-    runs = binding.struct_view(out["runs"], binding.RUN_DTYPE)
-    rec_rows = binding.records_to_rows(binding.to_numpy_records(out["rec"]))
-    algo = algorithmic_bytes(g.seq, g.offsets, rec_rows, None, runs, p.k, p.n, p.query_step)
-    dom = max(trace.items(), key=lambda kv: kv[1][1])
-    dname, (dcount, dms) = dom
+    # ---- per-family time, algorithmic bytes and the roofline
     peak, peak_kind = peaks()
-    per_launch_ms = dms / dcount
-    roof = {"kernel": dname, "bound": "hbm", "peak": peak, "unit": "GB/s",
-            "peak_source": peak_kind, "traffic": measured_traffic(dname)}
-    if dname in algo:
-        launches_per_step = dcount / args.steps
-        bytes_per_launch = algo[dname] / max(1.0, launches_per_step) if dname.startswith("k_rs") \
-            else algo[dname]
-        achieved = bytes_per_launch / (per_launch_ms / 1000) / 1e9
-        roof.update({"achieved": achieved, "frac": achieved / peak,
-                     "algorithmic_bytes_per_launch": bytes_per_launch,
-                     "launch_ms": per_launch_ms})
+    fam_ms = {}
+    for key, (cnt, t) in trace.items():
+        fam_ms[family_of(key)] = fam_ms.get(family_of(key), 0.0) + t / nsteps
+    filt = filter_algorithmic_bytes(out["rec"], W.offsets, p.k, p.n, p.query_step, W.self_mode,
+                                    out["nruns"])
+    algo = algorithmic_bytes(N, int(out["rec"].numel()), p.k, filt)
+    families = {}
+    for f, t in sorted(fam_ms.items(), key=lambda kv: -kv[1]):
+        e = {"ms_per_step": t, "share": t / ms}
+        if f in algo and t > 0:
+            gbs = algo[f] / (t / 1000) / 1e9
+            e.update({"algorithmic_bytes": algo[f], "gbs": gbs, "frac_of_hbm": gbs / peak})
+        families[f] = e
+    dom = max(fam_ms.items(), key=lambda kv: kv[1])[0]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = float(clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0)
+    issue_peak = sms * 4 * mhz / 1000.0  # G warp instructions per second
+    if dom in algo:
+        a = algo[dom] / (fam_ms[dom] / 1000) / 1e9
+        roof = {"kernel": f"{dom} family", "bound": "hbm", "achieved": a, "peak": peak,
+                "unit": "GB/s", "frac": a / peak, "peak_source": peak_kind,
+                "algorithmic_bytes_per_step": algo[dom], "ms_per_step": fam_ms[dom],
+                "traffic": None}
     else:
-        roof.update({"achieved": None, "frac": None, "launch_ms": per_launch_ms})
-    # the bound that holds for a latency/issue-bound kernel: warp instructions
-    # issued (ncu count of the committed capture) per live launch time against
-    # one instruction per scheduler per cycle (4 per SM) at the top SM clock
-    try:
-        inst = measured_traffic(dname, "warp_instructions_per_launch")
-        if inst:
-            sms = torch.cuda.get_device_properties(dev).multi_processor_count
-            ghz = float(clk.get("sm_max_mhz") or 2070.0) / 1000.0
-            ipeak = sms * 4 * ghz
-            iach = inst / (per_launch_ms / 1000) / 1e9
-            roof["issue"] = {"achieved": iach, "peak": ipeak, "unit": "G warp-instructions/s",
-                             "frac": iach / ipeak, "instructions_per_launch": inst,
-                             "peak_from": f"{sms} SMs x 4 schedulers x {ghz:.3f} GHz"}
-    except Exception as e:  # a missing counter must not cost the line
-        roof["issue"] = {"error": str(e)}
-    kernels = {k: {"launches_per_step": c / args.steps, "ms_per_step": t / args.steps}
+        # plain integer work bound by instruction issue: warp instructions per
+        # unit (one ncu capture on this workload and filter shape) x units of
+        # this pass, against 4 schedulers x SMs x the sampled SM clock
+        units = {"refine": int(out["nruns"]), "runsort": int(out["nruns"]),
+                 "chain": int(out["nruns"]), "merge": int(out["nchains"])}.get(dom, 0)
+        kname = {"refine": "k_refine_batch"}.get(dom, dom)
+        e = counters_entry(kname, W.name, variant)
+        roof = {"kernel": f"{dom} family", "bound": "alu", "peak": issue_peak,
+                "unit": "G warp-instructions/s", "peak_from": f"{sms} SMs x 4 schedulers x "
+                f"{mhz:.0f} MHz (median sampled)", "ms_per_step": fam_ms[dom],
+                "achieved": None, "frac": None, "traffic": None}
+        if e and units:
+            inst = e["warp_instructions_per_unit"] * units
+            a = inst / (fam_ms[dom] / 1000) / 1e9
+            roof.update({"achieved": a, "frac": a / issue_peak,
+                         "instructions_per_step": inst,
+                         "traffic": int(e["dram_bytes_per_unit"] * units)
+                         if e.get("dram_bytes_per_unit") else None,
+                         "counters_from": e.get("profile")})
+    kernels = {k: {"launches_per_step": c / nsteps, "ms_per_step": t / nsteps}
                for k, (c, t) in sorted(trace.items(), key=lambda kv: -kv[1][1])}
-    for k, v in kernels.items():
-        if k in algo and v["launches_per_step"]:
-            lb = algo[k] if not k.startswith("k_rs") else algo[k]
-            v["gbs"] = (lb * v["launches_per_step"] if k.startswith("k_rs") else lb) / \
-                (v["ms_per_step"] / 1000) / 1e9 if v["ms_per_step"] else None
     if args.trace:
-        print(json.dumps(kernels, indent=1), file=sys.stderr)
+        print(json.dumps({"families": families, "kernels": kernels}, indent=1), file=sys.stderr)
 
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        cpu = cpu_baseline_line(g.seq)
+        cpu = cpu_baseline_line(W)
 
     line = {
         "metric": METRIC, "value": value, "unit": "Mbp/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "genome_bases": N, "k": p.k, "w": p.w, "n": p.n,
-                   "query_step": p.query_step, "parallelism": f"replicas x{ws}",
+        "config": {"workload": WORKLOADS[W.name], "genome_bases": N,
+                   "sequences": len(W.offsets) - 1, "self_mode": W.self_mode, "k": p.k,
+                   "w": p.w, "n": p.n, "query_step": p.query_step,
+                   "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 and a 256 MB L2 flush between steps",
+                   "step": "one sedef_selfsearch call (pack ... merge) on the device-resident input",
                    "runs": int(out["nruns"]), "chains": int(out["nchains"]),
-                   "candidates": int(out["ncands"]), "filter": fstats,
-                   "filter_shape": variant},
-        "e2e": {"value": e2e_value, "unit": "Mbp/s", "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": int(N + 8 * len(g.offsets)),
-                "d2h_bytes_per_step": int(ncand * 40)},
+                   "candidates": int(ncands), "filter": fstats, "filter_accounting": filt,
+                   "filter_shape": variant, "generation_s": gen_s},
+        "plain": plain,
+        "e2e": {"value": ws * N / (e2e_ms / 1000) / 1e6, "unit": "Mbp/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(N + 8 * len(W.offsets)),
+                "d2h_bytes_per_step": int(nc_host * 40),
+                "call": "sedef_selfsearch_host (pinned host input, candidates copied back)"},
         "roofline": roof,
+        "families": families,
         "cpu_baseline": cpu,
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -635,6 +638,31 @@ def main():
     ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batch",
+                    choices=["batch", "chromosome", "plain", "human", "serve"])
+    ap.add_argument("--serve-genome", default="human", choices=["human", "chromosome"],
+                    help="serving: the genome whose index stays resident")
+    ap.add_argument("--rates", default="50,200,1000", help="serving: request rates per second")
+    ap.add_argument("--requests", type=int, default=200, help="serving: requests per rate")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--no-graph", action="store_true", help="skip the captured-graph measurement")
+    ap.add_argument("--trace", action="store_true", help="print the per-kernel table to stderr")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    elif args.workload == "serve":
+        serve_arm(args)
+    else:
+        run_workload(args)
 
 
 if __name__ == "__main__":

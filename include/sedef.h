@@ -144,6 +144,16 @@ typedef struct sedef_chain_t {
   uint32_t reserved;
 } sedef_chain_t;
 
+/*
+ * Potential SD region (f1, Section 3.2): a kept seed (i, j_star, o) grown
+ * into query [qa, qb) and target [ta, tb), global coordinates; est / den is
+ * the winnowed MinHash estimate of the grown regions (den = s = |W_Q|).
+ */
+typedef struct sedef_region_t {
+  uint32_t i, j_star, qa, qb, ta, tb;
+  uint32_t est, den, o, reserved;
+} sedef_region_t;
+
 /* SD candidate: one connected group of chains, per-sequence coordinates. */
 typedef struct sedef_cand_t {
   uint32_t qseq, q0, q1, tseq, t0, t1;
@@ -365,10 +375,50 @@ int sedef_qgram(sedef_ctx* ctx, const uint32_t* d_packed, const uint32_t* d_nbit
                 double p_gap, uint32_t* d_shared, uint8_t* d_pass, int64_t* h_npass);
 
 /*
+ * f1 (Section 3.2, SD extension): every kept run's seed (i, j_star, o) is
+ * grown into a potential SD region.  The query region starts as [i, i+n)
+ * and the target region as [j_star, j_star+n); both grow by one base per
+ * step -- right ends first, then left ends; for o = 1 the target grows at
+ * the opposite end -- while the winnowed MinHash estimate of the two
+ * regions (Section 2.2: s = |W_Q|, U = the s smallest hashes of W_Q u W_T,
+ * est = hashes of U in both with relative strand o) stays >= m(s).  Growth
+ * also stops at a sequence end, at max_len bases (Section 3.2 limits
+ * potential SDs to 1 Mbp), and, in a self search with both regions on one
+ * sequence, where the regions would overlap more than before.  W_Q and W_T
+ * come from the extension sketches d_qext / d_text: sedef_sketch of the
+ * same sequences with min_unmasked = 0 (the extension uses every k-mer,
+ * masked ones included), sorted by position.  In a self search (self_mode 1
+ * or 2) d_qext and d_text are the same array and a target minimizer inside
+ * the query region's k-mer span is not shared.  Writes one region per kept
+ * run, in run order, to d_regions[0..cap) and their number to *h_nregions
+ * (SEDEF_ERR_CAPACITY when cap is too small).  Needs k <= 12 (a 4-bit state
+ * per hash, 2^(2k) / 2 bytes of scratch per resident warp).  Synchronizes.
+ */
+int sedef_extend(sedef_ctx* ctx, const sedef_run_t* d_runs, int64_t nruns, const uint64_t* d_qext,
+                 int64_t nq, const int64_t* h_qoff, int32_t nqseq, const uint64_t* d_text,
+                 int64_t nt, const int64_t* h_toff, int32_t ntseq, const sedef_params* p,
+                 int64_t max_len, sedef_region_t* d_regions, int64_t cap, int64_t* h_nregions);
+
+/*
+ * Whole self-search of a device-resident input (Sections 2.2-3.3 in one
+ * call): pack, sketch, index, filter (with refine), chain and merge of
+ * d_seq (total bytes h_seq_off[nseq]) on the context's stream, with
+ * self_mode 1 (one genome) or 2 (a batch of independent genomes, one per
+ * sequence).  Writes the candidates to the caller's device buffer
+ * d_cands[0..cap) and their number to *h_ncands (SEDEF_ERR_CAPACITY when
+ * cap is too small).  Scratch comes from the context and is reused by the
+ * next call; the run buffer starts at the previous call's run count, so a
+ * repeated search runs the filter once.  Synchronizes.
+ */
+int sedef_selfsearch(sedef_ctx* ctx, const uint8_t* d_seq, const int64_t* h_seq_off,
+                     int32_t nseq, const sedef_params* p, sedef_cand_t* d_cands, int64_t cap,
+                     int64_t* h_ncands);
+
+/*
  * Whole self-search through host buffers: copies h_seq (total bytes
- * h_seq_off[nseq]) to the device, runs pack, sketch, index, filter, chain
- * and merge on the context's stream, and copies the candidates back to
- * h_cands.  Device memory comes from the context.  Synchronizes.
+ * h_seq_off[nseq]) to the device, runs sedef_selfsearch's stages on the
+ * context's stream, and copies the candidates back to h_cands.  Device
+ * memory comes from the context.  Synchronizes.
  */
 int sedef_selfsearch_host(sedef_ctx* ctx, const uint8_t* h_seq, const int64_t* h_seq_off,
                           int32_t nseq, const sedef_params* p, sedef_cand_t* h_cands, int64_t cap,
@@ -416,6 +466,44 @@ int sedef_graph_launch(sedef_graph* g, void* stream);
 int sedef_graph_wait(sedef_graph* g, int64_t* h_need);
 int64_t sedef_graph_nodes(sedef_graph* g);
 int sedef_graph_destroy(sedef_graph* g);
+
+/*
+ * Serving with continuous batching (no counterpart in the paper: this is the
+ * serving form of the seed stage, non-self search against a resident
+ * target index).  sedef_server_create keeps the target index (d_trec,
+ * d_tsorted, d_toff from sedef_sketch / sedef_index, owned by the caller;
+ * they must stay allocated) and allocates `slots` request slots of up to
+ * slot_bases query bases each.  A persistent filter kernel (one CTA per SM)
+ * drains a work queue of query windows in mapped host memory; the host adds
+ * a request's windows when sedef_server_submit admits it into a free slot,
+ * so requests that arrive while others are on the GPU join the running
+ * kernel.  sedef_server_submit copies the query (h_query, len bases) to the
+ * device, sketches it, builds its window table and publishes its windows;
+ * it returns SEDEF_ERR_CAPACITY when no slot is free.  sedef_server_poll
+ * waits up to wait_s seconds for a request whose windows are all filtered
+ * (*slot_out = its slot, or -1); sedef_server_finish then runs the rest of
+ * the path for that slot (windows the kernel's shared-memory tier could not
+ * hold, run ordering and refine, chaining, merging) and copies its
+ * candidates (query coordinates within the request, target coordinates per
+ * target sequence) to h_cands; the slot is free again afterwards.  A CTA of
+ * the persistent kernel that finds no work for idle_timeout_s seconds
+ * leaves; when all have left that way sedef_server_status returns
+ * SEDEF_ERR_TIMEOUT (running = 0, timed_out = 1), and the next submit or
+ * poll launches the kernel again.  submit may run on one host thread while
+ * poll and finish run on another; each of the three is not reentrant.
+ * sedef_server_destroy stops the kernel and frees the server.
+ */
+typedef struct sedef_server sedef_server;
+int sedef_server_create(sedef_ctx* ctx, const uint64_t* d_trec, const uint64_t* d_tsorted,
+                        const uint32_t* d_toff, int64_t nt, const int64_t* h_toff, int32_t ntseq,
+                        const sedef_params* p, int32_t slots, int64_t slot_bases,
+                        double idle_timeout_s, sedef_server** out);
+int sedef_server_submit(sedef_server* s, const uint8_t* h_query, int64_t len, int32_t* slot_out);
+int sedef_server_poll(sedef_server* s, double wait_s, int32_t* slot_out);
+int sedef_server_finish(sedef_server* s, int32_t slot, sedef_cand_t* h_cands, int64_t cap,
+                        int64_t* h_ncands);
+int sedef_server_status(sedef_server* s, int32_t* running, int32_t* timed_out);
+int sedef_server_destroy(sedef_server* s);
 
 #ifdef __cplusplus
 }

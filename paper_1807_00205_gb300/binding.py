@@ -22,10 +22,14 @@ RUN_DTYPE = np.dtype([("i", "<u4"), ("j_a", "<u4"), ("j_b", "<u4"), ("j_at_max",
 CHAIN_DTYPE = np.dtype([("i", "<u4"), ("qseq", "<u4"), ("q0", "<u4"), ("q1", "<u4"),
                         ("tseq", "<u4"), ("t0", "<u4"), ("t1", "<u4"), ("score", "<u2"),
                         ("s", "<u2"), ("o", "<u4"), ("reserved", "<u4")])
+REGION_DTYPE = np.dtype([("i", "<u4"), ("j_star", "<u4"), ("qa", "<u4"), ("qb", "<u4"),
+                         ("ta", "<u4"), ("tb", "<u4"), ("est", "<u4"), ("den", "<u4"),
+                         ("o", "<u4"), ("reserved", "<u4")])
 CAND_DTYPE = np.dtype([("qseq", "<u4"), ("q0", "<u4"), ("q1", "<u4"), ("tseq", "<u4"),
                        ("t0", "<u4"), ("t1", "<u4"), ("o", "<u4"), ("score", "<u4"),
                        ("nchains", "<u4"), ("reserved", "<u4")])
 assert RUN_DTYPE.itemsize == 32 and CHAIN_DTYPE.itemsize == 40 and CAND_DTYPE.itemsize == 40
+assert REGION_DTYPE.itemsize == 40
 
 
 class Params(ctypes.Structure):
@@ -41,10 +45,13 @@ EXPORTS = ["sedef_default_params", "sedef_last_error", "sedef_create", "sedef_de
            "sedef_set_stream", "sedef_trace_enable", "sedef_trace_report", "sedef_launch_count", "sedef_filter_stats",
            "sedef_threshold_table", "sedef_pack", "sedef_sketch", "sedef_sketch_noalloc",
            "sedef_index", "sedef_filter", "sedef_filter_autotune", "sedef_filter_variant",
-           "sedef_chain", "sedef_merge", "sedef_selfsearch_host", "sedef_index_blob_size",
+           "sedef_chain", "sedef_extend", "sedef_merge", "sedef_selfsearch",
+           "sedef_selfsearch_host",
+           "sedef_index_blob_size",
            "sedef_index_save", "sedef_index_blob_info", "sedef_index_load", "sedef_graph_create",
            "sedef_graph_launch", "sedef_graph_wait", "sedef_graph_nodes", "sedef_graph_destroy",
-           "sedef_qgram"]
+           "sedef_qgram", "sedef_server_create", "sedef_server_submit", "sedef_server_poll",
+           "sedef_server_finish", "sedef_server_status", "sedef_server_destroy"]
 
 CAP_NAMES = ["records", "slow_hits", "runs", "anchors", "chains", "cands"]
 
@@ -105,7 +112,17 @@ def load(build_if_missing: bool = True):
     lib.sedef_chain.argtypes = [vp, vp, i64, vp, i64, vp, i32, vp, vp, i64, vp, i32, P, vp, i64,
                                 ctypes.POINTER(i64)]
     lib.sedef_merge.argtypes = [vp, vp, i64, vp, i32, vp, i32, P, vp, i64, ctypes.POINTER(i64)]
+    lib.sedef_extend.argtypes = [vp, vp, i64, vp, i64, vp, i32, vp, i64, vp, i32, P, i64, vp, i64,
+                                 ctypes.POINTER(i64)]
+    lib.sedef_selfsearch.argtypes = [vp, vp, vp, i32, P, vp, i64, ctypes.POINTER(i64)]
     lib.sedef_selfsearch_host.argtypes = [vp, vp, vp, i32, P, vp, i64, ctypes.POINTER(i64)]
+    lib.sedef_server_create.argtypes = [vp, vp, vp, vp, i64, vp, i32, P, i32, i64,
+                                        ctypes.c_double, ctypes.POINTER(vp)]
+    lib.sedef_server_submit.argtypes = [vp, vp, i64, ctypes.POINTER(i32)]
+    lib.sedef_server_poll.argtypes = [vp, ctypes.c_double, ctypes.POINTER(i32)]
+    lib.sedef_server_finish.argtypes = [vp, i32, vp, i64, ctypes.POINTER(i64)]
+    lib.sedef_server_status.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.sedef_server_destroy.argtypes = [vp]
     lib.sedef_trace_enable.argtypes = [vp, ctypes.c_int]
     lib.sedef_trace_report.argtypes = [vp, ctypes.c_char_p, i64, ctypes.c_int]
     lib.sedef_launch_count.restype = ctypes.c_uint64
@@ -180,6 +197,8 @@ class Context:
         _check(self.lib.sedef_create(device, ctypes.c_void_p(self.stream.cuda_stream),
                                      ctypes.byref(h)))
         self.handle = h
+        self._run_cap = 0   # largest run count seen (first run-buffer size next time)
+        self._cand_cap = 0
 
     def close(self):
         if self.handle:
@@ -264,7 +283,8 @@ class Context:
 
     def sedef_filter(self, qrec, qoff, trec, tsorted, toff_tab, toff, p: Params, cap=None):
         qo, to = _offsets(qoff), _offsets(toff)
-        cap = cap if cap is not None else max(4096, int(qo[-1]) // 16)
+        if cap is None:
+            cap = max(4096, int(qo[-1]) // 16, self._run_cap + self._run_cap // 8)
         count = ctypes.c_int64()
         for _ in range(2):
             runs = self._empty(cap * RUN_DTYPE.itemsize, self.torch.uint8)
@@ -276,6 +296,7 @@ class Context:
                 cap = count.value
                 continue
             _check(st)
+            self._run_cap = max(self._run_cap, count.value)
             return runs[:count.value * RUN_DTYPE.itemsize], count.value
         raise SedefError(SEDEF_ERR_CAPACITY, "filter capacity")
 
@@ -327,6 +348,21 @@ class Context:
                                     _ptr(chains), cap, ctypes.byref(count)))
         return chains[:count.value * CHAIN_DTYPE.itemsize], count.value
 
+    def sedef_extend(self, runs, nruns, qext, qoff, text, toff, p: Params,
+                     max_len: int = 1_000_000):
+        """f1: potential SD regions of the kept seeds (device uint8 tensor of
+        sedef_region_t, count).  qext / text: extension sketches
+        (sedef_sketch with min_unmasked = 0)."""
+        qo, to = _offsets(qoff), _offsets(toff)
+        cap = max(int(nruns), 1)
+        count = ctypes.c_int64()
+        out = self._empty(cap * REGION_DTYPE.itemsize, self.torch.uint8)
+        _check(self.lib.sedef_extend(self.handle, _ptr(runs), int(nruns), _ptr(qext), qext.numel(),
+                                     qo.ctypes.data, len(qo) - 1, _ptr(text), text.numel(),
+                                     to.ctypes.data, len(to) - 1, ctypes.byref(p), int(max_len),
+                                     _ptr(out), cap, ctypes.byref(count)))
+        return out[:count.value * REGION_DTYPE.itemsize], count.value
+
     def sedef_merge(self, chains, nchains, qoff, toff, p: Params):
         qo, to = _offsets(qoff), _offsets(toff)
         cap = max(int(nchains), 1)
@@ -349,10 +385,30 @@ class Context:
                                     _ptr(ok), ctypes.byref(npass)))
         return shared[:nruns], ok[:nruns], npass.value
 
+    def sedef_selfsearch(self, d_seq, offsets, p: Params, cap=None):
+        """The whole self-search of a device-resident sequence in one call;
+        returns (candidates as a device uint8 tensor of sedef_cand_t, count)."""
+        off = _offsets(offsets)
+        if cap is None:
+            cap = max(4096, self._cand_cap + self._cand_cap // 8)
+        count = ctypes.c_int64()
+        for _ in range(2):
+            out = self._empty(cap * CAND_DTYPE.itemsize, self.torch.uint8)
+            st = self.lib.sedef_selfsearch(self.handle, _ptr(d_seq), off.ctypes.data, len(off) - 1,
+                                           ctypes.byref(p), _ptr(out), cap, ctypes.byref(count))
+            if st == SEDEF_ERR_CAPACITY:
+                cap = count.value
+                continue
+            _check(st)
+            self._cand_cap = max(self._cand_cap, count.value)
+            return out[:count.value * CAND_DTYPE.itemsize], count.value
+        raise SedefError(SEDEF_ERR_CAPACITY, "selfsearch capacity")
+
     def sedef_selfsearch_host(self, seq: np.ndarray, offsets, p: Params, cap=None):
         seq = np.ascontiguousarray(seq, dtype=np.uint8)
         off = _offsets(offsets)
-        cap = cap if cap is not None else max(4096, len(seq) // 256)
+        if cap is None:
+            cap = max(4096, len(seq) // 256, self._cand_cap + self._cand_cap // 8)
         count = ctypes.c_int64()
         for _ in range(2):
             out = np.zeros(cap, dtype=CAND_DTYPE)
@@ -363,6 +419,7 @@ class Context:
                 cap = count.value
                 continue
             _check(st)
+            self._cand_cap = max(self._cand_cap, count.value)
             return out[:count.value]
         raise SedefError(SEDEF_ERR_CAPACITY, "selfsearch capacity")
 

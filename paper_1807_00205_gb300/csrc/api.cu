@@ -20,6 +20,7 @@ struct sedef_ctx {
   // tracing: one (name, start, stop) per traced launch since the last report
   bool trace = false;
   struct Mark {
+    const char* stage;
     const char* name;
     cudaEvent_t start, stop;
   };
@@ -27,6 +28,10 @@ struct sedef_ctx {
   std::vector<cudaEvent_t> spare;  // recycled events
   int64_t filter_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int filter_variant = 0;  // first-tier filter shape (sedef_filter_autotune)
+  // run count of the last whole self-search (its run buffer's first size
+  // next time, so that a repeated search does not rerun the filter)
+  int64_t last_runs = 0;
+  const char* stage = "";  // label of traced launches (sedef::StageScope)
 };
 
 namespace sedef {
@@ -110,7 +115,7 @@ TraceScope::TraceScope(sedef_ctx* c, const char* name) : ctx(c), slot(-1) {
   cudaEvent_t a = take_event(c), b = take_event(c);
   if (!a || !b) return;
   cudaEventRecord(a, c->stream);
-  c->marks.push_back({name, a, b});
+  c->marks.push_back({c->stage, name, a, b});
   slot = (int)c->marks.size() - 1;
 }
 
@@ -119,6 +124,14 @@ TraceScope::~TraceScope() {
 }
 
 cudaStream_t ctx_stream(sedef_ctx* ctx) { return ctx->stream; }
+void ctx_pool_reset(sedef_ctx* ctx) { ctx->pool.reset(); }
+
+const char* ctx_set_stage(sedef_ctx* ctx, const char* stage) {
+  if (!ctx) return "";
+  const char* prev = ctx->stage;
+  ctx->stage = stage ? stage : "";
+  return prev;
+}
 
 int ctx_filter_variant(sedef_ctx* ctx) { return ctx->filter_variant; }
 void ctx_set_filter_variant(sedef_ctx* ctx, int v) { ctx->filter_variant = v; }
@@ -337,10 +350,11 @@ int sedef_trace_report(sedef_ctx* ctx, char* buf, int64_t cap, int reset) {
   for (auto& m : ctx->marks) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, m.start, m.stop);
-    auto it = agg.find(m.name);
+    const std::string key = m.stage[0] ? std::string(m.stage) + ":" + m.name : std::string(m.name);
+    auto it = agg.find(key);
     if (it == agg.end()) {
-      order.push_back(m.name);
-      agg[m.name] = {1, ms};
+      order.push_back(key);
+      agg[key] = {1, ms};
     } else {
       it->second.first += 1;
       it->second.second += ms;
@@ -391,6 +405,7 @@ int sedef_pack(sedef_ctx* ctx, const uint8_t* d_seq, int64_t n, uint32_t* d_pack
   if (!d_seq || !d_packed || !d_mask || !d_nbits) return fail(SEDEF_ERR_INVALID, "NULL buffer");
   if (n >= (int64_t(1) << 32)) return fail(SEDEF_ERR_UNSUPPORTED, "n must be < 2^32");
   SEDEF_CUDA(cudaSetDevice(ctx->device));
+  StageScope stage(ctx, "pack");
   return launch_pack(ctx, d_seq, n, d_packed, d_mask, d_nbits);
 }
 
@@ -407,6 +422,7 @@ int sedef_sketch(sedef_ctx* ctx, const uint32_t* d_packed, const uint32_t* d_mas
   if (rec_cap > 0 && !d_rec) return fail(SEDEF_ERR_INVALID, "NULL output buffer");
   SEDEF_CUDA(cudaSetDevice(ctx->device));
   ctx->pool.reset();
+  StageScope stage(ctx, "sketch");
   return run_sketch(ctx, d_packed, d_mask, d_nbits, h_seq_off, nseq, D, d_rec, rec_cap, h_nrec);
 }
 
@@ -420,6 +436,7 @@ int sedef_index(sedef_ctx* ctx, const uint64_t* d_rec, int64_t nrec, const sedef
   if (nrec > 0 && d_rec == d_sorted) return fail(SEDEF_ERR_INVALID, "d_rec and d_sorted overlap");
   SEDEF_CUDA(cudaSetDevice(ctx->device));
   ctx->pool.reset();
+  StageScope stage(ctx, "index");
   if (nrec > 0)
     SEDEF_TRY(radix_sort_u64(ctx, d_rec, nullptr, d_sorted, nullptr, nrec, 33, 33 + 2 * D.k));
   return build_offsets(ctx, d_sorted, nrec, D.k, d_off);
@@ -447,6 +464,7 @@ int sedef_filter(sedef_ctx* ctx, const uint64_t* d_qrec, int64_t nq, const int64
   std::vector<int32_t> mt(kMaxWindowRecs + 1);
   mtable(p, mt.data(), kMaxWindowRecs, nullptr);
   *h_nruns = 0;
+  StageScope stage(ctx, "filter");
   return run_filter(ctx, d_qrec, nq, h_qoff, nqseq, d_trec, d_tsorted, d_toff, nt, h_toff, ntseq,
                     D, mt.data(), d_runs, run_cap, h_nruns, 0);
 }
@@ -505,8 +523,36 @@ int sedef_chain(sedef_ctx* ctx, const sedef_run_t* d_runs, int64_t nruns, const 
   if (nruns == 0) return SEDEF_OK;
   if ((nq > 0 && !d_qrec) || (nt > 0 && !d_tsorted) || !d_toff)
     return fail(SEDEF_ERR_INVALID, "bad record arrays");
+  StageScope stage(ctx, "chain");
   return run_chain(ctx, d_runs, nruns, d_qrec, nq, h_qoff, nqseq, d_tsorted, nt, d_toff, h_toff,
                    ntseq, D, mt.data(), d_chains, cap, h_nchains);
+}
+
+int sedef_extend(sedef_ctx* ctx, const sedef_run_t* d_runs, int64_t nruns, const uint64_t* d_qext,
+                 int64_t nq, const int64_t* h_qoff, int32_t nqseq, const uint64_t* d_text,
+                 int64_t nt, const int64_t* h_toff, int32_t ntseq, const sedef_params* p,
+                 int64_t max_len, sedef_region_t* d_regions, int64_t cap, int64_t* h_nregions) {
+  if (!ctx || !h_nregions) return fail(SEDEF_ERR_INVALID, "NULL argument");
+  Derived D;
+  SEDEF_TRY(derive(p, &D));
+  SEDEF_TRY(check_offsets(h_qoff, nqseq, "query"));
+  SEDEF_TRY(check_offsets(h_toff, ntseq, "target"));
+  *h_nregions = 0;
+  if (D.k > 12) return fail(SEDEF_ERR_UNSUPPORTED, "sedef_extend: k must be at most 12");
+  if (max_len < D.n || max_len >= (int64_t(1) << 31))
+    return fail(SEDEF_ERR_INVALID, "sedef_extend: max_len must be in [n, 2^31)");
+  if (nruns < 0 || (nruns > 0 && !d_runs)) return fail(SEDEF_ERR_INVALID, "bad runs");
+  if (nq < 0 || nt < 0 || (nq > 0 && !d_qext) || (nt > 0 && !d_text))
+    return fail(SEDEF_ERR_INVALID, "bad record arrays");
+  if (D.self_mode && (nqseq != ntseq || d_qext != d_text || nq != nt))
+    return fail(SEDEF_ERR_INVALID, "self mode needs identical query and target");
+  if (cap > 0 && !d_regions) return fail(SEDEF_ERR_INVALID, "NULL output buffer");
+  if (nruns == 0) return SEDEF_OK;
+  SEDEF_CUDA(cudaSetDevice(ctx->device));
+  ctx->pool.reset();
+  StageScope stage(ctx, "extend");
+  return run_extend(ctx, d_runs, nruns, d_qext, nq, h_qoff, nqseq, d_text, nt, h_toff, ntseq, D,
+                    p, max_len, d_regions, cap, h_nregions);
 }
 
 int sedef_merge(sedef_ctx* ctx, const sedef_chain_t* d_chains, int64_t nchains,
@@ -523,26 +569,23 @@ int sedef_merge(sedef_ctx* ctx, const sedef_chain_t* d_chains, int64_t nchains,
   ctx->pool.reset();
   *h_ncands = 0;
   if (nchains == 0) return SEDEF_OK;
+  StageScope stage(ctx, "merge");
   return run_merge(ctx, d_chains, nchains, h_qoff, nqseq, h_toff, ntseq, D, d_cands, cap, h_ncands);
 }
 
-int sedef_selfsearch_host(sedef_ctx* ctx, const uint8_t* h_seq, const int64_t* h_seq_off,
-                          int32_t nseq, const sedef_params* p, sedef_cand_t* h_cands, int64_t cap,
-                          int64_t* h_ncands) {
-  if (!ctx || !h_ncands) return fail(SEDEF_ERR_INVALID, "NULL argument");
-  Derived D;
-  SEDEF_TRY(derive(p, &D));
-  SEDEF_TRY(check_offsets(h_seq_off, nseq, "sedef_selfsearch_host"));
-  if (!D.self_mode) return fail(SEDEF_ERR_INVALID, "self search needs self_mode = 1");
-  *h_ncands = 0;
-  if (nseq == 0 || h_seq_off[nseq] == 0) return SEDEF_OK;
-  if (!h_seq || (cap > 0 && !h_cands)) return fail(SEDEF_ERR_INVALID, "NULL buffer");
-  SEDEF_CUDA(cudaSetDevice(ctx->device));
+}  // extern "C"
+
+namespace {
+
+// The whole self-search on a device-resident sequence: pack, sketch, index,
+// filter (with refine), chain and merge on the context's stream.  Device
+// buffers come from the context's I/O pool (reused by the next call,
+// released by sedef_destroy); *cands points into it on return.
+int selfsearch_device(sedef_ctx* ctx, const uint8_t* seq, const int64_t* h_seq_off, int32_t nseq,
+                      const sedef_params* p, const sedef::Derived& D, sedef_cand_t** cands_out,
+                      int64_t* nc_out) {
+  using namespace sedef;
   const int64_t N = h_seq_off[nseq];
-  cudaStream_t st = ctx->stream;
-  // Buffers owned by this call (freed at the end); the stage calls use the
-  // context pool for their own scratch.
-  uint8_t* seq = nullptr;
   uint32_t *packed = nullptr, *mask = nullptr, *nbits = nullptr, *off = nullptr;
   uint64_t *rec = nullptr, *sorted = nullptr;
   sedef_run_t* runs = nullptr;
@@ -551,35 +594,15 @@ int sedef_selfsearch_host(sedef_ctx* ctx, const uint8_t* h_seq, const int64_t* h
   int status = SEDEF_OK;
   int64_t nrec = 0, nruns = 0, nch = 0, nc = 0;
   const size_t nwords16 = (size_t)((N + 15) / 16), nwords32 = (size_t)((N + 31) / 32);
-  // Device buffers come from the context's I/O pool: reused by the next
-  // call, released by sedef_destroy.
-  ctx->io.reset();
-  auto cleanup = [&]() { cudaStreamSynchronize(st); };
-#define STEP(x)                   \
-  do {                            \
-    status = (x);                 \
-    if (status != SEDEF_OK) {     \
-      cleanup();                  \
-      return status;              \
-    }                             \
+#define DALLOC(ptr, bytes)                                                 \
+  do {                                                                     \
+    ptr = (decltype(ptr))ctx->io.alloc((bytes) ? (bytes) : 256);           \
+    if (!ptr) return fail(SEDEF_ERR_OOM, "selfsearch: device allocation failed"); \
   } while (0)
-#define DALLOC(ptr, bytes)                                                   \
-  do {                                                                       \
-    ptr = (decltype(ptr))ctx->io.alloc((bytes) ? (bytes) : 256);             \
-    if (!ptr) {                                                              \
-      cleanup();                                                             \
-      return fail(SEDEF_ERR_OOM, "selfsearch: device allocation failed");    \
-    }                                                                        \
-  } while (0)
-  DALLOC(seq, (size_t)N);
   DALLOC(packed, nwords16 * 4);
   DALLOC(mask, nwords32 * 4);
   DALLOC(nbits, nwords32 * 4);
-  if (cudaMemcpyAsync(seq, h_seq, (size_t)N, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-    cleanup();
-    return fail(SEDEF_ERR_CUDA, "selfsearch: H2D copy failed");
-  }
-  STEP(sedef_pack(ctx, seq, N, packed, mask, nbits));
+  SEDEF_TRY(sedef_pack(ctx, seq, N, packed, mask, nbits));
   // sketch: start from the expected density and grow once if needed
   int64_t rcap = N / 4 + 1024;
   DALLOC(rec, (size_t)rcap * 8);
@@ -589,11 +612,13 @@ int sedef_selfsearch_host(sedef_ctx* ctx, const uint8_t* h_seq, const int64_t* h
     DALLOC(rec, (size_t)rcap * 8);
     status = sedef_sketch(ctx, packed, mask, nbits, h_seq_off, nseq, p, rec, rcap, &nrec);
   }
-  STEP(status);
+  SEDEF_TRY(status);
   DALLOC(sorted, (size_t)(nrec ? nrec : 1) * 8);
   DALLOC(off, ((size_t(1) << (2 * D.k)) + 1) * 4);
-  STEP(sedef_index(ctx, rec, nrec, p, sorted, off));
+  SEDEF_TRY(sedef_index(ctx, rec, nrec, p, sorted, off));
+  // runs: the larger of a density guess and the last search's count
   int64_t fcap = N / 32 + 4096;
+  if (ctx->last_runs + ctx->last_runs / 8 > fcap) fcap = ctx->last_runs + ctx->last_runs / 8;
   DALLOC(runs, (size_t)fcap * sizeof(sedef_run_t));
   status = sedef_filter(ctx, rec, nrec, h_seq_off, nseq, rec, sorted, off, nrec, h_seq_off, nseq, p,
                         runs, fcap, &nruns);
@@ -603,26 +628,96 @@ int sedef_selfsearch_host(sedef_ctx* ctx, const uint8_t* h_seq, const int64_t* h
     status = sedef_filter(ctx, rec, nrec, h_seq_off, nseq, rec, sorted, off, nrec, h_seq_off, nseq,
                           p, runs, fcap, &nruns);
   }
-  STEP(status);
+  SEDEF_TRY(status);
+  ctx->last_runs = nruns;
   DALLOC(chains, (size_t)(nruns ? nruns : 1) * sizeof(sedef_chain_t));
-  STEP(sedef_chain(ctx, runs, nruns, rec, nrec, h_seq_off, nseq, sorted, off, nrec, h_seq_off, nseq,
-                   p, chains, nruns, &nch));
+  SEDEF_TRY(sedef_chain(ctx, runs, nruns, rec, nrec, h_seq_off, nseq, sorted, off, nrec, h_seq_off,
+                        nseq, p, chains, nruns, &nch));
   DALLOC(cands, (size_t)(nch ? nch : 1) * sizeof(sedef_cand_t));
-  STEP(sedef_merge(ctx, chains, nch, h_seq_off, nseq, h_seq_off, nseq, p, cands, nch, &nc));
+  SEDEF_TRY(sedef_merge(ctx, chains, nch, h_seq_off, nseq, h_seq_off, nseq, p, cands, nch, &nc));
+#undef DALLOC
+  *cands_out = cands;
+  *nc_out = nc;
+  return SEDEF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sedef_selfsearch(sedef_ctx* ctx, const uint8_t* d_seq, const int64_t* h_seq_off, int32_t nseq,
+                     const sedef_params* p, sedef_cand_t* d_cands, int64_t cap,
+                     int64_t* h_ncands) {
+  if (!ctx || !h_ncands) return fail(SEDEF_ERR_INVALID, "NULL argument");
+  Derived D;
+  SEDEF_TRY(derive(p, &D));
+  SEDEF_TRY(check_offsets(h_seq_off, nseq, "sedef_selfsearch"));
+  if (!D.self_mode) return fail(SEDEF_ERR_INVALID, "self search needs self_mode 1 or 2");
+  *h_ncands = 0;
+  if (nseq == 0 || h_seq_off[nseq] == 0) return SEDEF_OK;
+  if (!d_seq || (cap > 0 && !d_cands)) return fail(SEDEF_ERR_INVALID, "NULL buffer");
+  SEDEF_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  ctx->io.reset();
+  sedef_cand_t* cands = nullptr;
+  int64_t nc = 0;
+  const int status = selfsearch_device(ctx, d_seq, h_seq_off, nseq, p, D, &cands, &nc);
+  if (status != SEDEF_OK) {
+    cudaStreamSynchronize(st);
+    return status;
+  }
   *h_ncands = nc;
   if (nc > cap) {
-    cleanup();
+    cudaStreamSynchronize(st);
+    return fail(SEDEF_ERR_CAPACITY, "selfsearch: candidate buffer too small");
+  }
+  if (nc > 0)
+    SEDEF_CUDA(cudaMemcpyAsync(d_cands, cands, (size_t)nc * sizeof(sedef_cand_t),
+                               cudaMemcpyDeviceToDevice, st));
+  SEDEF_CUDA(cudaStreamSynchronize(st));
+  return SEDEF_OK;
+}
+
+int sedef_selfsearch_host(sedef_ctx* ctx, const uint8_t* h_seq, const int64_t* h_seq_off,
+                          int32_t nseq, const sedef_params* p, sedef_cand_t* h_cands, int64_t cap,
+                          int64_t* h_ncands) {
+  if (!ctx || !h_ncands) return fail(SEDEF_ERR_INVALID, "NULL argument");
+  Derived D;
+  SEDEF_TRY(derive(p, &D));
+  SEDEF_TRY(check_offsets(h_seq_off, nseq, "sedef_selfsearch_host"));
+  if (!D.self_mode) return fail(SEDEF_ERR_INVALID, "self search needs self_mode 1 or 2");
+  *h_ncands = 0;
+  if (nseq == 0 || h_seq_off[nseq] == 0) return SEDEF_OK;
+  if (!h_seq || (cap > 0 && !h_cands)) return fail(SEDEF_ERR_INVALID, "NULL buffer");
+  SEDEF_CUDA(cudaSetDevice(ctx->device));
+  const int64_t N = h_seq_off[nseq];
+  cudaStream_t st = ctx->stream;
+  ctx->io.reset();
+  uint8_t* seq = (uint8_t*)ctx->io.alloc((size_t)N);
+  if (!seq) return fail(SEDEF_ERR_OOM, "selfsearch: device allocation failed");
+  if (cudaMemcpyAsync(seq, h_seq, (size_t)N, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    cudaStreamSynchronize(st);
+    return fail(SEDEF_ERR_CUDA, "selfsearch: H2D copy failed");
+  }
+  sedef_cand_t* cands = nullptr;
+  int64_t nc = 0;
+  const int status = selfsearch_device(ctx, seq, h_seq_off, nseq, p, D, &cands, &nc);
+  if (status != SEDEF_OK) {
+    cudaStreamSynchronize(st);
+    return status;
+  }
+  *h_ncands = nc;
+  if (nc > cap) {
+    cudaStreamSynchronize(st);
     return fail(SEDEF_ERR_CAPACITY, "selfsearch: candidate buffer too small");
   }
   if (nc > 0 &&
       cudaMemcpyAsync(h_cands, cands, (size_t)nc * sizeof(sedef_cand_t), cudaMemcpyDeviceToHost,
                       st) != cudaSuccess) {
-    cleanup();
+    cudaStreamSynchronize(st);
     return fail(SEDEF_ERR_CUDA, "selfsearch: D2H copy failed");
   }
-  cleanup();
-#undef STEP
-#undef DALLOC
+  SEDEF_CUDA(cudaStreamSynchronize(st));
   return SEDEF_OK;
 }
 

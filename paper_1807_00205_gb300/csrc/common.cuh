@@ -220,6 +220,10 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
                const int64_t* h_toff, int ntseq, const Derived& D, const int32_t* h_mtab,
                sedef_run_t* runs, int64_t cap, int64_t* nruns, int tune, Planned* pl = nullptr);
 int filter_variant_count();
+int run_extend(sedef_ctx* ctx, const sedef_run_t* runs, int64_t nruns, const uint64_t* qrec,
+               int64_t nq, const int64_t* h_qoff, int nqseq, const uint64_t* trec, int64_t nt,
+               const int64_t* h_toff, int ntseq, const Derived& D, const sedef_params* p,
+               int64_t max_len, sedef_region_t* out, int64_t cap, int64_t* nout);
 int run_chain(sedef_ctx* ctx, const sedef_run_t* runs, int64_t nruns, const uint64_t* qrec, int64_t nq,
               const int64_t* h_qoff, int nqseq, const uint64_t* tsorted, int64_t nt,
               const uint32_t* toff, const int64_t* h_toff, int ntseq, const Derived& D,
@@ -239,10 +243,20 @@ struct TraceScope {
   TraceScope(sedef_ctx* c, const char* name);
   ~TraceScope();
 };
+// Stage label of the traced launches (reported as "stage:kernel"); the
+// previous label comes back when the scope ends.
+const char* ctx_set_stage(sedef_ctx* ctx, const char* stage);
+struct StageScope {
+  sedef_ctx* ctx;
+  const char* prev;
+  StageScope(sedef_ctx* c, const char* stage) : ctx(c), prev(ctx_set_stage(c, stage)) {}
+  ~StageScope() { ctx_set_stage(ctx, prev); }
+};
 // Context accessors for the kernel translation units.
 cudaStream_t ctx_stream(sedef_ctx* ctx);
 void* ctx_alloc(sedef_ctx* ctx, size_t bytes);
 std::vector<char> ctx_pool_snapshot(sedef_ctx* ctx);
+void ctx_pool_reset(sedef_ctx* ctx);  // every pool block free for the next call
 void ctx_pool_restore(sedef_ctx* ctx, const std::vector<char>& used_before);
 void* ctx_host(sedef_ctx* ctx, size_t bytes);  // pinned host scratch
 int ctx_device(sedef_ctx* ctx);

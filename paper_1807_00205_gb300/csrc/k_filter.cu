@@ -31,7 +31,10 @@
 // present hash, so the estimate |S(W_Q u W_T) n W_Q n W_T| is exact at every
 // breakpoint.  Runs whose domain exceeds the batched kernel's slots go to
 // k_refine (one warp per run, bitsets over the sorted domain).
+#include <chrono>
 #include <cstring>
+#include <mutex>
+#include <thread>
 
 #include "common.cuh"
 
@@ -421,18 +424,193 @@ __device__ __forceinline__ void for_hits(const FArgs& a, const Smem& S, int64_t 
   }
 }
 
+// One query window through a shared-memory tier: W_Q, the prefilter, the
+// collected hits, dense groups and the exact sweep; a window the tier
+// cannot hold goes to io.out_list (or io.wide_list).  Every thread of the
+// block calls it.
+template <int TPB, int LCAP, int GCAP, int SLOTS>
+__device__ void fast_window(const FArgs& a, const TierIO& io,
+                            FastSmemT<TPB, LCAP, GCAP, SLOTS>& S, int64_t wdx) {
+  constexpr int kFThreads = TPB;
+  constexpr int kLCap = LCAP;
+  constexpr int kGCap = GCAP;
+  const int64_t i = __ldcg(a.win_i + wdx);
+  const uint32_t qa = __ldcg(a.win_qa + wdx), qb = __ldcg(a.win_qb + wdx);
+  const int c = (int)(qb - qa);
+  if (c == 0) return;
+  if (c > kQCap) {
+    if (threadIdx.x == 0) io.out_list[atomicAdd(io.out_count, 1u)] = (uint32_t)wdx;
+    return;
+  }
+  for (int x = threadIdx.x; x < c; x += blockDim.x) {
+    const uint64_t r = __ldcg(a.qrec + qa + x);
+    S.qkey[x] = (rec_hash(r) << 1) | rec_strand(r);
+  }
+  __syncthreads();
+  QBuild qb_;
+  qb_.qkey = S.qkey;
+  qb_.dh = S.dh;
+  qb_.dm = S.dm;
+  qb_.pst = S.pst;
+  qb_.plen = S.plen;
+  qb_.tmp = S.tmp;
+  int64_t seq_lo = 0, seq_hi = 0;
+  if (a.self_mode == 2) {
+    const int sq = __ldcg(a.win_seq + wdx);
+    seq_lo = a.tseq[sq];
+    seq_hi = a.tseq[sq + 1];
+  }
+  const int s = build_wq(a, qb_, c, seq_lo, seq_hi);
+  if (s == 0) return;
+  // prefix of posting lengths (hit enumeration)
+  if (threadIdx.x < 32) {
+    uint32_t run = 0;
+    for (int base = 0; base < s; base += 32) {
+      const int x = base + threadIdx.x;
+      const uint32_t v = x < s ? S.plen[x] : 0u;
+      const uint32_t inc = warp_inclusive_sum(v);
+      if (x < s) S.pre[x] = run + inc - v;
+      run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (threadIdx.x == 0) S.pre[s] = run;
+  }
+  if (threadIdx.x == 0) {
+    S.s = s;
+    S.nhit = 0;
+    S.ovf = 0;
+  }
+  __syncthreads();
+  const uint32_t H = S.pre[s];
+  if (H == 0) return;
+  if (H > (uint32_t)kHMax || H > io.hlim) {
+    if (threadIdx.x == 0) {
+      if (H <= (uint32_t)kHMax && io.wide_list)
+        io.wide_list[atomicAdd(io.wide_count, 1u)] = (uint32_t)wdx;
+      else
+        io.out_list[atomicAdd(io.out_count, 1u)] = (uint32_t)wdx;
+    }
+    return;
+  }
+  uint32_t nslots = kSlots;
+  while (nslots < 4u * H && nslots < (uint32_t)SLOTS) nslots <<= 1;
+  const uint32_t smask = nslots - 1;
+  for (uint32_t x = threadIdx.x; x < nslots / 2; x += blockDim.x) S.slots[x] = 0;
+  __syncthreads();
+  const int m = a.mtab[s];
+  // pass 1: (bin, o) counts
+  for_hits(a, S, i, (int)H, [&](uint32_t t, uint32_t, uint32_t o) {
+    const uint32_t sl = slot_of(t, o, smask);
+    atomicAdd(&S.slots[sl >> 1], 1u << ((sl & 1) * 16));
+  });
+  __syncthreads();
+  // pass 2: collect the hits of bins whose pair (b, b+1) or (b-1, b) may pass
+  for_hits(a, S, i, (int)H, [&](uint32_t t, uint32_t hid, uint32_t o) {
+    const uint32_t b = t >> kBinShift;
+    const uint32_t c0 = slot_count(S.slots, slot_of(t, o, smask));
+    const uint32_t cn = slot_count(S.slots, (((b + 1) << 1) | o) & smask);
+    bool need = c0 + cn >= (uint32_t)m;
+    if (!need && b > 0) {
+      const uint32_t cp = slot_count(S.slots, (((b - 1) << 1) | o) & smask);
+      need = cp + c0 >= (uint32_t)m;
+    }
+    if (need) {
+      const int at = atomicAdd(&S.nhit, 1);
+      if (at < kLCap)
+        S.hits[at] = ((unsigned long long)o << 63) | ((unsigned long long)t << 20) | hid;
+    }
+  });
+  __syncthreads();
+  const int L = S.nhit;
+  if (L > kLCap) {
+    if (threadIdx.x == 0) io.out_list[atomicAdd(io.out_count, 1u)] = (uint32_t)wdx;
+    return;
+  }
+  // statistics count the windows this tier finishes (each window once)
+  if (L < m) {
+    if (io.stats && threadIdx.x == 0) {
+      atomicAdd(a.stats + 0, (unsigned long long)H);
+      atomicAdd(a.stats + 1, (unsigned long long)L);
+    }
+    return;
+  }
+  const int np = next_pow2(L < 2 ? 2 : L);
+  for (int x = L + threadIdx.x; x < np; x += blockDim.x) S.hits[x] = ~0ull;
+  __syncthreads();
+  block_sort(S.hits, np);
+  // dense groups of both strands (warp 0), then one warp per group
+  int split = 0;
+  {
+    // first hit with o = 1
+    int lo2 = 0, hi2 = L;
+    while (lo2 < hi2) {
+      const int mid = (lo2 + hi2) >> 1;
+      if ((S.hits[mid] >> 63) == 0) lo2 = mid + 1; else hi2 = mid;
+    }
+    split = lo2;
+  }
+  if (threadIdx.x < 32) {
+    int ng = 0;
+    for (int o = 0; o < 2; ++o) {
+      const unsigned long long* base = S.hits + (o ? split : 0);
+      const int64_t cnt = o ? L - split : split;
+      find_groups(
+          [&](int64_t x) {
+            const unsigned long long h = base[x];
+            return make_uint2((uint32_t)(h >> 20), (uint32_t)(h & 0xFFFFFu));
+          },
+          cnt, m, a.span, [&](int64_t lo, int64_t hi) {
+            if (threadIdx.x == 0 && ng < kGCap) {
+              S.glo[ng] = (uint32_t)(lo < 0 ? 0 : lo);
+              S.ghi[ng] = (uint32_t)hi;
+            }
+            ++ng;
+          });
+      if (o == 0 && threadIdx.x == 0) S.ng0 = ng;
+    }
+    if (threadIdx.x == 0) S.ng = ng;
+  }
+  __syncthreads();
+  const int ng = S.ng, ng0 = S.ng0;
+  if (ng > kGCap) {
+    if (threadIdx.x == 0) io.out_list[atomicAdd(io.out_count, 1u)] = (uint32_t)wdx;
+    return;
+  }
+  if (io.stats && threadIdx.x == 0) {
+    atomicAdd(a.stats + 0, (unsigned long long)H);
+    atomicAdd(a.stats + 1, (unsigned long long)L);
+  }
+  {
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+      WinInfo w;
+      w.i = i;
+      w.qseq = __ldcg(a.win_seq + wdx);
+      w.s = s;
+      w.m = m;
+      for (int g = warp; g < ng; g += kFThreads / 32) {
+        w.o = g < ng0 ? 0 : 1;
+        const unsigned long long* base = S.hits + (w.o ? split : 0);
+        const int64_t cnt = w.o ? L - split : split;
+        sweep_group(a, w,
+                    [&](int64_t x) {
+                      const unsigned long long h = base[x];
+                      return make_uint2((uint32_t)(h >> 20), (uint32_t)(h & 0xFFFFFu));
+                    },
+                    cnt, S.cnt[warp], (int64_t)S.glo[g], (int64_t)S.ghi[g]);
+      }
+    }
+  }
+}
+
 // SLOTS is the largest (bin, o) table; a window uses the smallest power of
 // two >= 4 H (at least 2,048 slots), so that aliasing stays rare however
 // many hits the window has.
 template <int TPB, int LCAP, int GCAP, int SLOTS>
 __global__ void __launch_bounds__(TPB) k_filter_fast(FArgs a, TierIO io) {
   using FastSmem = FastSmemT<TPB, LCAP, GCAP, SLOTS>;
-  constexpr int kFThreads = TPB;
-  constexpr int kLCap = LCAP;
-  constexpr int kGCap = GCAP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FastSmem& S = *reinterpret_cast<FastSmem*>(smem_raw);
-  for (int x = threadIdx.x; x < kQCap * (kFThreads / 32); x += blockDim.x) (&S.cnt[0][0])[x] = 0;
+  for (int x = threadIdx.x; x < kQCap * (TPB / 32); x += blockDim.x) (&S.cnt[0][0])[x] = 0;
   const int64_t count = io.in_list ? (int64_t)*io.in_count : a.nwin;
   while (true) {
     __syncthreads();
@@ -443,172 +621,7 @@ __global__ void __launch_bounds__(TPB) k_filter_fast(FArgs a, TierIO io) {
     __syncthreads();
     const int64_t wdx = S.win;
     if (wdx < 0) break;
-    const int64_t i = a.win_i[wdx];
-    const uint32_t qa = a.win_qa[wdx], qb = a.win_qb[wdx];
-    const int c = (int)(qb - qa);
-    if (c == 0) continue;
-    if (c > kQCap) {
-      if (threadIdx.x == 0) io.out_list[atomicAdd(io.out_count, 1u)] = (uint32_t)wdx;
-      continue;
-    }
-    for (int x = threadIdx.x; x < c; x += blockDim.x) {
-      const uint64_t r = __ldg(a.qrec + qa + x);
-      S.qkey[x] = (rec_hash(r) << 1) | rec_strand(r);
-    }
-    __syncthreads();
-    QBuild qb_;
-    qb_.qkey = S.qkey;
-    qb_.dh = S.dh;
-    qb_.dm = S.dm;
-    qb_.pst = S.pst;
-    qb_.plen = S.plen;
-    qb_.tmp = S.tmp;
-    int64_t seq_lo = 0, seq_hi = 0;
-    if (a.self_mode == 2) {
-      const int sq = a.win_seq[wdx];
-      seq_lo = a.tseq[sq];
-      seq_hi = a.tseq[sq + 1];
-    }
-    const int s = build_wq(a, qb_, c, seq_lo, seq_hi);
-    if (s == 0) continue;
-    // prefix of posting lengths (hit enumeration)
-    if (threadIdx.x < 32) {
-      uint32_t run = 0;
-      for (int base = 0; base < s; base += 32) {
-        const int x = base + threadIdx.x;
-        const uint32_t v = x < s ? S.plen[x] : 0u;
-        const uint32_t inc = warp_inclusive_sum(v);
-        if (x < s) S.pre[x] = run + inc - v;
-        run += __shfl_sync(0xffffffffu, inc, 31);
-      }
-      if (threadIdx.x == 0) S.pre[s] = run;
-    }
-    if (threadIdx.x == 0) {
-      S.s = s;
-      S.nhit = 0;
-      S.ovf = 0;
-    }
-    __syncthreads();
-    const uint32_t H = S.pre[s];
-    if (H == 0) continue;
-    if (H > (uint32_t)kHMax || H > io.hlim) {
-      if (threadIdx.x == 0) {
-        if (H <= (uint32_t)kHMax && io.wide_list)
-          io.wide_list[atomicAdd(io.wide_count, 1u)] = (uint32_t)wdx;
-        else
-          io.out_list[atomicAdd(io.out_count, 1u)] = (uint32_t)wdx;
-      }
-      continue;
-    }
-    uint32_t nslots = kSlots;
-    while (nslots < 4u * H && nslots < (uint32_t)SLOTS) nslots <<= 1;
-    const uint32_t smask = nslots - 1;
-    for (uint32_t x = threadIdx.x; x < nslots / 2; x += blockDim.x) S.slots[x] = 0;
-    __syncthreads();
-    const int m = a.mtab[s];
-    // pass 1: (bin, o) counts
-    for_hits(a, S, i, (int)H, [&](uint32_t t, uint32_t, uint32_t o) {
-      const uint32_t sl = slot_of(t, o, smask);
-      atomicAdd(&S.slots[sl >> 1], 1u << ((sl & 1) * 16));
-    });
-    __syncthreads();
-    // pass 2: collect the hits of bins whose pair (b, b+1) or (b-1, b) may pass
-    for_hits(a, S, i, (int)H, [&](uint32_t t, uint32_t hid, uint32_t o) {
-      const uint32_t b = t >> kBinShift;
-      const uint32_t c0 = slot_count(S.slots, slot_of(t, o, smask));
-      const uint32_t cn = slot_count(S.slots, (((b + 1) << 1) | o) & smask);
-      bool need = c0 + cn >= (uint32_t)m;
-      if (!need && b > 0) {
-        const uint32_t cp = slot_count(S.slots, (((b - 1) << 1) | o) & smask);
-        need = cp + c0 >= (uint32_t)m;
-      }
-      if (need) {
-        const int at = atomicAdd(&S.nhit, 1);
-        if (at < kLCap)
-          S.hits[at] = ((unsigned long long)o << 63) | ((unsigned long long)t << 20) | hid;
-      }
-    });
-    __syncthreads();
-    const int L = S.nhit;
-    if (L > kLCap) {
-      if (threadIdx.x == 0) io.out_list[atomicAdd(io.out_count, 1u)] = (uint32_t)wdx;
-      continue;
-    }
-    // statistics count the windows this tier finishes (each window once)
-    if (L < m) {
-      if (io.stats && threadIdx.x == 0) {
-        atomicAdd(a.stats + 0, (unsigned long long)H);
-        atomicAdd(a.stats + 1, (unsigned long long)L);
-      }
-      continue;
-    }
-    const int np = next_pow2(L < 2 ? 2 : L);
-    for (int x = L + threadIdx.x; x < np; x += blockDim.x) S.hits[x] = ~0ull;
-    __syncthreads();
-    block_sort(S.hits, np);
-    // dense groups of both strands (warp 0), then one warp per group
-    int split = 0;
-    {
-      // first hit with o = 1
-      int lo2 = 0, hi2 = L;
-      while (lo2 < hi2) {
-        const int mid = (lo2 + hi2) >> 1;
-        if ((S.hits[mid] >> 63) == 0) lo2 = mid + 1; else hi2 = mid;
-      }
-      split = lo2;
-    }
-    if (threadIdx.x < 32) {
-      int ng = 0;
-      for (int o = 0; o < 2; ++o) {
-        const unsigned long long* base = S.hits + (o ? split : 0);
-        const int64_t cnt = o ? L - split : split;
-        find_groups(
-            [&](int64_t x) {
-              const unsigned long long h = base[x];
-              return make_uint2((uint32_t)(h >> 20), (uint32_t)(h & 0xFFFFFu));
-            },
-            cnt, m, a.span, [&](int64_t lo, int64_t hi) {
-              if (threadIdx.x == 0 && ng < kGCap) {
-                S.glo[ng] = (uint32_t)(lo < 0 ? 0 : lo);
-                S.ghi[ng] = (uint32_t)hi;
-              }
-              ++ng;
-            });
-        if (o == 0 && threadIdx.x == 0) S.ng0 = ng;
-      }
-      if (threadIdx.x == 0) S.ng = ng;
-    }
-    __syncthreads();
-    const int ng = S.ng, ng0 = S.ng0;
-    if (ng > kGCap) {
-      if (threadIdx.x == 0) io.out_list[atomicAdd(io.out_count, 1u)] = (uint32_t)wdx;
-      continue;
-    }
-    if (io.stats && threadIdx.x == 0) {
-      atomicAdd(a.stats + 0, (unsigned long long)H);
-      atomicAdd(a.stats + 1, (unsigned long long)L);
-    }
-    {
-      const int warp = threadIdx.x >> 5;
-      if ((threadIdx.x & 31) == 0) {
-        WinInfo w;
-        w.i = i;
-        w.qseq = a.win_seq[wdx];
-        w.s = s;
-        w.m = m;
-        for (int g = warp; g < ng; g += kFThreads / 32) {
-          w.o = g < ng0 ? 0 : 1;
-          const unsigned long long* base = S.hits + (w.o ? split : 0);
-          const int64_t cnt = w.o ? L - split : split;
-          sweep_group(a, w,
-                      [&](int64_t x) {
-                        const unsigned long long h = base[x];
-                        return make_uint2((uint32_t)(h >> 20), (uint32_t)(h & 0xFFFFFu));
-                      },
-                      cnt, S.cnt[warp], (int64_t)S.glo[g], (int64_t)S.ghi[g]);
-        }
-      }
-    }
+    fast_window<TPB, LCAP, GCAP, SLOTS>(a, io, S, wdx);
   }
 }
 
@@ -2006,6 +2019,8 @@ template <int TPB, int LCAP, int GCAP, int SLOTS = kSlots>
 int launch_fast(sedef_ctx* ctx, const FArgs& a, const TierIO& io_in, int64_t max_windows,
                 const char* name) {
   const size_t sm = sizeof(FastSmemT<TPB, LCAP, GCAP, SLOTS>);
+  static_assert(sizeof(FastSmemT<TPB, LCAP, GCAP, SLOTS>) <= 227 * 1024,
+                "a filter tier must fit one CTA's shared memory");
   static bool attr = false;  // one per instantiation
   if (!attr) {
     SEDEF_CUDA(cudaFuncSetAttribute(k_filter_fast<TPB, LCAP, GCAP, SLOTS>,
@@ -2040,11 +2055,14 @@ constexpr int kNumTier1 = 4;
 const FastLaunch kTier2[] = {launch_fast<256, 8192, 2048>, launch_fast<256, 4096, 1024>,
                              launch_fast<512, 8192, 2048>};
 constexpr int kNumTier2 = 3;
-// Wide tier: windows with more hits than a 2,048-slot table can separate
+// Wide tiers: windows with more hits than a 2,048-slot table can separate
 // (long posting lists of a large target), before the global path.  32,768
-// (bin, o) slots keep the prefilter selective up to 65,535 hits.
+// (bin, o) slots keep the prefilter selective up to 65,535 hits; the second
+// wide tier holds 16,384 collected hits for windows in regions with many
+// homologous copies.
 constexpr int kWideSlots = 32768;
 const FastLaunch kTierWide = launch_fast<512, 2048, 512, kWideSlots>;
+const FastLaunch kTierWide2 = launch_fast<512, 16384, 1024, kWideSlots>;
 // variant = (warp tier off) * 12 + t1 * kNumTier2 + t2
 constexpr int kNumShapes = kNumTier1 * kNumTier2;
 constexpr int kNumVariants = 2 * kNumShapes;
@@ -2056,11 +2074,172 @@ int filter_variant_count() { return kNumVariants; }
 int scan_exclusive_u32(sedef_ctx* ctx, const uint32_t* in, uint32_t* out, int64_t n,
                        uint32_t* d_total);
 
+namespace {
+
+// The global path (eager) over the windows a.ov_list[0..nov): hits counted
+// per window, then batches of at most 2^27 hits emitted, radix-sorted by
+// (window, o, t) and swept by dense group.  Adds the hits to
+// *slow_hits_total.
+int global_path_eager(sedef_ctx* ctx, const FArgs& a, int64_t nov, unsigned long long* counters,
+                      int64_t* slow_hits_total) {
+  cudaStream_t st = ctx_stream(ctx);
+  // slow path: count, then batches of emit -> sort -> sweep
+  unsigned long long* ocnt = (unsigned long long*)ctx_alloc(ctx, (size_t)(nov + 1) * 8);
+  int32_t* os = (int32_t*)ctx_alloc(ctx, (size_t)(nov + 1) * 4);
+  if (!ocnt || !os) return SEDEF_ERR_OOM;
+  int64_t sgrid = nov < (int64_t)ctx_sm_count(ctx) * 4 ? nov : (int64_t)ctx_sm_count(ctx) * 4;
+  SEDEF_KERNEL(ctx, "k_slow_count",
+               k_slow_count<unsigned long long><<<(int)sgrid, kSThreads, 0, st>>>(a, nov, ocnt, os,
+                                                                                  nullptr, nullptr));
+  std::vector<unsigned long long> hc(nov + 1, 0);
+  SEDEF_CUDA(cudaMemcpyAsync(hc.data(), ocnt, (size_t)nov * 8, cudaMemcpyDeviceToHost, st));
+  SEDEF_CUDA(cudaStreamSynchronize(st));
+  std::vector<unsigned long long> base(nov + 1, 0);
+  for (int64_t v = 0; v < nov; ++v) base[v + 1] = base[v] + hc[v];
+  unsigned long long* d_base = (unsigned long long*)ctx_alloc(ctx, (size_t)(nov + 1) * 8);
+  if (!d_base) return SEDEF_ERR_OOM;
+  SEDEF_CUDA(cudaMemcpyAsync(d_base, base.data(), (size_t)(nov + 1) * 8, cudaMemcpyHostToDevice, st));
+  *slow_hits_total += (int64_t)base[nov];
+  const unsigned long long budget = 1ull << 27;  // hits per batch
+  int64_t v0 = 0;
+  while (v0 < nov) {
+    int64_t v1 = v0 + 1;
+    while (v1 < nov && base[v1 + 1] - base[v0] <= budget && v1 - v0 < (1 << 20)) ++v1;
+    const unsigned long long nh = base[v1] - base[v0];
+    // a batch's scratch goes back to the pool once the batch has run
+    const std::vector<char> used_before = ctx_pool_snapshot(ctx);
+    if (nh > 0) {
+      uint64_t* keys = (uint64_t*)ctx_alloc(ctx, (size_t)nh * 8);
+      uint32_t* vals = (uint32_t*)ctx_alloc(ctx, (size_t)nh * 4);
+      uint64_t* skeys = (uint64_t*)ctx_alloc(ctx, (size_t)nh * 8);
+      uint32_t* svals = (uint32_t*)ctx_alloc(ctx, (size_t)nh * 4);
+      if (!keys || !vals || !skeys || !svals) return SEDEF_ERR_OOM;
+      const int64_t nb = v1 - v0;
+      int g = (int)(nb < (int64_t)ctx_sm_count(ctx) * 4 ? nb : (int64_t)ctx_sm_count(ctx) * 4);
+      SEDEF_KERNEL(ctx, "k_slow_emit",
+                   k_slow_emit<<<g, kSThreads, 0, st>>>(a, v0, v1, d_base, keys, vals, nullptr,
+                                                        (int64_t)nh));
+      int wbits = 0;
+      while ((int64_t(1) << wbits) < nb) ++wbits;
+      SEDEF_TRY(radix_sort_u64(ctx, keys, vals, skeys, svals, (int64_t)nh, 0, 33 + wbits));
+      SlowTask* tasks = (SlowTask*)ctx_alloc(ctx, (size_t)nh * sizeof(SlowTask));
+      if (!tasks) return SEDEF_ERR_OOM;
+      SEDEF_CUDA(cudaMemsetAsync(counters + 6, 0, 8, st));
+      const int64_t gw = (nb + 7) / 8;
+      int g2 = (int)(gw < (int64_t)ctx_sm_count(ctx) * 8 ? gw : (int64_t)ctx_sm_count(ctx) * 8);
+      SEDEF_KERNEL(ctx, "k_slow_groups",
+                   k_slow_groups<<<g2, 256, 0, st>>>(a, v0, v1, d_base, os, skeys, tasks,
+                                                     counters + 6, (int64_t)nh, nullptr,
+                                                     (int64_t)nh));
+      SEDEF_KERNEL(ctx, "k_slow_tasks",
+                   k_slow_tasks<<<ctx_sm_count(ctx) * 8, 32 * kTaskWarps, 0, st>>>(
+                       a, v0, d_base, os, skeys, svals, tasks, counters + 6, (int64_t)nh));
+      SEDEF_CUDA(cudaStreamSynchronize(st));
+    }
+    ctx_pool_restore(ctx, used_before);
+    v0 = v1;
+  }
+  return SEDEF_OK;
+}
+
+// Orders the `total` raw runs by (window, o, j_a) into `runs` and refines
+// them (the winnowed MinHash estimate at every breakpoint of each run).
+// druns / dnt: live counts of a planned pass (nullptr when eager).
+int order_and_refine(sedef_ctx* ctx, const FArgs& a, const Derived& D, int nqseq,
+                     const int64_t* d_wbase, int64_t nwin, const uint32_t* wqa, const uint32_t* wqb,
+                     const uint64_t* qrec, int64_t nq, const uint64_t* trec, int64_t nt,
+                     const uint32_t* toff, unsigned long long* counters, sedef_run_t* raw,
+                     int64_t total, sedef_run_t* runs, const uint32_t* druns, const uint32_t* dnt) {
+  cudaStream_t st = ctx_stream(ctx);
+  // order runs by (i, o); the sweep emits each window's runs in j order
+  ctx_set_stage(ctx, "runsort");
+  uint64_t* keys = (uint64_t*)ctx_alloc(ctx, (size_t)total * 8);
+  uint64_t* skeys = (uint64_t*)ctx_alloc(ctx, (size_t)total * 8);
+  uint32_t* perm = (uint32_t*)ctx_alloc(ctx, (size_t)total * 4);
+  if (!keys || !skeys || !perm) return SEDEF_ERR_OOM;
+  const int tb = (int)((total + 255) / 256);
+  int wb = 1;
+  while ((int64_t(1) << wb) < nwin) ++wb;
+  if (33 + wb <= 64) {
+    SEDEF_KERNEL(ctx, "k_run_keys",
+                 k_run_keys<<<tb, 256, 0, st>>>(raw, total, a.qseq, nqseq, d_wbase, D.step, 0, keys,
+                                                druns));
+    SEDEF_TRY(radix_sort_u64(ctx, keys, nullptr, skeys, perm, total, 0, 33 + wb, druns));
+  } else {
+    // stable two-pass order: by j_a, then by (window, o)
+    uint32_t* perm1 = (uint32_t*)ctx_alloc(ctx, (size_t)total * 4);
+    uint32_t* perm2 = (uint32_t*)ctx_alloc(ctx, (size_t)total * 4);
+    uint64_t* k2 = (uint64_t*)ctx_alloc(ctx, (size_t)total * 8);
+    if (!perm1 || !perm2 || !k2) return SEDEF_ERR_OOM;
+    SEDEF_KERNEL(ctx, "k_run_keys",
+                 k_run_keys<<<tb, 256, 0, st>>>(raw, total, a.qseq, nqseq, d_wbase, D.step, 1, keys,
+                                                druns));
+    SEDEF_TRY(radix_sort_u64(ctx, keys, nullptr, skeys, perm1, total, 0, 32, druns));
+    SEDEF_KERNEL(ctx, "k_run_keys",
+                 k_run_keys<<<tb, 256, 0, st>>>(raw, total, a.qseq, nqseq, d_wbase, D.step, 2, keys,
+                                                druns));
+    SEDEF_KERNEL(ctx, "k_permute_u64",
+                 k_permute_u64<<<tb, 256, 0, st>>>(keys, perm1, total, k2, druns));
+    SEDEF_TRY(radix_sort_u64(ctx, k2, nullptr, skeys, perm2, total, 0, wb + 1, druns));
+    SEDEF_KERNEL(ctx, "k_compose_perm",
+                 k_compose_perm<<<tb, 256, 0, st>>>(perm1, perm2, total, perm, druns));
+  }
+  SEDEF_KERNEL(ctx, "k_gather_runs",
+               k_gather_runs<<<tb, 256, 0, st>>>(raw, perm, total, runs, druns));
+  // refine: lean kernel over all runs, then the large kernel over the runs
+  // it handed over (their count stays on the device)
+  ctx_set_stage(ctx, "refine");
+  uint32_t* big = (uint32_t*)ctx_alloc(ctx, (size_t)total * 4);
+  if (!big) return SEDEF_ERR_OOM;
+  RefineArgs ra;
+  ra.runs = runs;
+  ra.nruns = total;
+  ra.qrec = qrec;
+  ra.nq = nq;
+  ra.trec = trec;
+  ra.nt = nt;
+  ra.dnruns = druns;
+  ra.dnt = dnt;
+  ra.toff = toff;
+  ra.mtab = a.mtab;
+  ra.span = D.span;
+  ra.max_occ = D.max_occ;
+  ra.self_mode = D.self_mode;
+  ra.big = big;
+  ra.nbig = (unsigned int*)(counters + 3);
+  uint4* ranges = (uint4*)ctx_alloc(ctx, (size_t)total * sizeof(uint4));
+  if (!ranges) return SEDEF_ERR_OOM;
+  SEDEF_KERNEL(ctx, "k_run_ranges",
+               k_run_ranges<<<tb, 256, 0, st>>>(runs, total, a.qseq, nqseq, d_wbase, D.step, wqa, wqb,
+                                                trec, nt, D.span, ranges, druns, dnt));
+  ra.ranges = ranges;
+  ra.next = counters + 6;
+  SEDEF_CUDA(cudaMemsetAsync(counters + 6, 0, 16, st));
+  using Big = RefineWarpT<kMaxWindowRecs, 1024>;
+  const size_t lean_sm = sizeof(BatchWarp) * kBWarps, big_sm = sizeof(Big) * kRWarpsBig;
+  int rper = 0;
+  SEDEF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rper, k_refine_batch, 32 * kBWarps,
+                                                           lean_sm));
+  if (rper < 1) rper = 1;
+  int64_t rgrid = (total + kBWarps * 32 - 1) / (kBWarps * 32);
+  if (rgrid > (int64_t)ctx_sm_count(ctx) * rper) rgrid = (int64_t)ctx_sm_count(ctx) * rper;
+  if (rgrid < 1) rgrid = 1;
+  SEDEF_KERNEL(ctx, "k_refine",
+               k_refine_batch<<<(int)rgrid, 32 * kBWarps, lean_sm, st>>>(ra));
+  SEDEF_KERNEL(ctx, "k_refine_big",
+               k_refine<kMaxWindowRecs, 1024, false><<<ctx_sm_count(ctx), 32 * kRWarpsBig, big_sm,
+                                                       st>>>(ra));
+  return SEDEF_OK;
+}
+
+}  // namespace
+
 int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* h_qoff, int nqseq,
                const uint64_t* trec, const uint64_t* tsorted, const uint32_t* toff, int64_t nt,
                const int64_t* h_toff, int ntseq, const Derived& D, const int32_t* h_mtab,
                sedef_run_t* runs, int64_t cap, int64_t* nruns, int tune, Planned* pl) {
   cudaStream_t st = ctx_stream(ctx);
+  StageScope stage(ctx, "filter");  // the caller's label comes back on return
   if (pl && tune) return fail(SEDEF_ERR_INVALID, "sedef_filter: no autotuning inside a planned pass");
   // live record counts of a planned pass (query and target are one sketch)
   const uint32_t* dnq = pl ? pl->n_rec : nullptr;
@@ -2104,16 +2283,18 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   uint32_t* ovl1 = (uint32_t*)ctx_alloc(ctx, (size_t)nwin * 4);
   uint32_t* ovl0 = (uint32_t*)ctx_alloc(ctx, (size_t)nwin * 4);
   uint32_t* ovlw = (uint32_t*)ctx_alloc(ctx, (size_t)nwin * 4);
-  if (!ovl0 || !ovlw) return SEDEF_ERR_OOM;
+  uint32_t* ovlw2 = (uint32_t*)ctx_alloc(ctx, (size_t)nwin * 4);
+  if (!ovl0 || !ovlw || !ovlw2) return SEDEF_ERR_OOM;
   // [0] runs, [1] windows for the global path, [2] tier-1 work, [3] large
   // refine runs, [4] hits, [5] collected hits, [6]/[7] task and refine work,
   // [8] tier-2 work, [9] windows tier 1 handed to tier 2, [10] sample size,
   // [11] global-path hits (planned pass), [12]/[13] warp-tier hand-overs and
-  // work, [14] windows for the wide tier, [15] wide-tier work
-  unsigned long long* counters = (unsigned long long*)ctx_alloc(ctx, 128);
+  // work, [14] windows for the wide tier, [15] wide-tier work, [16]/[17] the
+  // same for the second wide tier
+  unsigned long long* counters = (unsigned long long*)ctx_alloc(ctx, 256);
   sedef_run_t* raw = (sedef_run_t*)ctx_alloc(ctx, (size_t)(cap > 0 ? cap : 1) * sizeof(sedef_run_t));
   if (!wi || !wqa || !wqb || !wseq || !ovl || !ovl1 || !counters || !raw) return SEDEF_ERR_OOM;
-  SEDEF_CUDA(cudaMemsetAsync(counters, 0, 128, st));
+  SEDEF_CUDA(cudaMemsetAsync(counters, 0, 256, st));
 
   FArgs a;
   a.qrec = qrec;
@@ -2179,7 +2360,7 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
       const bool warp_tier = v < kNumShapes;
       for (int rep = 0; rep < 2; ++rep) {  // the first repetition warms up
         SEDEF_CUDA(cudaMemsetAsync(counters, 0, 80, st));
-        SEDEF_CUDA(cudaMemsetAsync(counters + 12, 0, 32, st));
+        SEDEF_CUDA(cudaMemsetAsync(counters + 12, 0, 48, st));
         TierIO io0{d_sample, (const unsigned int*)(counters + 10), ovl0,
                    (unsigned int*)(counters + 12), (unsigned int*)(counters + 13), 0};
         TierIO io{warp_tier ? ovl0 : d_sample,
@@ -2191,13 +2372,16 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
                    (unsigned int*)(counters + 8), 0};
         io2.wide_list = ovlw;
         io2.wide_count = (unsigned int*)(counters + 14);
-        TierIO iow{ovlw, (const unsigned int*)(counters + 14), ovl, (unsigned int*)(counters + 1),
-                   (unsigned int*)(counters + 15), 0};
+        TierIO iow{ovlw, (const unsigned int*)(counters + 14), ovlw2,
+                   (unsigned int*)(counters + 16), (unsigned int*)(counters + 15), 0};
+        TierIO iow2{ovlw2, (const unsigned int*)(counters + 16), ovl,
+                    (unsigned int*)(counters + 1), (unsigned int*)(counters + 17), 0};
         SEDEF_CUDA(cudaEventRecord(e0, st));
         if (warp_tier) SEDEF_TRY(launch_warp_tier(ctx, a, io0, ns, "k_filter_tune"));
         SEDEF_TRY(kTier1[sh / kNumTier2](ctx, a, io, ns, "k_filter_tune"));
         SEDEF_TRY(kTier2[sh % kNumTier2](ctx, a, io2, ns, "k_filter_tune"));
         SEDEF_TRY(kTierWide(ctx, a, iow, ns, "k_filter_tune"));
+        SEDEF_TRY(kTierWide2(ctx, a, iow2, ns, "k_filter_tune"));
         SEDEF_CUDA(cudaEventRecord(e1, st));
         SEDEF_CUDA(cudaEventSynchronize(e1));
         SEDEF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
@@ -2239,9 +2423,12 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
     io2.wide_list = ovlw;
     io2.wide_count = (unsigned int*)(counters + 14);
     SEDEF_TRY(kTier2[sh % kNumTier2](ctx, a, io2, nwin, "k_filter_mid"));
-    TierIO iow{ovlw, (const unsigned int*)(counters + 14), ovl, (unsigned int*)(counters + 1),
+    TierIO iow{ovlw, (const unsigned int*)(counters + 14), ovlw2, (unsigned int*)(counters + 16),
                (unsigned int*)(counters + 15), 1};
     SEDEF_TRY(kTierWide(ctx, a, iow, nwin, "k_filter_wide"));
+    TierIO iow2{ovlw2, (const unsigned int*)(counters + 16), ovl, (unsigned int*)(counters + 1),
+                (unsigned int*)(counters + 17), 1};
+    SEDEF_TRY(kTierWide2(ctx, a, iow2, nwin, "k_filter_wide2"));
   }
 
   unsigned long long* h_cnt = nullptr;
@@ -2297,62 +2484,7 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   }
 
   if (nov > 0) {
-    // slow path: count, then batches of emit -> sort -> sweep
-    unsigned long long* ocnt = (unsigned long long*)ctx_alloc(ctx, (size_t)(nov + 1) * 8);
-    int32_t* os = (int32_t*)ctx_alloc(ctx, (size_t)(nov + 1) * 4);
-    if (!ocnt || !os) return SEDEF_ERR_OOM;
-    int64_t sgrid = nov < (int64_t)ctx_sm_count(ctx) * 4 ? nov : (int64_t)ctx_sm_count(ctx) * 4;
-    SEDEF_KERNEL(ctx, "k_slow_count",
-                 k_slow_count<unsigned long long><<<(int)sgrid, kSThreads, 0, st>>>(a, nov, ocnt, os,
-                                                                                    nullptr, nullptr));
-    std::vector<unsigned long long> hc(nov + 1, 0);
-    SEDEF_CUDA(cudaMemcpyAsync(hc.data(), ocnt, (size_t)nov * 8, cudaMemcpyDeviceToHost, st));
-    SEDEF_CUDA(cudaStreamSynchronize(st));
-    std::vector<unsigned long long> base(nov + 1, 0);
-    for (int64_t v = 0; v < nov; ++v) base[v + 1] = base[v] + hc[v];
-    unsigned long long* d_base = (unsigned long long*)ctx_alloc(ctx, (size_t)(nov + 1) * 8);
-    if (!d_base) return SEDEF_ERR_OOM;
-    SEDEF_CUDA(cudaMemcpyAsync(d_base, base.data(), (size_t)(nov + 1) * 8, cudaMemcpyHostToDevice, st));
-    slow_hits_total = (int64_t)base[nov];
-    const unsigned long long budget = 1ull << 27;  // hits per batch
-    int64_t v0 = 0;
-    while (v0 < nov) {
-      int64_t v1 = v0 + 1;
-      while (v1 < nov && base[v1 + 1] - base[v0] <= budget && v1 - v0 < (1 << 20)) ++v1;
-      const unsigned long long nh = base[v1] - base[v0];
-      // a batch's scratch goes back to the pool once the batch has run
-      const std::vector<char> used_before = ctx_pool_snapshot(ctx);
-      if (nh > 0) {
-        uint64_t* keys = (uint64_t*)ctx_alloc(ctx, (size_t)nh * 8);
-        uint32_t* vals = (uint32_t*)ctx_alloc(ctx, (size_t)nh * 4);
-        uint64_t* skeys = (uint64_t*)ctx_alloc(ctx, (size_t)nh * 8);
-        uint32_t* svals = (uint32_t*)ctx_alloc(ctx, (size_t)nh * 4);
-        if (!keys || !vals || !skeys || !svals) return SEDEF_ERR_OOM;
-        const int64_t nb = v1 - v0;
-        int g = (int)(nb < (int64_t)ctx_sm_count(ctx) * 4 ? nb : (int64_t)ctx_sm_count(ctx) * 4);
-        SEDEF_KERNEL(ctx, "k_slow_emit",
-                     k_slow_emit<<<g, kSThreads, 0, st>>>(a, v0, v1, d_base, keys, vals, nullptr,
-                                                          (int64_t)nh));
-        int wbits = 0;
-        while ((int64_t(1) << wbits) < nb) ++wbits;
-        SEDEF_TRY(radix_sort_u64(ctx, keys, vals, skeys, svals, (int64_t)nh, 0, 33 + wbits));
-        SlowTask* tasks = (SlowTask*)ctx_alloc(ctx, (size_t)nh * sizeof(SlowTask));
-        if (!tasks) return SEDEF_ERR_OOM;
-        SEDEF_CUDA(cudaMemsetAsync(counters + 6, 0, 8, st));
-        const int64_t gw = (nb + 7) / 8;
-        int g2 = (int)(gw < (int64_t)ctx_sm_count(ctx) * 8 ? gw : (int64_t)ctx_sm_count(ctx) * 8);
-        SEDEF_KERNEL(ctx, "k_slow_groups",
-                     k_slow_groups<<<g2, 256, 0, st>>>(a, v0, v1, d_base, os, skeys, tasks,
-                                                       counters + 6, (int64_t)nh, nullptr,
-                                                       (int64_t)nh));
-        SEDEF_KERNEL(ctx, "k_slow_tasks",
-                     k_slow_tasks<<<ctx_sm_count(ctx) * 8, 32 * kTaskWarps, 0, st>>>(
-                         a, v0, d_base, os, skeys, svals, tasks, counters + 6, (int64_t)nh));
-        SEDEF_CUDA(cudaStreamSynchronize(st));
-      }
-      ctx_pool_restore(ctx, used_before);
-      v0 = v1;
-    }
+    SEDEF_TRY(global_path_eager(ctx, a, nov, counters, &slow_hits_total));
     SEDEF_CUDA(cudaMemcpyAsync(h_cnt, counters, 8, cudaMemcpyDeviceToHost, st));
     SEDEF_CUDA(cudaStreamSynchronize(st));
   }
@@ -2373,83 +2505,8 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
     if (total > cap) return fail(SEDEF_ERR_CAPACITY, "sedef_filter: run buffer too small");
     if (total == 0) return SEDEF_OK;
   }
-  // order runs by (i, o); the sweep emits each window's runs in j order
-  uint64_t* keys = (uint64_t*)ctx_alloc(ctx, (size_t)total * 8);
-  uint64_t* skeys = (uint64_t*)ctx_alloc(ctx, (size_t)total * 8);
-  uint32_t* perm = (uint32_t*)ctx_alloc(ctx, (size_t)total * 4);
-  if (!keys || !skeys || !perm) return SEDEF_ERR_OOM;
-  const int tb = (int)((total + 255) / 256);
-  int wb = 1;
-  while ((int64_t(1) << wb) < nwin) ++wb;
-  const int64_t* d_wbase = (const int64_t*)(d_up + ow);
-  if (33 + wb <= 64) {
-    SEDEF_KERNEL(ctx, "k_run_keys",
-                 k_run_keys<<<tb, 256, 0, st>>>(raw, total, a.qseq, nqseq, d_wbase, D.step, 0, keys,
-                                                druns));
-    SEDEF_TRY(radix_sort_u64(ctx, keys, nullptr, skeys, perm, total, 0, 33 + wb, druns));
-  } else {
-    // stable two-pass order: by j_a, then by (window, o)
-    uint32_t* perm1 = (uint32_t*)ctx_alloc(ctx, (size_t)total * 4);
-    uint32_t* perm2 = (uint32_t*)ctx_alloc(ctx, (size_t)total * 4);
-    uint64_t* k2 = (uint64_t*)ctx_alloc(ctx, (size_t)total * 8);
-    if (!perm1 || !perm2 || !k2) return SEDEF_ERR_OOM;
-    SEDEF_KERNEL(ctx, "k_run_keys",
-                 k_run_keys<<<tb, 256, 0, st>>>(raw, total, a.qseq, nqseq, d_wbase, D.step, 1, keys,
-                                                druns));
-    SEDEF_TRY(radix_sort_u64(ctx, keys, nullptr, skeys, perm1, total, 0, 32, druns));
-    SEDEF_KERNEL(ctx, "k_run_keys",
-                 k_run_keys<<<tb, 256, 0, st>>>(raw, total, a.qseq, nqseq, d_wbase, D.step, 2, keys,
-                                                druns));
-    SEDEF_KERNEL(ctx, "k_permute_u64",
-                 k_permute_u64<<<tb, 256, 0, st>>>(keys, perm1, total, k2, druns));
-    SEDEF_TRY(radix_sort_u64(ctx, k2, nullptr, skeys, perm2, total, 0, wb + 1, druns));
-    SEDEF_KERNEL(ctx, "k_compose_perm",
-                 k_compose_perm<<<tb, 256, 0, st>>>(perm1, perm2, total, perm, druns));
-  }
-  SEDEF_KERNEL(ctx, "k_gather_runs",
-               k_gather_runs<<<tb, 256, 0, st>>>(raw, perm, total, runs, druns));
-  // refine: lean kernel over all runs, then the large kernel over the runs
-  // it handed over (their count stays on the device)
-  uint32_t* big = (uint32_t*)ctx_alloc(ctx, (size_t)total * 4);
-  if (!big) return SEDEF_ERR_OOM;
-  RefineArgs ra;
-  ra.runs = runs;
-  ra.nruns = total;
-  ra.qrec = qrec;
-  ra.nq = nq;
-  ra.trec = trec;
-  ra.nt = nt;
-  ra.dnruns = druns;
-  ra.dnt = dnt;
-  ra.toff = toff;
-  ra.mtab = a.mtab;
-  ra.span = D.span;
-  ra.max_occ = D.max_occ;
-  ra.self_mode = D.self_mode;
-  ra.big = big;
-  ra.nbig = (unsigned int*)(counters + 3);
-  uint4* ranges = (uint4*)ctx_alloc(ctx, (size_t)total * sizeof(uint4));
-  if (!ranges) return SEDEF_ERR_OOM;
-  SEDEF_KERNEL(ctx, "k_run_ranges",
-               k_run_ranges<<<tb, 256, 0, st>>>(runs, total, a.qseq, nqseq, d_wbase, D.step, wqa, wqb,
-                                                trec, nt, D.span, ranges, druns, dnt));
-  ra.ranges = ranges;
-  ra.next = counters + 6;
-  SEDEF_CUDA(cudaMemsetAsync(counters + 6, 0, 16, st));
-  using Big = RefineWarpT<kMaxWindowRecs, 1024>;
-  const size_t lean_sm = sizeof(BatchWarp) * kBWarps, big_sm = sizeof(Big) * kRWarpsBig;
-  int rper = 0;
-  SEDEF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rper, k_refine_batch, 32 * kBWarps,
-                                                           lean_sm));
-  if (rper < 1) rper = 1;
-  int64_t rgrid = (total + kBWarps * 32 - 1) / (kBWarps * 32);
-  if (rgrid > (int64_t)ctx_sm_count(ctx) * rper) rgrid = (int64_t)ctx_sm_count(ctx) * rper;
-  if (rgrid < 1) rgrid = 1;
-  SEDEF_KERNEL(ctx, "k_refine",
-               k_refine_batch<<<(int)rgrid, 32 * kBWarps, lean_sm, st>>>(ra));
-  SEDEF_KERNEL(ctx, "k_refine_big",
-               k_refine<kMaxWindowRecs, 1024, false><<<ctx_sm_count(ctx), 32 * kRWarpsBig, big_sm,
-                                                       st>>>(ra));
+  SEDEF_TRY(order_and_refine(ctx, a, D, nqseq, (const int64_t*)(d_up + ow), nwin, wqa, wqb, qrec,
+                             nq, trec, nt, toff, counters, raw, total, runs, druns, dnt));
   if (pl) return SEDEF_OK;
   SEDEF_CUDA(cudaMemcpyAsync(h_cnt, counters, 64, cudaMemcpyDeviceToHost, st));
   SEDEF_CUDA(cudaStreamSynchronize(st));
@@ -2463,3 +2520,635 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
 }
 
 }  // namespace sedef
+
+// ===================================================== continuous batching ==
+//
+// Serving against a resident target index.  A persistent kernel (one CTA
+// per SM with the wide tier's shared memory, so that every SM keeps room for
+// the kernels of other streams) drains a work queue of query windows: a
+// ring of (slot, window) items in mapped host memory that the host
+// publishes as requests are admitted into free slots.  A slot holds one
+// request's query sketch, window table and outputs in device memory that
+// the server allocated once.  A CTA claims an item only when the ring holds
+// one (compare-and-swap on the device head below the published tail), runs
+// the window through the shared-memory tier into its slot's runs (windows
+// the tier cannot hold into the slot's overflow list), and the CTA that
+// finishes a slot's last window writes the slot's epoch into a mapped
+// completion word.  The host then runs the global path for the overflow
+// windows, the run ordering, refine, chaining and merging of that slot on
+// its own stream while the kernel keeps serving the other slots.  A CTA that
+// finds the ring empty sleeps and polls; when nothing arrives for
+// idle_timeout (or the host raises the stop word) it leaves, and a CTA that
+// left on the idle limit records SEDEF_ERR_TIMEOUT in the control block.
+// The host relaunches the kernel when work arrives and no CTA is running.
+// Query-side data is read past L1 (a slot's buffers are refilled while the
+// kernel runs).
+namespace sedef {
+namespace {
+
+constexpr int kServeMaxSlots = 64;
+constexpr int kServeTPB = 512, kServeLCap = 2048, kServeGCap = 512;
+using ServeSmem = FastSmemT<kServeTPB, kServeLCap, kServeGCap, kWideSlots>;
+
+struct ServeItem {
+  uint32_t slot, window;
+};
+
+// Control block in mapped host memory (both sides read and write it).
+struct ServeCtl {
+  unsigned long long tail;                   // items published (host)
+  int stop;                                  // host: leave now
+  int status;                                // device: SEDEF_ERR_TIMEOUT after an idle exit
+  long long nwin[kServeMaxSlots];            // host: windows of the slot's request
+  unsigned int epoch[kServeMaxSlots];        // host: admission number of the slot
+  unsigned int done_epoch[kServeMaxSlots];   // device: epoch whose last window finished
+};
+
+// Per-slot constants in device memory (written once, at creation).
+struct SlotDev {
+  FArgs a;              // the slot's query, windows and outputs
+  unsigned int* done;   // windows finished (reset at admission)
+};
+
+struct ServeArgs {
+  const SlotDev* slots;
+  const ServeItem* ring;     // mapped host memory (device view)
+  unsigned long long ring_cap;
+  ServeCtl* ctl;             // mapped host memory (device view)
+  unsigned long long* head;  // device memory
+  unsigned long long idle_ns;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__global__ void __launch_bounds__(kServeTPB) k_serve(ServeArgs sv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ServeSmem& S = *reinterpret_cast<ServeSmem*>(smem_raw);
+  __shared__ long long s_item;
+  __shared__ unsigned int s_slot, s_window;
+  for (int x = threadIdx.x; x < kQCap * (kServeTPB / 32); x += blockDim.x) (&S.cnt[0][0])[x] = 0;
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // claim the next published item; sleep while there is none, at most
+      // idle_ns in a row
+      long long got = -1;
+      const unsigned long long idle_from = global_ns();
+      unsigned int nap = 256;
+      while (true) {
+        const unsigned long long t = ld_acquire_sys(&sv.ctl->tail);
+        const unsigned long long h = *(volatile unsigned long long*)sv.head;
+        if (h < t) {
+          if (atomicCAS(sv.head, h, h + 1) == h) {
+            got = (long long)h;
+            break;
+          }
+          continue;
+        }
+        if (*(volatile int*)&sv.ctl->stop) break;
+        if (global_ns() - idle_from > sv.idle_ns) {
+          *(volatile int*)&sv.ctl->status = SEDEF_ERR_TIMEOUT;
+          __threadfence_system();
+          break;
+        }
+        __nanosleep(nap);
+        if (nap < 8192) nap <<= 1;
+      }
+      s_item = got;
+      if (got >= 0) {
+        const volatile ServeItem* it = sv.ring + (unsigned long long)got % sv.ring_cap;
+        s_slot = it->slot;
+        s_window = it->window;
+      }
+    }
+    __syncthreads();
+    if (s_item < 0) break;
+    const unsigned int slot = s_slot;
+    const SlotDev& sd = sv.slots[slot];
+    TierIO io;
+    io.in_list = nullptr;
+    io.in_count = nullptr;
+    io.out_list = sd.a.ov_list;
+    io.out_count = sd.a.nov;
+    io.next = nullptr;
+    io.stats = 1;
+    fast_window<kServeTPB, kServeLCap, kServeGCap, kWideSlots>(sd.a, io, S, (int64_t)s_window);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();  // this window's runs and hand-overs before its count
+      const unsigned int d = atomicAdd(sd.done, 1u) + 1u;
+      if ((long long)d == *(volatile long long*)&sv.ctl->nwin[slot]) {
+        __threadfence_system();
+        *(volatile unsigned int*)&sv.ctl->done_epoch[slot] =
+            *(volatile unsigned int*)&sv.ctl->epoch[slot];
+        __threadfence_system();
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// Host side of one server.
+struct Server {
+  int device = 0;
+  int nslots = 0;
+  int64_t slot_bases = 0;
+  Derived D;
+  sedef_params P;
+  std::vector<int32_t> mtab;
+  // the resident target (owned by the caller)
+  const uint64_t* trec = nullptr;
+  const uint64_t* tsorted = nullptr;
+  const uint32_t* toff = nullptr;
+  int64_t nt = 0;
+  std::vector<int64_t> h_toff;
+  // streams and contexts: admission, the persistent kernel, finishing
+  cudaStream_t s_prep = nullptr, s_kern = nullptr, s_fin = nullptr;
+  sedef_ctx* c_prep = nullptr;
+  sedef_ctx* c_fin = nullptr;
+  cudaEvent_t kern_done = nullptr;
+  bool kern_launched = false;
+  char* d_shared = nullptr;  // target offsets and the m table
+  // mapped host memory: host views and device views
+  ServeCtl* ctl = nullptr;
+  ServeCtl* d_ctl = nullptr;
+  ServeItem* ring = nullptr;
+  ServeItem* d_ring = nullptr;
+  unsigned long long ring_cap = 0;
+  unsigned long long tail = 0;
+  unsigned long long* d_head = nullptr;
+  SlotDev* d_slots = nullptr;
+  double idle_s = 1.0;
+  struct Slot {
+    uint8_t* seq = nullptr;
+    uint32_t *packed = nullptr, *mask = nullptr, *nbits = nullptr;
+    uint64_t* qrec = nullptr;
+    int64_t rec_cap = 0;
+    uint32_t *wi = nullptr, *wqa = nullptr, *wqb = nullptr, *ov = nullptr;
+    int32_t* wseq = nullptr;
+    int64_t win_cap = 0;
+    sedef_run_t* raw = nullptr;
+    int64_t run_cap = 0;
+    unsigned long long* counters = nullptr;  // 32 words, as in the filter
+    unsigned int* done = nullptr;
+    char* d_up = nullptr;                    // query offsets (2) and window bases (2)
+    int state = 0;                           // 0 free, 1 admitted, 2 queued, 3 filtered
+    unsigned int epoch = 0;
+    int64_t len = 0, nrec = 0, nwin = 0;
+    FArgs a;
+  };
+  std::vector<Slot> slots;
+  std::vector<void*> dev_allocs;
+  std::mutex mu;
+};
+
+namespace {
+
+int server_alloc(Server* s, void** p, size_t bytes) {
+  if (cudaMalloc(p, bytes ? bytes : 256) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(SEDEF_ERR_OOM, "server: device allocation failed");
+  }
+  s->dev_allocs.push_back(*p);
+  return SEDEF_OK;
+}
+
+// Launches the persistent kernel unless a launch is still running.  Caller
+// holds mu.
+int server_kick(Server* s) {
+  if (s->kern_launched) {
+    const cudaError_t q = cudaEventQuery(s->kern_done);
+    if (q == cudaErrorNotReady) return SEDEF_OK;
+    if (q != cudaSuccess) return cuda_fail(q, "server: kernel event");
+  }
+  __atomic_store_n(&s->ctl->status, 0, __ATOMIC_RELEASE);
+  ServeArgs sv;
+  sv.slots = s->d_slots;
+  sv.ring = s->d_ring;
+  sv.ring_cap = s->ring_cap;
+  sv.ctl = s->d_ctl;
+  sv.head = s->d_head;
+  sv.idle_ns = (unsigned long long)(s->idle_s * 1e9);
+  const size_t sm = sizeof(ServeSmem);
+  SEDEF_CUDA(cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_serve<<<ctx_sm_count(s->c_prep), kServeTPB, sm, s->s_kern>>>(sv);
+  count_launch();
+  SEDEF_LAUNCHED("k_serve");
+  SEDEF_CUDA(cudaEventRecord(s->kern_done, s->s_kern));
+  s->kern_launched = true;
+  return SEDEF_OK;
+}
+
+// Admission work of one slot on the prep stream: query upload, pack,
+// sketch, window table, counters; synchronizes.
+int server_prepare(Server* s, Server::Slot& L, const uint8_t* h_query, int64_t len) {
+  sedef_ctx* c = s->c_prep;
+  cudaStream_t st = s->s_prep;
+  ctx_pool_reset(c);
+  if (len == 0) {
+    L.len = L.nrec = L.nwin = 0;
+    return SEDEF_OK;
+  }
+  SEDEF_CUDA(cudaMemcpyAsync(L.seq, h_query, (size_t)len, cudaMemcpyHostToDevice, st));
+  SEDEF_TRY(launch_pack(c, L.seq, len, L.packed, L.mask, L.nbits));
+  const int64_t qoff[2] = {0, len};
+  int64_t nrec = 0;
+  SEDEF_TRY(run_sketch(c, L.packed, L.mask, L.nbits, qoff, 1, s->D, L.qrec, L.rec_cap, &nrec));
+  if (nrec > L.rec_cap) return fail(SEDEF_ERR_CAPACITY, "server: sketch exceeds the slot");
+  const int64_t nwin = len >= s->D.n ? (len - s->D.n) / s->D.step + 1 : 0;
+  const int64_t up[4] = {0, len, 0, nwin};  // query offsets, window bases
+  int64_t* h_up = (int64_t*)ctx_host(c, 64);
+  if (!h_up) return SEDEF_ERR_OOM;
+  std::memcpy(h_up, up, sizeof(up));
+  SEDEF_CUDA(cudaMemcpyAsync(L.d_up, h_up, sizeof(up), cudaMemcpyHostToDevice, st));
+  SEDEF_CUDA(cudaMemsetAsync(L.counters, 0, 256 + 64, st));
+  if (nwin > 0 && nrec > 0)
+    SEDEF_KERNEL(c, "k_windows",
+                 k_windows<<<(int)((nwin + 255) / 256), 256, 0, st>>>(
+                     L.qrec, nrec, (const int64_t*)L.d_up, 1, (const int64_t*)L.d_up + 2, nwin,
+                     s->D.step, s->D.span, L.wi, L.wqa, L.wqb, L.wseq, nullptr));
+  SEDEF_CUDA(cudaStreamSynchronize(st));
+  L.len = len;
+  L.nrec = nrec;
+  L.nwin = (nrec > 0) ? nwin : 0;
+  L.a.qrec = L.qrec;
+  L.a.nwin = L.nwin;
+  return SEDEF_OK;
+}
+
+}  // namespace
+}  // namespace sedef
+
+extern "C" {
+
+using sedef::Server;
+
+int sedef_server_destroy(sedef_server* srv) {
+  using namespace sedef;
+  Server* s = (Server*)srv;
+  if (!s) return SEDEF_OK;
+  cudaSetDevice(s->device);
+  if (s->ctl) {
+    __atomic_store_n(&s->ctl->stop, 1, __ATOMIC_RELEASE);
+    if (s->kern_launched) cudaEventSynchronize(s->kern_done);
+  }
+  if (s->s_prep) cudaStreamSynchronize(s->s_prep);
+  if (s->s_fin) cudaStreamSynchronize(s->s_fin);
+  if (s->c_prep) sedef_destroy(s->c_prep);
+  if (s->c_fin) sedef_destroy(s->c_fin);
+  for (void* p : s->dev_allocs) cudaFree(p);
+  if (s->ctl) cudaFreeHost(s->ctl);
+  if (s->ring) cudaFreeHost(s->ring);
+  if (s->kern_done) cudaEventDestroy(s->kern_done);
+  if (s->s_prep) cudaStreamDestroy(s->s_prep);
+  if (s->s_kern) cudaStreamDestroy(s->s_kern);
+  if (s->s_fin) cudaStreamDestroy(s->s_fin);
+  delete s;
+  return SEDEF_OK;
+}
+
+int sedef_server_create(sedef_ctx* ctx, const uint64_t* d_trec, const uint64_t* d_tsorted,
+                        const uint32_t* d_toff, int64_t nt, const int64_t* h_toff, int32_t ntseq,
+                        const sedef_params* p, int32_t slots, int64_t slot_bases,
+                        double idle_timeout_s, sedef_server** out) {
+  using namespace sedef;
+  if (!ctx || !out || !p) return fail(SEDEF_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  Derived D;
+  SEDEF_TRY(derive(p, &D));
+  if (D.self_mode != 0) return fail(SEDEF_ERR_INVALID, "sedef_server_create: self_mode must be 0");
+  if (slots < 1 || slots > kServeMaxSlots)
+    return fail(SEDEF_ERR_INVALID, "sedef_server_create: slots must be in [1, 64]");
+  if (slot_bases < D.n || slot_bases >= (int64_t(1) << 31))
+    return fail(SEDEF_ERR_INVALID, "sedef_server_create: slot_bases must be in [n, 2^31)");
+  if (!(idle_timeout_s > 0 && idle_timeout_s < 3600))
+    return fail(SEDEF_ERR_INVALID, "sedef_server_create: idle timeout must be in (0, 3600) s");
+  if (ntseq < 1 || !h_toff || h_toff[0] != 0 || nt < 1 || !d_trec || !d_tsorted || !d_toff)
+    return fail(SEDEF_ERR_INVALID, "sedef_server_create: bad target index");
+  for (int u = 0; u < ntseq; ++u)
+    if (h_toff[u + 1] < h_toff[u]) return fail(SEDEF_ERR_INVALID, "target offsets decrease");
+  SEDEF_CUDA(cudaSetDevice(ctx_device(ctx)));
+  Server* s = new Server();
+  auto bail = [&](int st) {
+    const std::string msg = sedef_last_error();
+    sedef_server_destroy((sedef_server*)s);
+    set_error(msg);
+    return st;
+  };
+  s->device = ctx_device(ctx);
+  s->nslots = slots;
+  s->slot_bases = slot_bases;
+  s->D = D;
+  s->P = *p;
+  s->idle_s = idle_timeout_s;
+  s->trec = d_trec;
+  s->tsorted = d_tsorted;
+  s->toff = d_toff;
+  s->nt = nt;
+  s->h_toff.assign(h_toff, h_toff + ntseq + 1);
+  s->mtab.resize(kMaxWindowRecs + 1);
+  mtable(p, s->mtab.data(), kMaxWindowRecs, nullptr);
+  if (cudaStreamCreateWithFlags(&s->s_prep, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->s_kern, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->s_fin, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->kern_done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(SEDEF_ERR_CUDA, "sedef_server_create: stream or event creation failed"));
+  }
+  int st = sedef_create(s->device, s->s_prep, &s->c_prep);
+  if (st == SEDEF_OK) st = sedef_create(s->device, s->s_fin, &s->c_fin);
+  if (st != SEDEF_OK) return bail(st);
+  ctx_set_filter_variant(s->c_fin, ctx_filter_variant(ctx));
+  const size_t up = (size_t)(ntseq + 1) * 8 + (size_t)(kMaxWindowRecs + 1) * 4;
+  if ((st = server_alloc(s, (void**)&s->d_shared, up)) != SEDEF_OK) return bail(st);
+  if (cudaMemcpy(s->d_shared, h_toff, (size_t)(ntseq + 1) * 8, cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(s->d_shared + (ntseq + 1) * 8, s->mtab.data(), (size_t)(kMaxWindowRecs + 1) * 4,
+                 cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(fail(SEDEF_ERR_CUDA, "sedef_server_create: upload failed"));
+  s->slots.resize(slots);
+  const int64_t win_cap = (slot_bases - D.n) / D.step + 1;
+  s->ring_cap = (unsigned long long)(win_cap * slots);
+  if (cudaHostAlloc((void**)&s->ctl, sizeof(ServeCtl), cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostAlloc((void**)&s->ring, s->ring_cap * sizeof(ServeItem), cudaHostAllocMapped) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(SEDEF_ERR_OOM, "sedef_server_create: mapped host allocation failed"));
+  }
+  std::memset(s->ctl, 0, sizeof(ServeCtl));
+  if (cudaHostGetDevicePointer((void**)&s->d_ctl, s->ctl, 0) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&s->d_ring, s->ring, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(SEDEF_ERR_CUDA, "sedef_server_create: no device view of mapped memory"));
+  }
+  if ((st = server_alloc(s, (void**)&s->d_head, 8)) != SEDEF_OK) return bail(st);
+  if ((st = server_alloc(s, (void**)&s->d_slots, sizeof(SlotDev) * slots)) != SEDEF_OK)
+    return bail(st);
+  if (cudaMemset(s->d_head, 0, 8) != cudaSuccess)
+    return bail(fail(SEDEF_ERR_CUDA, "sedef_server_create: memset failed"));
+  std::vector<SlotDev> sdev(slots);
+  for (int k = 0; k < slots; ++k) {
+    Server::Slot& L = s->slots[k];
+    L.rec_cap = slot_bases;
+    L.win_cap = win_cap;
+    L.run_cap = win_cap * 64 + 4096;
+    void* v = nullptr;
+#define SALLOC(field, type, bytes)                                   \
+  do {                                                               \
+    if ((st = server_alloc(s, &v, (size_t)(bytes))) != SEDEF_OK) return bail(st); \
+    L.field = (type)v;                                               \
+  } while (0)
+    SALLOC(seq, uint8_t*, slot_bases);
+    SALLOC(packed, uint32_t*, ((slot_bases + 15) / 16) * 4);
+    SALLOC(mask, uint32_t*, ((slot_bases + 31) / 32) * 4);
+    SALLOC(nbits, uint32_t*, ((slot_bases + 31) / 32) * 4);
+    SALLOC(qrec, uint64_t*, L.rec_cap * 8);
+    SALLOC(wi, uint32_t*, win_cap * 4 * 5);
+    SALLOC(raw, sedef_run_t*, L.run_cap * (int64_t)sizeof(sedef_run_t));
+    SALLOC(counters, unsigned long long*, 256 + 64 + 64);
+#undef SALLOC
+    L.wqa = L.wi + win_cap;
+    L.wqb = L.wqa + win_cap;
+    L.ov = L.wqb + win_cap;
+    L.wseq = (int32_t*)(L.ov + win_cap);
+    L.done = (unsigned int*)((char*)L.counters + 256);
+    L.d_up = (char*)L.counters + 256 + 64;
+    FArgs& a = L.a;
+    std::memset(&a, 0, sizeof(a));
+    a.qrec = L.qrec;
+    a.trec = d_trec;
+    a.tsorted = d_tsorted;
+    a.toff = d_toff;
+    a.tseq = (const int64_t*)s->d_shared;
+    a.qseq = (const int64_t*)L.d_up;
+    a.mtab = (const int32_t*)(s->d_shared + (ntseq + 1) * 8);
+    a.win_i = L.wi;
+    a.win_qa = L.wqa;
+    a.win_qb = L.wqb;
+    a.win_seq = L.wseq;
+    a.ntseq = ntseq;
+    a.nqseq = 1;
+    a.ttotal = h_toff[ntseq];
+    a.k = D.k;
+    a.n = D.n;
+    a.span = D.span;
+    a.max_occ = D.max_occ;
+    a.self_mode = 0;
+    a.overlap = D.overlap;
+    a.runs = L.raw;
+    a.nruns = L.counters;
+    a.run_cap = L.run_cap;
+    a.ov_list = L.ov;
+    a.nov = (unsigned int*)(L.counters + 1);
+    a.next_window = (unsigned int*)(L.counters + 2);
+    a.stats = L.counters + 4;
+    sdev[k].a = a;
+    sdev[k].done = L.done;
+  }
+  if (cudaMemcpy(s->d_slots, sdev.data(), sizeof(SlotDev) * slots, cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return bail(fail(SEDEF_ERR_CUDA, "sedef_server_create: slot table upload failed"));
+  *out = (sedef_server*)s;
+  return SEDEF_OK;
+}
+
+int sedef_server_submit(sedef_server* srv, const uint8_t* h_query, int64_t len, int32_t* slot_out) {
+  using namespace sedef;
+  Server* s = (Server*)srv;
+  if (!s || !slot_out || (len > 0 && !h_query)) return fail(SEDEF_ERR_INVALID, "NULL argument");
+  *slot_out = -1;
+  if (len < 0 || len > s->slot_bases)
+    return fail(SEDEF_ERR_UNSUPPORTED, "sedef_server_submit: query longer than a slot holds");
+  SEDEF_CUDA(cudaSetDevice(s->device));
+  int k = -1;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    for (int x = 0; x < s->nslots && k < 0; ++x)
+      if (s->slots[x].state == 0) k = x;
+    if (k < 0) return fail(SEDEF_ERR_CAPACITY, "sedef_server_submit: no free slot");
+    s->slots[k].state = 1;
+  }
+  Server::Slot& L = s->slots[k];
+  const int st = server_prepare(s, L, h_query, len);
+  std::lock_guard<std::mutex> g(s->mu);
+  if (st != SEDEF_OK) {
+    L.state = 0;
+    return st;
+  }
+  L.epoch += 1;
+  *slot_out = k;
+  if (L.nwin == 0) {  // nothing to filter: the slot is done at once
+    L.state = 3;
+    return SEDEF_OK;
+  }
+  __atomic_store_n(&s->ctl->nwin[k], (long long)L.nwin, __ATOMIC_RELAXED);
+  __atomic_store_n(&s->ctl->epoch[k], L.epoch, __ATOMIC_RELAXED);
+  for (int64_t w = 0; w < L.nwin; ++w) {
+    ServeItem& it = s->ring[(s->tail + (unsigned long long)w) % s->ring_cap];
+    it.slot = (uint32_t)k;
+    it.window = (uint32_t)w;
+  }
+  s->tail += (unsigned long long)L.nwin;
+  L.state = 2;
+  __atomic_store_n(&s->ctl->tail, s->tail, __ATOMIC_RELEASE);  // items before the tail
+  return server_kick(s);
+}
+
+int sedef_server_poll(sedef_server* srv, double wait_s, int32_t* slot_out) {
+  using namespace sedef;
+  Server* s = (Server*)srv;
+  if (!s || !slot_out) return fail(SEDEF_ERR_INVALID, "NULL argument");
+  *slot_out = -1;
+  SEDEF_CUDA(cudaSetDevice(s->device));
+  const auto t0 = std::chrono::steady_clock::now();
+  while (true) {
+    {
+      std::lock_guard<std::mutex> g(s->mu);
+      bool queued = false;
+      for (int k = 0; k < s->nslots; ++k) {
+        Server::Slot& L = s->slots[k];
+        if (L.state == 2 &&
+            __atomic_load_n(&s->ctl->done_epoch[k], __ATOMIC_ACQUIRE) == L.epoch)
+          L.state = 3;
+        if (L.state == 3) {
+          L.state = 4;  // handed to the caller for sedef_server_finish
+          *slot_out = k;
+          return SEDEF_OK;
+        }
+        queued |= L.state == 2;
+      }
+      // items left behind by a kernel that went idle are served by a new one
+      if (queued) SEDEF_TRY(server_kick(s));
+    }
+    const double el =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el >= wait_s) return SEDEF_OK;
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+int sedef_server_finish(sedef_server* srv, int32_t slot, sedef_cand_t* h_cands, int64_t cap,
+                        int64_t* h_ncands) {
+  using namespace sedef;
+  Server* s = (Server*)srv;
+  if (!s || !h_ncands || slot < 0 || slot >= (s ? s->nslots : 0))
+    return fail(SEDEF_ERR_INVALID, "bad argument");
+  *h_ncands = 0;
+  Server::Slot& L = s->slots[slot];
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    if (L.state != 4) return fail(SEDEF_ERR_INVALID, "sedef_server_finish: slot not polled");
+  }
+  SEDEF_CUDA(cudaSetDevice(s->device));
+  sedef_ctx* c = s->c_fin;
+  cudaStream_t st = s->s_fin;
+  ctx_pool_reset(c);
+  auto release = [&](int status) {
+    std::lock_guard<std::mutex> g(s->mu);
+    L.state = 0;
+    return status;
+  };
+  const int64_t qoff[2] = {0, L.len};
+  int64_t nc = 0;
+  if (L.nwin > 0) {
+    unsigned long long* h_cnt = (unsigned long long*)ctx_host(c, 64);
+    if (!h_cnt) return release(SEDEF_ERR_OOM);
+    if (cudaMemcpyAsync(h_cnt, L.counters, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return release(fail(SEDEF_ERR_CUDA, "sedef_server_finish: counter copy failed"));
+    const int64_t nov = (int64_t)(h_cnt[1] & 0xFFFFFFFFull);
+    int64_t slow = 0;
+    int status = SEDEF_OK;
+    if (nov > 0) status = global_path_eager(c, L.a, nov, L.counters, &slow);
+    if (status == SEDEF_OK &&
+        (cudaMemcpyAsync(h_cnt, L.counters, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+         cudaStreamSynchronize(st) != cudaSuccess))
+      status = fail(SEDEF_ERR_CUDA, "sedef_server_finish: counter copy failed");
+    if (status != SEDEF_OK) return release(status);
+    const int64_t total = (int64_t)h_cnt[0];
+    sedef_run_t* runs = nullptr;
+    if (total > L.run_cap) {
+      // more runs than the slot holds: the whole filter again, sized exactly
+      runs = (sedef_run_t*)ctx_alloc(c, (size_t)total * sizeof(sedef_run_t));
+      if (!runs) return release(SEDEF_ERR_OOM);
+      int64_t got = 0;
+      status = run_filter(c, L.qrec, L.nrec, qoff, 1, s->trec, s->tsorted, s->toff, s->nt,
+                          s->h_toff.data(), (int)s->h_toff.size() - 1, s->D, s->mtab.data(), runs,
+                          total, &got, 0);
+      if (status != SEDEF_OK) return release(status);
+    } else if (total > 0) {
+      runs = (sedef_run_t*)ctx_alloc(c, (size_t)total * sizeof(sedef_run_t));
+      if (!runs) return release(SEDEF_ERR_OOM);
+      {
+        StageScope stage(c, "runsort");
+        status = order_and_refine(c, L.a, s->D, 1, (const int64_t*)L.d_up + 2, L.nwin, L.wqa, L.wqb,
+                                  L.qrec, L.nrec, s->trec, s->nt, s->toff, L.counters, L.raw, total,
+                                  runs, nullptr, nullptr);
+      }
+      if (status != SEDEF_OK) return release(status);
+    }
+    if (total > 0) {
+      sedef_chain_t* chains = (sedef_chain_t*)ctx_alloc(c, (size_t)total * sizeof(sedef_chain_t));
+      if (!chains) return release(SEDEF_ERR_OOM);
+      int64_t nch = 0;
+      {
+        StageScope stage(c, "chain");
+        status = run_chain(c, runs, total, L.qrec, L.nrec, qoff, 1, s->tsorted, s->nt, s->toff,
+                           s->h_toff.data(), (int)s->h_toff.size() - 1, s->D, s->mtab.data(),
+                           chains, total, &nch);
+      }
+      if (status != SEDEF_OK) return release(status);
+      if (nch > 0) {
+        sedef_cand_t* cands = (sedef_cand_t*)ctx_alloc(c, (size_t)nch * sizeof(sedef_cand_t));
+        if (!cands) return release(SEDEF_ERR_OOM);
+        {
+          StageScope stage(c, "merge");
+          status = run_merge(c, chains, nch, qoff, 1, s->h_toff.data(),
+                             (int)s->h_toff.size() - 1, s->D, cands, nch, &nc);
+        }
+        if (status != SEDEF_OK) return release(status);
+        *h_ncands = nc;
+        if (nc > cap) return release(fail(SEDEF_ERR_CAPACITY, "sedef_server_finish: buffer too small"));
+        if (nc > 0 &&
+            cudaMemcpyAsync(h_cands, cands, (size_t)nc * sizeof(sedef_cand_t),
+                            cudaMemcpyDeviceToHost, st) != cudaSuccess)
+          return release(fail(SEDEF_ERR_CUDA, "sedef_server_finish: copy failed"));
+      }
+    }
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess)
+    return release(fail(SEDEF_ERR_CUDA, "sedef_server_finish: stream failed"));
+  *h_ncands = nc;
+  return release(SEDEF_OK);
+}
+
+int sedef_server_status(sedef_server* srv, int32_t* running, int32_t* timed_out) {
+  using namespace sedef;
+  Server* s = (Server*)srv;
+  if (!s) return fail(SEDEF_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::mutex> g(s->mu);
+  int run = 0;
+  if (s->kern_launched) {
+    const cudaError_t q = cudaEventQuery(s->kern_done);
+    if (q == cudaErrorNotReady) run = 1;
+    else if (q != cudaSuccess) return cuda_fail(q, "server: kernel event");
+  }
+  const int tmo = __atomic_load_n(&s->ctl->status, __ATOMIC_ACQUIRE) == SEDEF_ERR_TIMEOUT;
+  if (running) *running = run;
+  if (timed_out) *timed_out = tmo;
+  return (!run && tmo) ? SEDEF_ERR_TIMEOUT : SEDEF_OK;
+}
+
+}  // extern "C"

@@ -117,6 +117,7 @@ extern "C" int sedef_qgram(sedef_ctx* ctx, const uint32_t* d_packed, const uint3
   if (!d_packed || !d_nbits || !d_runs || !d_shared || !d_pass)
     return fail(SEDEF_ERR_INVALID, "sedef_qgram: NULL buffer");
   SEDEF_CUDA(cudaSetDevice(ctx_device(ctx)));
+  StageScope stage(ctx, "qgram");
   cudaStream_t st = ctx_stream(ctx);
   // least integer >= B - 1e-9 (Section 3.2 bound), in double
   const double B = (double)D.n * (1.0 - p->delta_g - (double)q * p->delta_m) -

@@ -304,12 +304,17 @@ def chromosome_100mbp(seed: int = 0x5EDEF002, length: int = 100_000_000,
 
 
 def batch_genomes(seed: int = 0x5EDEF003, count: int = 200, len_lo: int = 1_000_000,
-                  len_hi: int = 20_000_000, sd_lo: int = 50, sd_hi: int = 500) -> list:
+                  len_hi: int = 20_000_000, sd_lo: int = 50, sd_hi: int = 500,
+                  max_genomes: int | None = None) -> list:
     """Independent genomes of log-uniform size, 41% GC, 30% soft-masked
-    repeats, sd_lo..sd_hi planted duplications of 1-50 kbp at 75-99%."""
+    repeats, sd_lo..sd_hi planted duplications of 1-50 kbp at 75-99%.
+    With max_genomes, only the first max_genomes of the same batch (the
+    genomes are drawn one after another, so they are identical)."""
     rng = np.random.default_rng(seed)
     out = []
     sizes = log_uniform_int(rng, len_lo, len_hi + 1, size=count)
+    if max_genomes is not None:
+        sizes = sizes[:max_genomes]
     for g, L in enumerate(sizes):
         L = int(L)
         seq = random_bases(rng, L, 0.41)
