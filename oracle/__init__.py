@@ -92,6 +92,12 @@ def _load():
             lib.orc_qgram_shared.argtypes = [vp, i64, i64, i64, i32, i32]
             lib.orc_qgram.restype = vp
             lib.orc_qgram.argtypes = [vp, vp, i64, i64, vp, i32, ctypes.c_double]
+            lib.orc_mems.restype = vp
+            lib.orc_mems.argtypes = [vp, i64, vp, i64, i64]
+            lib.orc_chain_tiers.restype = vp
+            lib.orc_chain_tiers.argtypes = [vp, i64, i64, i64, i64, i64]
+            lib.orc_chain2.restype = vp
+            lib.orc_chain2.argtypes = [vp, vp, i64, i64, i64, i64, i64, i64, i64, i64, i32]
             lib.orc_extend.restype = vp
             lib.orc_extend.argtypes = [vp, i64, i64, vp, i64, vp, i32, vp, i64, vp, i32, vp, i64,
                                        i32]
@@ -279,6 +285,41 @@ def extend(runs, qrecs_all, qoff, trecs_all, toff, p: dict, max_len: int = MAX_S
     h = lib.orc_extend(_ptr(runs), len(runs), runs.shape[1], _ptr(qrecs_all), len(qrecs_all),
                        _ptr(qoff), len(qoff) - 1, _ptr(trecs_all), len(trecs_all), _ptr(toff),
                        len(toff) - 1, _ptr(_par_array(p)), int(max_len), int(threads))
+    return _table(lib, h)
+
+
+# Section 3.3: exact seeds of at least 11 bases; initial chains with gaps of
+# at most l * delta_G = 100 (l = 1,000); final chains with gaps of at most
+# 10,000 and an affine penalty (readings: open 25, one per 50 gap bases);
+# an SD spans at least 1,000 bases.
+CHAIN2 = dict(k2=11, g1=100, g2=10_000, gap_open=25, gap_div=50, min_len=1000)
+CHAIN2_COLS = ["region", "o", "q0", "q1", "t0", "t1", "score", "seeds", "parts"]
+
+
+def mems(x: bytes, y: bytes, k2: int = 11) -> np.ndarray:
+    """Maximal exact ACGT matches of at least k2 bases: rows (x, y, L)."""
+    lib = _load()
+    bx, by = np.frombuffer(x, dtype=np.uint8), np.frombuffer(y, dtype=np.uint8)
+    return _table(lib, lib.orc_mems(_ptr(bx), len(bx), _ptr(by), len(by), k2))
+
+
+def chain_tiers(seeds, g1=100, g2=10_000, gap_open=25, gap_div=50) -> np.ndarray:
+    """Both chaining tiers on explicit seeds (x, y, L): final chains
+    (x0, x1, y0, y1, score, seeds, parts) in extraction order."""
+    lib = _load()
+    seeds = _c(seeds, np.int64).reshape(-1, 3)
+    return _table(lib, lib.orc_chain_tiers(_ptr(seeds), len(seeds), g1, g2, gap_open, gap_div))
+
+
+def chain2(seq, regions, c: dict = None, threads: int = 1) -> np.ndarray:
+    """f2 (Section 3.3): the final chains (SDs) inside each potential SD
+    region (rows of `extend`); see CHAIN2_COLS."""
+    lib = _load()
+    c = dict(CHAIN2, **(c or {}))
+    seq = _c(seq, np.uint8)
+    regions = _c(regions, np.int64).reshape(-1, len(EXTEND_COLS))
+    h = lib.orc_chain2(_ptr(seq), _ptr(regions), len(regions), regions.shape[1], c["k2"], c["g1"],
+                       c["g2"], c["gap_open"], c["gap_div"], c["min_len"], int(threads))
     return _table(lib, h)
 
 

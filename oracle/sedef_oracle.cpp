@@ -24,6 +24,8 @@
 //   tau       Section 3.1 closed form tau >= (1-dG)/(1+dG) / (2 e^{k dM} - 1)
 //   extend    Section 3.2 (seeds grown into potential SD regions while the
 //             winnowed MinHash estimate stays >= tau; all k-mers)
+//   chain2    Section 3.3 (two-tier local chaining of exact seeds of at
+//             least 11 bases inside the potential SD regions)
 //
 // Readings where the paper is silent are listed in the design notes; the code
 // below states each one where it is used.
@@ -985,6 +987,240 @@ void* orc_extend(const int64_t* runs, int64_t nruns, int64_t run_cols, const int
   Table* T = new Table();
   T->ncols = 9;
   for (auto& row : out) T->v.insert(T->v.end(), row.begin(), row.end());
+  return T;
+}
+
+}  // extern "C"
+
+// ---- f2 two-tier local chaining inside potential SD regions (Section 3.3) --
+// For every region row (i, o, j*, qa, qb, ta, tb, ...) the query is
+// X = G[qa, qb) and the target Y = G[ta, tb) (reverse-complemented when
+// o = 1), both read case-insensitively.
+//   Seeds: maximal exact matches (x, y, L) of at least k2 bases of A, C, G,
+//   T between X and Y (Section 3.3: matching seeds of size 11 and higher).
+//   Initial chains: a seed b may follow a if it starts later on both axes
+//   and the gaps from a's end to b's start are at most g1 on both axes (the
+//   maximum gap l * delta_G with l the 1,000 bp SD length; a gap may be
+//   negative where an indel makes the seeds overlap); the link adds the
+//   bases of b that are new on both axes, gain = min(L_b, end_b - end_a on
+//   x, end_b - end_a on y), and must add at least one.  f(b) = the larger of
+//   L_b and the best f(a) + gain (ties: the later seed in (x, y) order).
+//   Chains are taken greedily: the seed of largest f (then the earlier seed)
+//   that no chain holds yet, and its predecessors back to the first one a
+//   chain already holds; score = L of the first seed plus the gains.
+//   Final chains: initial chains chained again with gaps of at most g2
+//   (10,000 bp) on both axes and an affine penalty go + g / gdiv for a gap
+//   of g = the larger of the two gaps (Section 3.3 leaves the penalty's
+//   values open); F(d) = S(d) + max(0, max F(c) - pen(c, d)), and the same
+//   greedy extraction (score = the summed initial-chain scores less the
+//   penalties of the links taken).  A final chain spanning at least min_len
+//   bases on both axes is an SD (l >= 1,000).
+// Rows (region index, o, q0, q1, t0, t1, score, seeds, initial chains) in
+// genome coordinates, sorted by (region, q0, q1, t0, t1, score).
+namespace {
+
+struct Mem {
+  int64_t x, y, L;
+};
+
+std::string region_text(const uint8_t* seq, int64_t a, int64_t b, bool revcomp) {
+  return upper_window(seq, a, b - a, revcomp);
+}
+
+bool acgt(char c) { return c == 'A' || c == 'C' || c == 'G' || c == 'T'; }
+
+// Maximal exact matches of at least k2 ACGT bases (x, y ascending).
+std::vector<Mem> find_mems(const std::string& X, const std::string& Y, int64_t k2) {
+  std::map<std::string, std::vector<int64_t>> at;
+  for (int64_t y = 0; y + k2 <= (int64_t)Y.size(); ++y) {
+    std::string w = Y.substr(y, k2);
+    bool ok = true;
+    for (char c : w) ok = ok && acgt(c);
+    if (ok) at[w].push_back(y);
+  }
+  std::vector<Mem> out;
+  for (int64_t x = 0; x + k2 <= (int64_t)X.size(); ++x) {
+    auto it = at.find(X.substr(x, k2));
+    if (it == at.end()) continue;
+    for (int64_t y : it->second) {
+      // left-maximal: the bases before do not extend the match
+      if (x > 0 && y > 0 && X[x - 1] == Y[y - 1] && acgt(X[x - 1])) continue;
+      int64_t L = k2;
+      while (x + L < (int64_t)X.size() && y + L < (int64_t)Y.size() && X[x + L] == Y[y + L] &&
+             acgt(X[x + L]))
+        ++L;
+      out.push_back({x, y, L});
+    }
+  }
+  std::sort(out.begin(), out.end(), [](const Mem& a, const Mem& b) {
+    return std::tie(a.x, a.y) < std::tie(b.x, b.y);
+  });
+  return out;
+}
+
+struct Box {
+  int64_t x0, x1, y0, y1, score, seeds, parts;
+};
+
+// Greedy extraction of disjoint chains from a DP (f, pred over items in
+// their sort order): repeatedly the item of largest f (then smallest index)
+// not yet taken, with its predecessors back to the first one already taken.
+std::vector<std::vector<int64_t>> extract_chains(const std::vector<int64_t>& f,
+                                                 const std::vector<int64_t>& pred) {
+  const int64_t A = (int64_t)f.size();
+  std::vector<int64_t> order(A);
+  for (int64_t a = 0; a < A; ++a) order[a] = a;
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    return f[a] != f[b] ? f[a] > f[b] : a < b;
+  });
+  std::vector<char> used(A, 0);
+  std::vector<std::vector<int64_t>> chains;
+  for (int64_t b : order) {
+    if (used[b]) continue;
+    std::vector<int64_t> path;
+    for (int64_t c = b; c >= 0 && !used[c]; c = pred[c]) {
+      used[c] = 1;
+      path.push_back(c);
+    }
+    std::reverse(path.begin(), path.end());
+    chains.push_back(path);
+  }
+  return chains;
+}
+
+std::vector<Box> chain_two_tiers(const std::vector<Mem>& mems, int64_t g1, int64_t g2,
+                                 int64_t gap_open, int64_t gap_div) {
+  // tier 1 over the seeds
+  const int64_t A = (int64_t)mems.size();
+  auto gain = [&](int64_t a, int64_t b) -> int64_t {  // <= 0: b cannot follow a
+    const Mem &P = mems[a], &Q = mems[b];
+    if (P.x >= Q.x || P.y >= Q.y) return 0;
+    if (Q.x - (P.x + P.L) > g1 || Q.y - (P.y + P.L) > g1) return 0;
+    return std::min(Q.L, std::min(Q.x + Q.L - (P.x + P.L), Q.y + Q.L - (P.y + P.L)));
+  };
+  std::vector<int64_t> f(A), pred(A, -1);
+  for (int64_t b = 0; b < A; ++b) {
+    f[b] = mems[b].L;
+    for (int64_t a = 0; a < b; ++a) {
+      const int64_t g = gain(a, b);
+      if (g <= 0) continue;
+      const int64_t v = f[a] + g;
+      if (v > f[b] || (v == f[b] && pred[b] >= 0)) {
+        f[b] = v;
+        pred[b] = a;
+      }
+    }
+  }
+  std::vector<Box> init;
+  for (auto& ch : extract_chains(f, pred)) {
+    Box B{mems[ch.front()].x, 0, mems[ch.front()].y, 0, mems[ch.front()].L, (int64_t)ch.size(), 1};
+    for (size_t u = 0; u < ch.size(); ++u) {
+      B.x1 = std::max(B.x1, mems[ch[u]].x + mems[ch[u]].L);
+      B.y1 = std::max(B.y1, mems[ch[u]].y + mems[ch[u]].L);
+      if (u > 0) B.score += gain(ch[u - 1], ch[u]);
+    }
+    init.push_back(B);
+  }
+  std::sort(init.begin(), init.end(), [](const Box& a, const Box& b) {
+    return std::tie(a.x0, a.y0, a.x1, a.y1, a.score) < std::tie(b.x0, b.y0, b.x1, b.y1, b.score);
+  });
+  // tier 2 over the initial chains (affine gap penalty)
+  const int64_t C = (int64_t)init.size();
+  auto pen = [&](const Box& c, const Box& d, int64_t* ok) {
+    const int64_t gq = d.x0 - c.x1, gt = d.y0 - c.y1;
+    *ok = gq >= 0 && gt >= 0 && gq <= g2 && gt <= g2;
+    return gap_open + std::max(gq, gt) / gap_div;
+  };
+  std::vector<int64_t> F(C), P(C, -1);
+  for (int64_t d = 0; d < C; ++d) {
+    int64_t best = 0, arg = -1;
+    for (int64_t c = 0; c < d; ++c) {
+      int64_t ok = 0;
+      const int64_t v = F[c] - pen(init[c], init[d], &ok);
+      if (!ok) continue;
+      if (v > best || (v == best && arg >= 0)) {
+        best = v;
+        arg = c;
+      }
+    }
+    F[d] = init[d].score + best;
+    P[d] = arg;
+  }
+  std::vector<Box> fin;
+  for (auto& ch : extract_chains(F, P)) {
+    const Box& a = init[ch.front()];
+    const Box& z = init[ch.back()];
+    Box B{a.x0, z.x1, a.y0, z.y1, 0, 0, (int64_t)ch.size()};
+    for (size_t u = 0; u < ch.size(); ++u) {
+      B.score += init[ch[u]].score;
+      B.seeds += init[ch[u]].seeds;
+      if (u > 0) {
+        int64_t ok = 0;
+        B.score -= pen(init[ch[u - 1]], init[ch[u]], &ok);
+      }
+    }
+    fin.push_back(B);
+  }
+  return fin;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Seeds of one pair of substrings (pins): rows (x, y, L).
+void* orc_mems(const uint8_t* x, int64_t nx, const uint8_t* y, int64_t ny, int64_t k2) {
+  std::string X((const char*)x, nx), Y((const char*)y, ny);
+  Table* T = new Table();
+  T->ncols = 3;
+  for (auto& m : find_mems(X, Y, k2)) T->row({m.x, m.y, m.L});
+  return T;
+}
+
+// Both tiers on explicit seed rows (x, y, L) (pins): final chain rows
+// (x0, x1, y0, y1, score, seeds, parts) in extraction order.
+void* orc_chain_tiers(const int64_t* seeds, int64_t A, int64_t g1, int64_t g2, int64_t gap_open,
+                      int64_t gap_div) {
+  std::vector<Mem> m(A);
+  for (int64_t a = 0; a < A; ++a) m[a] = {seeds[3 * a], seeds[3 * a + 1], seeds[3 * a + 2]};
+  std::sort(m.begin(), m.end(),
+            [](const Mem& a, const Mem& b) { return std::tie(a.x, a.y) < std::tie(b.x, b.y); });
+  Table* T = new Table();
+  T->ncols = 7;
+  for (auto& b : chain_two_tiers(m, g1, g2, gap_open, gap_div))
+    T->row({b.x0, b.x1, b.y0, b.y1, b.score, b.seeds, b.parts});
+  return T;
+}
+
+void* orc_chain2(const uint8_t* seq, const int64_t* regions, int64_t nreg, int64_t reg_cols,
+                 int64_t k2, int64_t g1, int64_t g2, int64_t gap_open, int64_t gap_div,
+                 int64_t min_len, int nthreads) {
+  std::vector<std::vector<std::vector<int64_t>>> out(nreg);
+  auto one = [&](int64_t r) {
+    const int64_t* R = regions + r * reg_cols;
+    const int64_t o = R[1], qa = R[3], qb = R[4], ta = R[5], tb = R[6];
+    const std::string X = region_text(seq, qa, qb, false);
+    const std::string Y = region_text(seq, ta, tb, o != 0);
+    for (auto& b : chain_two_tiers(find_mems(X, Y, k2), g1, g2, gap_open, gap_div)) {
+      if (b.x1 - b.x0 < min_len || b.y1 - b.y0 < min_len) continue;
+      const int64_t t0 = o ? tb - b.y1 : ta + b.y0, t1 = o ? tb - b.y0 : ta + b.y1;
+      out[r].push_back({r, o, qa + b.x0, qa + b.x1, t0, t1, b.score, b.seeds, b.parts});
+    }
+    std::sort(out[r].begin(), out[r].end());
+  };
+  if (nthreads < 1) nthreads = 1;
+  std::atomic<int64_t> next(0);
+  auto work = [&]() {
+    for (int64_t r; (r = next.fetch_add(1)) < nreg;) one(r);
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nthreads; ++t) th.emplace_back(work);
+  work();
+  for (auto& t : th) t.join();
+  Table* T = new Table();
+  T->ncols = 9;
+  for (auto& v : out)
+    for (auto& row : v) T->v.insert(T->v.end(), row.begin(), row.end());
   return T;
 }
 

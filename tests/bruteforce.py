@@ -361,3 +361,120 @@ def extend_rows(runs, qrecs, qoff, trecs, toff, p, tau, max_len, slip=None):
                     qa, qb, ta, tb, est, den = nqa, nqb, nta, ntb, e2, d2
         rows.append((i, o, js, qa, qb, ta, tb, est, den))
     return rows
+
+
+# ------------------------------------------------------- two-tier chains --
+
+_ACGT = set("ACGT")
+
+
+def mems(X: str, Y: str, k2: int):
+    """Maximal exact ACGT matches by scanning every diagonal."""
+    out = []
+    for d in range(-(len(X) - 1), len(Y)):
+        x, y = (0, d) if d >= 0 else (-d, 0)
+        run = 0
+        while x < len(X) and y < len(Y):
+            if X[x] == Y[y] and X[x] in _ACGT:
+                run += 1
+            else:
+                if run >= k2:
+                    out.append((x - run, y - run, run))
+                run = 0
+            x += 1
+            y += 1
+        if run >= k2:
+            out.append((x - run, y - run, run))
+    return sorted(out)
+
+
+def _best_ending(items, link):
+    """For every item b: the best score of a chain ending at b, by
+    enumerating every chain (link(a, b) -> added score, or None)."""
+    n = len(items)
+    best = [None] * n
+
+    def extend(path, score):
+        b = path[-1]
+        if best[b] is None or score > best[b]:
+            best[b] = score
+        for c in range(n):
+            g = link(b, c)
+            if g is not None:
+                extend(path + [c], score + g)
+
+    for a in range(n):
+        extend([a], items[a][-1])
+    return best
+
+
+def _take_chains(items, best, link):
+    """The greedy extraction: predecessors chosen from the enumerated best
+    scores (the later item among those that reach the best), then chains
+    taken by decreasing best score (earlier item on ties)."""
+    n = len(items)
+    pred = []
+    for b in range(n):
+        cand = [a for a in range(n) if link(a, b) is not None
+                and best[a] + link(a, b) == best[b] and best[b] > items[b][-1]]
+        pred.append(max(cand) if cand else -1)
+    order = sorted(range(n), key=lambda b: (-best[b], b))
+    used, chains = set(), []
+    for b in order:
+        if b in used:
+            continue
+        path = []
+        c = b
+        while c >= 0 and c not in used:
+            used.add(c)
+            path.append(c)
+            c = pred[c]
+        chains.append(path[::-1])
+    return chains
+
+
+def chain_tiers(seeds, g1, g2, gap_open, gap_div):
+    """Both tiers of the Section 3.3 chaining on explicit seeds (x, y, L),
+    with every best chain score found by enumerating chains; final chains
+    (x0, x1, y0, y1, score, seeds, parts) in extraction order."""
+    S = sorted(set(map(tuple, seeds)))
+
+    def gain(a, b):
+        P, Q = S[a], S[b]
+        if P[0] >= Q[0] or P[1] >= Q[1]:
+            return None
+        if Q[0] - (P[0] + P[2]) > g1 or Q[1] - (P[1] + P[2]) > g1:
+            return None
+        g = min(Q[2], Q[0] + Q[2] - (P[0] + P[2]), Q[1] + Q[2] - (P[1] + P[2]))
+        return g if g > 0 else None
+
+    best = _best_ending(S, gain)
+    init = []
+    for ch in _take_chains(S, best, gain):
+        score = S[ch[0]][2] + sum(gain(a, b) for a, b in zip(ch, ch[1:]))
+        init.append((S[ch[0]][0], max(S[c][0] + S[c][2] for c in ch), S[ch[0]][1],
+                     max(S[c][1] + S[c][2] for c in ch), len(ch), score))
+    init.sort(key=lambda b: (b[0], b[2], b[1], b[3], b[5]))
+
+    def pen(c, d):
+        C, D = init[c], init[d]
+        gq, gt = D[0] - C[1], D[2] - C[3]
+        if gq < 0 or gt < 0 or gq > g2 or gt > g2:
+            return None
+        return gap_open + max(gq, gt) // gap_div
+
+    def link2(c, d):
+        p = pen(c, d)
+        return None if p is None else init[d][5] - p
+
+    # a link only counts when it raises the score (F = S + max(0, ...))
+    best2 = _best_ending(init, lambda c, d: link2(c, d))
+    best2 = [max(init[d][5], b) for d, b in enumerate(best2)]
+    chains = _take_chains(init, best2, lambda c, d: (
+        link2(c, d) if link2(c, d) is not None and best2[c] + link2(c, d) > init[d][5] else None))
+    out = []
+    for ch in chains:
+        score = sum(init[c][5] for c in ch) - sum(pen(a, b) for a, b in zip(ch, ch[1:]))
+        out.append((init[ch[0]][0], init[ch[-1]][1], init[ch[0]][2], init[ch[-1]][3], score,
+                    sum(init[c][4] for c in ch), len(ch)))
+    return out

@@ -661,3 +661,82 @@ def test_extension_contains_planted_duplications():
         o = 1 if sd.reverse else 0
         assert any(row[1] == o and row[3] <= first[0] and row[4] >= first[1]
                    and row[5] <= second[0] and row[6] >= second[1] for row in ext.tolist()), sd
+
+
+# ------------------------------------------ f2 two-tier chaining (3.3) ----
+
+@pytest.mark.parametrize("seed", range(6))
+def test_seeds_are_maximal_exact_matches(seed):
+    """The seeds of Section 3.3 (exact matches of at least k2 bases), found
+    through a k-mer table, equal a scan of every diagonal."""
+    rng = np.random.default_rng(seed)
+    alpha = np.frombuffer(b"ACGTACGTACGTN", dtype=np.uint8)
+    X = alpha[rng.integers(0, len(alpha), 150)]
+    Y = alpha[rng.integers(0, len(alpha), 120)]
+    core = synth.random_bases(rng, 40)
+    X[20:60] = core
+    Y[50:90] = core                  # a shared stretch (with a mismatch below)
+    Y[70] = ord("A") if Y[70] != ord("A") else ord("C")
+    X[100:130] = X[10:40]            # a repeat inside X
+    k2 = 5 + seed % 3 * 3
+    got = [tuple(r) for r in oracle.mems(X.tobytes(), Y.tobytes(), k2).tolist()]
+    want = bf.mems(X.tobytes().decode(), Y.tobytes().decode(), k2)
+    assert got == want and len(got) > 0
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_chain_tiers_match_chain_enumeration(seed):
+    """Both chaining tiers (seeds into initial chains, initial chains into
+    final chains with the affine penalty) against the same rules with every
+    best score found by enumerating all chains."""
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(2, 10))
+    base = np.sort(rng.integers(0, 400, n))
+    seeds = np.stack([base, base + rng.integers(-30, 31, n) + 50, rng.integers(11, 40, n)], axis=1)
+    if seed % 5 == 0:  # seeds that overlap on one axis (indels)
+        seeds[1:, 1] = seeds[:-1, 1] + seeds[:-1, 2] - rng.integers(0, 5, n - 1)
+    g1, g2, go, gd = 25, 150, 6, 10
+    got = [tuple(r) for r in oracle.chain_tiers(seeds, g1, g2, go, gd).tolist()]
+    want = bf.chain_tiers([tuple(s) for s in seeds.tolist()], g1, g2, go, gd)
+    assert got == want
+
+
+def test_chain2_finds_the_planted_duplications():
+    """Section 3.3's purpose: inside the potential SD regions the final
+    chains recover each planted duplication (2-8 kbp, 90-99.5% identity,
+    small indels) as one chain whose ends lie within 50 bp of the mates'."""
+    g = synth.small_case(41, lengths=(400_000,), n_sd=8, sd_lo=2000, sd_hi=8000,
+                         id_lo=0.90, id_hi=0.995)
+    p = oracle.params()
+    r = oracle.selfsearch(g.seq, g.offsets, p, threads=8)
+    allk = oracle.sketch(g.seq, g.offsets, oracle.params(min_unmasked=0))
+    ext = oracle.extend(r["runs"], allk, g.offsets, allk, g.offsets, p, threads=8)
+    fin = oracle.chain2(g.seq, ext, threads=8)
+    assert len(g.planted) >= 6
+    for sd in g.planted:
+        a, b = (sd.src, sd.src + sd.length), (sd.dst, sd.dst + sd.copy_length)
+        first, second = (a, b) if a[0] < b[0] else (b, a)
+        o = 1 if sd.reverse else 0
+        assert any(row[1] == o and abs(row[2] - first[0]) <= 50 and abs(row[3] - first[1]) <= 50
+                   and abs(row[4] - second[0]) <= 50 and abs(row[5] - second[1]) <= 50
+                   for row in fin.tolist()), sd
+
+
+def test_chain2_exact_copy_is_one_chain():
+    """An exact copy inside its regions is one final chain covering the copy
+    (one seed, score = its length, a few chance bases at most beyond)."""
+    rng = np.random.default_rng(9)
+    L = 3000
+    core = synth.random_bases(rng, L)
+    seq = np.concatenate([synth.random_bases(rng, 700), core, synth.random_bases(rng, 900),
+                          synth.reverse_complement(core), synth.random_bases(rng, 500)])
+    s0, s1 = 700 + L + 900, 700 + L + 900 + L
+    for o, (ta, tb) in ((1, (s0 - 300, s1 + 200)),):
+        regions = np.array([[700, o, s0, 500, 700 + L + 400, ta, tb, 0, 0]], dtype=np.int64)
+        fin = oracle.chain2(seq, regions)
+        assert len(fin) == 1
+        _, oo, q0, q1, t0, t1, score, seeds, parts = fin[0].tolist()
+        assert oo == 1 and parts == 1 and seeds == 1
+        assert 690 <= q0 <= 700 and 700 + L <= q1 <= 700 + L + 10
+        assert s0 - 10 <= t0 <= s0 and s1 <= t1 <= s1 + 10
+        assert score == q1 - q0 == t1 - t0 >= L
