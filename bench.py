@@ -422,7 +422,7 @@ def run_workload(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     t0 = time.time()
-    W = make_workload(args.workload)
+    W = make_workload(args.workload, max_genomes=args.genomes)
     gen_s = time.time() - t0
     N = W.length
     p = binding.params(self_mode=W.self_mode)
@@ -440,7 +440,10 @@ def run_workload(args):
     # the filter's first-tier shape is autotuned once, then one pass stage by
     # stage keeps every intermediate for the accounting below (untimed)
     with torch.cuda.stream(stream):
-        out = ctx.selfsearch(d_seq, W.offsets, p, autotune=True)
+        if args.variant is None:
+            out = ctx.selfsearch(d_seq, W.offsets, p, autotune=True)
+        else:
+            ctx.sedef_filter_variant(args.variant)
         variant = ctx.sedef_filter_variant()[0]
         out = ctx.selfsearch(d_seq, W.offsets, p)
     fstats = ctx.sedef_filter_stats()
@@ -476,7 +479,7 @@ def run_workload(args):
 
     # ---- plain form of the batch: one pass per genome (self_mode 1)
     plain = None
-    if W.genomes is not None:
+    if W.genomes is not None and not args.no_plain:
         pp = binding.params(self_mode=1)
         views = [d_seq[int(W.offsets[g]):int(W.offsets[g + 1])] for g in range(len(W.genomes))]
         offs1 = [np.array([0, int(W.offsets[g + 1] - W.offsets[g])], dtype=np.int64)
@@ -655,6 +658,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-graph", action="store_true", help="skip the captured-graph measurement")
+    ap.add_argument("--no-plain", action="store_true", help="batch: skip the one-pass-per-genome form")
+    ap.add_argument("--genomes", type=int, default=None,
+                    help="batch: only the first N genomes of the batch (smaller runs, e.g. profiling)")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="the filter's first-tier shape instead of autotuning it")
     ap.add_argument("--trace", action="store_true", help="print the per-kernel table to stderr")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -154,6 +154,18 @@ typedef struct sedef_region_t {
   uint32_t est, den, o, reserved;
 } sedef_region_t;
 
+/*
+ * An SD found by the two-tier chaining of Section 3.3 inside a potential
+ * SD region: query [q0, q1) and target [t0, t1), global coordinates, with
+ * the strand o, the chain score (aligned bases less the gap penalties), the
+ * exact seeds it holds and the initial chains it joins; region = the index
+ * of its potential SD region in the sedef_chain2 input.
+ */
+typedef struct sedef_sd_t {
+  uint32_t region, o, q0, q1, t0, t1;
+  uint32_t score, seeds, parts, reserved;
+} sedef_sd_t;
+
 /* SD candidate: one connected group of chains, per-sequence coordinates. */
 typedef struct sedef_cand_t {
   uint32_t qseq, q0, q1, tseq, t0, t1;
@@ -177,6 +189,15 @@ const char* sedef_last_error(void);
 int sedef_create(int device, void* stream, sedef_ctx** out);
 int sedef_destroy(sedef_ctx* ctx);
 int sedef_set_stream(sedef_ctx* ctx, void* stream);
+
+/*
+ * Caps the device scratch memory the context may hold (its pool and the
+ * buffers of sedef_selfsearch*) at `bytes` (< 0: no cap, the default).  A
+ * call whose scratch would pass the cap fails with SEDEF_ERR_OOM as if
+ * cudaMalloc had failed, and the context stays usable.  Lowering the cap
+ * below what the context holds gives its blocks back first.  Synchronizes.
+ */
+int sedef_set_scratch_limit(sedef_ctx* ctx, int64_t bytes);
 
 /*
  * Tracing.  While enabled, every kernel the context launches is bracketed by
@@ -290,8 +311,9 @@ int sedef_filter(sedef_ctx* ctx, const uint64_t* d_qrec, int64_t nq, const int64
 /*
  * Autotuner of the filter's first shared-memory tier: times each compiled
  * shape (threads per query window; hits and dense groups a window may keep
- * in shared memory) on a uniform sample of at most 8192 of the query
- * windows (same arguments as sedef_filter) and keeps the fastest for later
+ * in shared memory) on a uniform sample of the query windows (at least
+ * 65,536 or one in sixteen; best of two timed runs each) with the same
+ * arguments as sedef_filter, and keeps the fastest for later
  * sedef_filter calls on this context; *variant_out receives its number.
  * Results never depend on the shape: windows a shape cannot hold move to
  * the next tier.  Synchronizes.
@@ -400,6 +422,29 @@ int sedef_extend(sedef_ctx* ctx, const sedef_run_t* d_runs, int64_t nruns, const
                  int64_t max_len, sedef_region_t* d_regions, int64_t cap, int64_t* h_nregions);
 
 /*
+ * f2 (Section 3.3, detecting the final SDs inside potential SD regions):
+ * for every region of d_regions (sedef_extend's output) the query
+ * X = G[qa, qb) and the target Y = G[ta, tb) (reverse complement when
+ * o = 1), read from sedef_pack's d_packed / d_nbits over nbases bases (case
+ * does not matter; non-ACGT bases match nothing).  Seeds are the maximal
+ * exact matches of at least 11 bases.  Tier 1: colinear seeds whose gaps
+ * on both axes are at most ceil(1000 * delta_G) (seeds may overlap where an
+ * indel shifts the diagonal; a link scores the bases new on both axes),
+ * best chains by DP (ties: the later seed), taken greedily by decreasing
+ * score as disjoint initial chains.  Tier 2: initial chains chained with
+ * gaps of at most 10,000 on both axes and an affine gap penalty of
+ * 25 + g / 50 for the larger gap g (the paper leaves its values open), a
+ * link only when it raises the score, the same greedy extraction.  Every
+ * final chain spanning at least 1,000 bases on both axes is one sedef_sd_t,
+ * sorted by (region, q0, q1, t0, t1, score).  Regions must be shorter than
+ * 2^20 bases (SEDEF_ERR_UNSUPPORTED otherwise).  Writes d_out[0..cap) and
+ * *h_nout (SEDEF_ERR_CAPACITY when cap is too small).  Synchronizes.
+ */
+int sedef_chain2(sedef_ctx* ctx, const uint32_t* d_packed, const uint32_t* d_nbits, int64_t nbases,
+                 const sedef_region_t* d_regions, int64_t nregions, const sedef_params* p,
+                 sedef_sd_t* d_out, int64_t cap, int64_t* h_nout);
+
+/*
  * Whole self-search of a device-resident input (Sections 2.2-3.3 in one
  * call): pack, sketch, index, filter (with refine), chain and merge of
  * d_seq (total bytes h_seq_off[nseq]) on the context's stream, with
@@ -485,7 +530,9 @@ int sedef_graph_destroy(sedef_graph* g);
  * the path for that slot (windows the kernel's shared-memory tier could not
  * hold, run ordering and refine, chaining, merging) and copies its
  * candidates (query coordinates within the request, target coordinates per
- * target sequence) to h_cands; the slot is free again afterwards.  A CTA of
+ * target sequence) to h_cands; the slot is free again afterwards (when cap
+ * is too small it returns SEDEF_ERR_CAPACITY with the count in *h_ncands
+ * and keeps the candidates: call it again with a larger buffer).  A CTA of
  * the persistent kernel that finds no work for idle_timeout_s seconds
  * leaves; when all have left that way sedef_server_status returns
  * SEDEF_ERR_TIMEOUT (running = 0, timed_out = 1), and the next submit or

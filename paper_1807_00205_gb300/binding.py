@@ -25,6 +25,9 @@ CHAIN_DTYPE = np.dtype([("i", "<u4"), ("qseq", "<u4"), ("q0", "<u4"), ("q1", "<u
 REGION_DTYPE = np.dtype([("i", "<u4"), ("j_star", "<u4"), ("qa", "<u4"), ("qb", "<u4"),
                          ("ta", "<u4"), ("tb", "<u4"), ("est", "<u4"), ("den", "<u4"),
                          ("o", "<u4"), ("reserved", "<u4")])
+SD_DTYPE = np.dtype([("region", "<u4"), ("o", "<u4"), ("q0", "<u4"), ("q1", "<u4"),
+                     ("t0", "<u4"), ("t1", "<u4"), ("score", "<u4"), ("seeds", "<u4"),
+                     ("parts", "<u4"), ("reserved", "<u4")])
 CAND_DTYPE = np.dtype([("qseq", "<u4"), ("q0", "<u4"), ("q1", "<u4"), ("tseq", "<u4"),
                        ("t0", "<u4"), ("t1", "<u4"), ("o", "<u4"), ("score", "<u4"),
                        ("nchains", "<u4"), ("reserved", "<u4")])
@@ -42,10 +45,10 @@ class Params(ctypes.Structure):
 
 
 EXPORTS = ["sedef_default_params", "sedef_last_error", "sedef_create", "sedef_destroy",
-           "sedef_set_stream", "sedef_trace_enable", "sedef_trace_report", "sedef_launch_count", "sedef_filter_stats",
+           "sedef_set_stream", "sedef_set_scratch_limit", "sedef_trace_enable", "sedef_trace_report", "sedef_launch_count", "sedef_filter_stats",
            "sedef_threshold_table", "sedef_pack", "sedef_sketch", "sedef_sketch_noalloc",
            "sedef_index", "sedef_filter", "sedef_filter_autotune", "sedef_filter_variant",
-           "sedef_chain", "sedef_extend", "sedef_merge", "sedef_selfsearch",
+           "sedef_chain", "sedef_extend", "sedef_chain2", "sedef_merge", "sedef_selfsearch",
            "sedef_selfsearch_host",
            "sedef_index_blob_size",
            "sedef_index_save", "sedef_index_blob_info", "sedef_index_load", "sedef_graph_create",
@@ -84,6 +87,7 @@ def load(build_if_missing: bool = True):
     lib.sedef_create.argtypes = [ctypes.c_int, vp, ctypes.POINTER(vp)]
     lib.sedef_destroy.argtypes = [vp]
     lib.sedef_set_stream.argtypes = [vp, vp]
+    lib.sedef_set_scratch_limit.argtypes = [vp, i64]
     lib.sedef_threshold_table.argtypes = [P, vp, i32, ctypes.POINTER(ctypes.c_double)]
     lib.sedef_pack.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.sedef_sketch.argtypes = [vp, vp, vp, vp, vp, i32, P, vp, i64, ctypes.POINTER(i64)]
@@ -114,6 +118,7 @@ def load(build_if_missing: bool = True):
     lib.sedef_merge.argtypes = [vp, vp, i64, vp, i32, vp, i32, P, vp, i64, ctypes.POINTER(i64)]
     lib.sedef_extend.argtypes = [vp, vp, i64, vp, i64, vp, i32, vp, i64, vp, i32, P, i64, vp, i64,
                                  ctypes.POINTER(i64)]
+    lib.sedef_chain2.argtypes = [vp, vp, vp, i64, vp, i64, P, vp, i64, ctypes.POINTER(i64)]
     lib.sedef_selfsearch.argtypes = [vp, vp, vp, i32, P, vp, i64, ctypes.POINTER(i64)]
     lib.sedef_selfsearch_host.argtypes = [vp, vp, vp, i32, P, vp, i64, ctypes.POINTER(i64)]
     lib.sedef_server_create.argtypes = [vp, vp, vp, vp, i64, vp, i32, P, i32, i64,
@@ -213,6 +218,10 @@ class Context:
 
     def _empty(self, n, dtype):
         return self.torch.empty(max(int(n), 1), dtype=dtype, device=self.device)
+
+    def sedef_set_scratch_limit(self, nbytes: int):
+        """Caps the context's device scratch (< 0: no cap)."""
+        _check(self.lib.sedef_set_scratch_limit(self.handle, int(nbytes)))
 
     # -- tracing ----------------------------------------------------------------
 
@@ -362,6 +371,24 @@ class Context:
                                      to.ctypes.data, len(to) - 1, ctypes.byref(p), int(max_len),
                                      _ptr(out), cap, ctypes.byref(count)))
         return out[:count.value * REGION_DTYPE.itemsize], count.value
+
+    def sedef_chain2(self, packed, nbits, nbases: int, regions, nregions: int, p: Params,
+                     cap: int = None):
+        """f2: the SDs inside the potential SD regions (device uint8 tensor of
+        sedef_sd_t, count)."""
+        cap = cap if cap is not None else max(1024, 4 * int(nregions))
+        count = ctypes.c_int64()
+        for _ in range(2):
+            out = self._empty(cap * SD_DTYPE.itemsize, self.torch.uint8)
+            st = self.lib.sedef_chain2(self.handle, _ptr(packed), _ptr(nbits), int(nbases),
+                                       _ptr(regions), int(nregions), ctypes.byref(p), _ptr(out), cap,
+                                       ctypes.byref(count))
+            if st == SEDEF_ERR_CAPACITY:
+                cap = count.value
+                continue
+            _check(st)
+            return out[:count.value * SD_DTYPE.itemsize], count.value
+        raise SedefError(SEDEF_ERR_CAPACITY, "chain2 capacity")
 
     def sedef_merge(self, chains, nchains, qoff, toff, p: Params):
         qo, to = _offsets(qoff), _offsets(toff)
@@ -575,3 +602,72 @@ def records_to_rows(rec: np.ndarray) -> np.ndarray:
 
 def struct_view(t, dtype) -> np.ndarray:
     return t.cpu().numpy().view(dtype)
+
+
+class DeviceServer:
+    """sedef_server_*: continuous batching over a resident target index.  A
+    persistent filter kernel drains a device work queue of query windows;
+    `submit` admits a request into a free slot (None when none is free),
+    `poll` returns a slot whose windows are filtered, `finish` completes it
+    and returns its candidates."""
+
+    def __init__(self, ctx: "Context", trec, tsorted, toff_tab, toffsets, p: Params,
+                 slots: int = 8, slot_bases: int = 5_000_000, idle_timeout_s: float = 1.0):
+        self.lib = ctx.lib
+        self.ctx = ctx  # the index tensors and the context outlive the server
+        self.keep = (trec, tsorted, toff_tab)
+        off = _offsets(toffsets)
+        self.p = params_from_struct(p, self_mode=0)
+        self.slots = slots
+        self.slot_bases = slot_bases
+        h = ctypes.c_void_p()
+        _check(self.lib.sedef_server_create(ctx.handle, _ptr(trec), _ptr(tsorted), _ptr(toff_tab),
+                                            trec.numel(), off.ctypes.data, len(off) - 1,
+                                            ctypes.byref(self.p), slots, slot_bases,
+                                            float(idle_timeout_s), ctypes.byref(h)))
+        self.handle = h
+        self._cap = 1 << 16
+
+    def submit(self, seq: np.ndarray):
+        """The slot the request went to, or None when every slot is busy."""
+        seq = np.ascontiguousarray(seq, dtype=np.uint8)
+        slot = ctypes.c_int32(-1)
+        st = self.lib.sedef_server_submit(self.handle, seq.ctypes.data, len(seq), ctypes.byref(slot))
+        if st == SEDEF_ERR_CAPACITY:
+            return None
+        _check(st)
+        return slot.value
+
+    def poll(self, wait_s: float = 0.0):
+        slot = ctypes.c_int32(-1)
+        _check(self.lib.sedef_server_poll(self.handle, float(wait_s), ctypes.byref(slot)))
+        return slot.value if slot.value >= 0 else None
+
+    def finish(self, slot: int) -> np.ndarray:
+        count = ctypes.c_int64()
+        for _ in range(2):
+            out = np.zeros(self._cap, dtype=CAND_DTYPE)
+            st = self.lib.sedef_server_finish(self.handle, slot, out.ctypes.data, self._cap,
+                                              ctypes.byref(count))
+            if st == SEDEF_ERR_CAPACITY:
+                self._cap = int(count.value) + 1024
+                continue
+            _check(st)
+            return out[:count.value]
+        raise SedefError(SEDEF_ERR_CAPACITY, "server candidates")
+
+    def status(self) -> dict:
+        run, tmo = ctypes.c_int32(), ctypes.c_int32()
+        st = self.lib.sedef_server_status(self.handle, ctypes.byref(run), ctypes.byref(tmo))
+        return {"status": st, "running": bool(run.value), "timed_out": bool(tmo.value)}
+
+    def close(self):
+        if self.handle:
+            self.lib.sedef_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

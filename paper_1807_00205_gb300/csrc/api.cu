@@ -32,6 +32,8 @@ struct sedef_ctx {
   // next time, so that a repeated search does not rerun the filter)
   int64_t last_runs = 0;
   const char* stage = "";  // label of traced launches (sedef::StageScope)
+  size_t scratch_limit = SIZE_MAX;  // device bytes both pools may hold
+  size_t scratch_held = 0;
 };
 
 namespace sedef {
@@ -62,11 +64,14 @@ void* Pool::alloc(size_t bytes) {
     blocks[best].used = true;
     return blocks[best].ptr;
   }
+  if (limit && held && *held + bytes > *limit) return nullptr;
   void* p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+  const cudaError_t e = ordered ? cudaMallocAsync(&p, bytes, *ordered) : cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
+  if (held) *held += bytes;
   blocks.push_back({p, bytes, true});
   return p;
 }
@@ -87,7 +92,10 @@ void Pool::restore(const std::vector<char>& used_before) {
 }
 
 void Pool::release() {
-  for (auto& b : blocks) cudaFree(b.ptr);
+  for (auto& b : blocks) {
+    if (ordered) cudaFreeAsync(b.ptr, *ordered); else cudaFree(b.ptr);
+    if (held) *held -= b.size;
+  }
   blocks.clear();
 }
 
@@ -125,6 +133,14 @@ TraceScope::~TraceScope() {
 
 cudaStream_t ctx_stream(sedef_ctx* ctx) { return ctx->stream; }
 void ctx_pool_reset(sedef_ctx* ctx) { ctx->pool.reset(); }
+int ctx_use_stream_ordered_alloc(sedef_ctx* ctx) {
+  ctx->pool.ordered = ctx->io.ordered = &ctx->stream;
+  if (!ctx_host(ctx, 1 << 20)) return SEDEF_ERR_OOM;
+  return SEDEF_OK;
+}
+int64_t ctx_scratch_limit(sedef_ctx* ctx) {
+  return ctx->scratch_limit == SIZE_MAX ? -1 : (int64_t)ctx->scratch_limit;
+}
 
 const char* ctx_set_stage(sedef_ctx* ctx, const char* stage) {
   if (!ctx) return "";
@@ -308,6 +324,8 @@ int sedef_create(int device, void* stream, sedef_ctx** out) {
   c->pool.device = device;
   c->io.device = device;
   c->stream = (cudaStream_t)stream;
+  c->pool.limit = c->io.limit = &c->scratch_limit;
+  c->pool.held = c->io.held = &c->scratch_held;
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
   *out = c;
   return SEDEF_OK;
@@ -326,6 +344,19 @@ int sedef_destroy(sedef_ctx* ctx) {
   ctx->io.release();
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   delete ctx;
+  return SEDEF_OK;
+}
+
+int sedef_set_scratch_limit(sedef_ctx* ctx, int64_t bytes) {
+  if (!ctx) return fail(SEDEF_ERR_INVALID, "ctx is NULL");
+  SEDEF_CUDA(cudaSetDevice(ctx->device));
+  SEDEF_CUDA(cudaStreamSynchronize(ctx->stream));
+  // blocks above the new limit are given back first
+  if (bytes >= 0 && ctx->scratch_held > (size_t)bytes) {
+    ctx->pool.release();
+    ctx->io.release();
+  }
+  ctx->scratch_limit = bytes < 0 ? SIZE_MAX : (size_t)bytes;
   return SEDEF_OK;
 }
 
@@ -553,6 +584,24 @@ int sedef_extend(sedef_ctx* ctx, const sedef_run_t* d_runs, int64_t nruns, const
   StageScope stage(ctx, "extend");
   return run_extend(ctx, d_runs, nruns, d_qext, nq, h_qoff, nqseq, d_text, nt, h_toff, ntseq, D,
                     p, max_len, d_regions, cap, h_nregions);
+}
+
+int sedef_chain2(sedef_ctx* ctx, const uint32_t* d_packed, const uint32_t* d_nbits, int64_t nbases,
+                 const sedef_region_t* d_regions, int64_t nregions, const sedef_params* p,
+                 sedef_sd_t* d_out, int64_t cap, int64_t* h_nout) {
+  if (!ctx || !h_nout) return fail(SEDEF_ERR_INVALID, "NULL argument");
+  Derived D;
+  SEDEF_TRY(derive(p, &D));
+  *h_nout = 0;
+  if (nregions < 0 || (nregions > 0 && !d_regions)) return fail(SEDEF_ERR_INVALID, "bad regions");
+  if (nbases < 0 || (nbases > 0 && (!d_packed || !d_nbits)))
+    return fail(SEDEF_ERR_INVALID, "bad packed sequence");
+  if (cap > 0 && !d_out) return fail(SEDEF_ERR_INVALID, "NULL output buffer");
+  if (nregions == 0) return SEDEF_OK;
+  SEDEF_CUDA(cudaSetDevice(ctx->device));
+  ctx->pool.reset();
+  StageScope stage(ctx, "chain2");
+  return run_chain2(ctx, d_packed, d_nbits, nbases, d_regions, nregions, D, d_out, cap, h_nout);
 }
 
 int sedef_merge(sedef_ctx* ctx, const sedef_chain_t* d_chains, int64_t nchains,

@@ -60,6 +60,13 @@ struct Pool {
   };
   std::vector<Block> blocks;
   int device = 0;
+  // device bytes the pool may hold in all (sedef_set_scratch_limit); an
+  // allocation past it fails as cudaMalloc would
+  const size_t* limit = nullptr;
+  size_t* held = nullptr;
+  // stream-ordered blocks (cudaMallocAsync / cudaFreeAsync on *ordered):
+  // they do not synchronize with the work of other streams
+  const cudaStream_t* ordered = nullptr;
   void* alloc(size_t bytes);
   void reset();
   void release();
@@ -220,6 +227,9 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
                const int64_t* h_toff, int ntseq, const Derived& D, const int32_t* h_mtab,
                sedef_run_t* runs, int64_t cap, int64_t* nruns, int tune, Planned* pl = nullptr);
 int filter_variant_count();
+int run_chain2(sedef_ctx* ctx, const uint32_t* packed, const uint32_t* nbits, int64_t nbases,
+               const sedef_region_t* d_regions, int64_t nregions, const Derived& D,
+               sedef_sd_t* out, int64_t cap, int64_t* nout);
 int run_extend(sedef_ctx* ctx, const sedef_run_t* runs, int64_t nruns, const uint64_t* qrec,
                int64_t nq, const int64_t* h_qoff, int nqseq, const uint64_t* trec, int64_t nt,
                const int64_t* h_toff, int ntseq, const Derived& D, const sedef_params* p,
@@ -257,6 +267,11 @@ cudaStream_t ctx_stream(sedef_ctx* ctx);
 void* ctx_alloc(sedef_ctx* ctx, size_t bytes);
 std::vector<char> ctx_pool_snapshot(sedef_ctx* ctx);
 void ctx_pool_reset(sedef_ctx* ctx);  // every pool block free for the next call
+// The context allocates its scratch in stream order and keeps a 1 MB pinned
+// buffer, so that its calls never synchronize with other streams' kernels
+// (a persistent kernel on another stream would hold them up).
+int ctx_use_stream_ordered_alloc(sedef_ctx* ctx);
+int64_t ctx_scratch_limit(sedef_ctx* ctx);  // sedef_set_scratch_limit's cap (-1: none)
 void ctx_pool_restore(sedef_ctx* ctx, const std::vector<char>& used_before);
 void* ctx_host(sedef_ctx* ctx, size_t bytes);  // pinned host scratch
 int ctx_device(sedef_ctx* ctx);

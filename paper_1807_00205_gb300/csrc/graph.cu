@@ -120,6 +120,8 @@ int sedef_graph_create(sedef_ctx* ctx, const uint8_t* d_seq, const int64_t* h_of
   int rc = sedef_create(ctx_device(ctx), g->stream, &g->ctx);
   if (rc != SEDEF_OK) return bail(rc);
   ctx_set_filter_variant(g->ctx, ctx_filter_variant(ctx));
+  // the graph's scratch counts against the caller's cap
+  if ((rc = sedef_set_scratch_limit(g->ctx, ctx_scratch_limit(ctx))) != SEDEF_OK) return bail(rc);
   auto at_least_1 = [](int64_t v) { return v < 1 ? (int64_t)1 : v; };
   g->caps.records = at_least_1(caps->records);
   g->caps.slow_hits = at_least_1(caps->slow_hits);

@@ -1,19 +1,23 @@
-"""Serving: a resident target index and a continuously batched request loop.
+"""Serving: a resident target index and continuous batching of requests.
 
 The target genome is packed, sketched and indexed once and stays in device
-memory.  Requests (query regions) arrive on a host queue.  Each worker -- a
-host thread with its own library context and CUDA stream -- repeatedly takes
-every request that is waiting (up to a base budget, and only while the
-admission controller finds room in device memory), runs pack, sketch,
-filter, refine, chain and merge for them in one pass against the resident
-index (non-self mode, one query sequence per request), and splits the
-candidates back by request.  Requests that arrive while a batch is on the
-GPU are admitted to the next free worker, so batches of different workers
-overlap on the device.  The plain form runs one request per pass on one
-worker.
+memory.  Requests (query regions) arrive on a host queue.
 
-Results of a request are the same alone and in a batch: every query window
-is compared with the whole target independently of the other sequences.
+Served form (batching=True): continuous batching on the device through the
+library's server (sedef_server_*).  A persistent filter kernel drains a work
+queue of query windows; an admission thread moves waiting requests into free
+request slots as slots free up (the slots are sized once, from free device
+memory), so a request that arrives while others are on the GPU joins the
+running kernel at once; a completion thread finishes every request whose
+windows are done (global path, refine, chaining, merging) on its own stream
+while the kernel keeps filtering the others.
+
+Plain form (batching=False): one request per pass (pack ... merge) on one
+worker.  With several workers and batching=False each worker takes every
+waiting request (admitted by free memory) into one pass.
+
+Results of a request are the same alone, in a batch and served: every query
+window is compared with the whole target independently of the others.
 """
 from __future__ import annotations
 
@@ -96,6 +100,16 @@ class ResidentIndex:
             self.tsorted, self.toff = ctx.sedef_index(self.trec, self.p_index)
         torch.cuda.synchronize(ctx.device)
 
+    @classmethod
+    def from_arrays(cls, trec, tsorted, toff, offsets, p: "binding.Params") -> "ResidentIndex":
+        """An index already on the device (records by position, records by
+        hash, offsets) over sequences at `offsets`."""
+        self = cls.__new__(cls)
+        self.p_index = binding.params_from_struct(p, self_mode=1)
+        self.trec, self.tsorted, self.toff = trec, tsorted, toff
+        self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        return self
+
     def save(self, ctx: "binding.Context") -> bytes:
         return ctx.sedef_index_save(self.trec, self.tsorted, self.toff, self.p_index.k,
                                     self.offsets)
@@ -126,12 +140,16 @@ def search(ctx: "binding.Context", index: ResidentIndex, reqs: list, p: "binding
 
 
 class Server:
-    """Continuous batching over `workers` host threads (each its own stream)."""
+    """Serves requests against a resident index: the device work queue
+    (batching=True) or host workers (batching=False; see the module notes)."""
+
+    SLOT_BYTES_PER_BASE = 32  # device bytes a request slot holds per query base
 
     def __init__(self, index: ResidentIndex, p: "binding.Params", workers: int = 2,
                  batching: bool = True, max_batch_bases: int = 64 << 20,
                  reserve_bytes: int = 8 << 30, device: int = 0, free_bytes_fn=None,
-                 ctx_factory=None):
+                 ctx_factory=None, slots: int = 8, slot_bases: int = 5_000_000,
+                 idle_timeout_s: float = 1.0):
         import torch
         self.index = index
         self.p = p
@@ -140,8 +158,27 @@ class Server:
         self.cv = threading.Condition()
         self.stop = False
         self.completed = []
+        self.batches = 0
         if free_bytes_fn is None:
             free_bytes_fn = lambda: torch.cuda.mem_get_info(device)[0]  # noqa: E731
+        self.device_queue = batching and ctx_factory is None
+        if self.device_queue:
+            # admission by free HBM: as many slots as the free memory (less a
+            # reserve for the finishing passes) holds, at most `slots`
+            per_slot = slot_bases * self.SLOT_BYTES_PER_BASE
+            fit = max(1, (free_bytes_fn() - reserve_bytes) // per_slot)
+            self.nslots = int(min(slots, fit))
+            self.ctx = binding.Context(device)
+            self.dev = binding.DeviceServer(self.ctx, index.trec, index.tsorted, index.toff,
+                                            index.offsets, p, slots=self.nslots,
+                                            slot_bases=slot_bases, idle_timeout_s=idle_timeout_s)
+            self.inflight = {}
+            self.threads = [threading.Thread(target=self._admit, daemon=True),
+                            threading.Thread(target=self._complete, daemon=True)]
+            self.ctxs = [self.ctx]
+            # a request longer than a slot goes through one plain pass
+            self.fallback = binding.Context(device, stream=torch.cuda.Stream(device))
+            return
         self.admission = Admission(max_batch_bases if batching else 1, reserve_bytes,
                                    free_bytes_fn)
         if ctx_factory is None:
@@ -149,12 +186,24 @@ class Server:
         self.ctxs = [ctx_factory() for _ in range(workers)]
         self.threads = [threading.Thread(target=self._work, args=(c,), daemon=True)
                         for c in self.ctxs]
-        self.batches = 0
 
     def warm(self, seqs: list, autotune: bool = True):
-        """Picks the filter shape on these query sequences against the
-        resident index (autotuner, first worker's context; every worker takes
-        the result), then one untimed pass per worker over them."""
+        """Untimed passes over these query sequences.  Host workers first
+        pick the filter shape on them against the resident index (autotuner;
+        every worker takes the result)."""
+        if self.device_queue:
+            for q in seqs:
+                if len(q) > self.dev.slot_bases:
+                    continue
+                slot = self.dev.submit(q)
+                while slot is None:
+                    time.sleep(0.001)
+                    slot = self.dev.submit(q)
+                done = None
+                while done is None:
+                    done = self.dev.poll(0.01)
+                self.dev.finish(done)
+            return
         if autotune and seqs:
             import torch
             c0 = self.ctxs[0]
@@ -182,6 +231,86 @@ class Server:
             self.queue.append(r)
             self.cv.notify()
 
+    def _done(self, reqs: list):
+        now = time.perf_counter()
+        with self.cv:
+            for r in reqs:
+                r.done = now
+            self.completed.extend(reqs)
+            self.batches += 1
+
+    # -- device work queue ---------------------------------------------------
+
+    def _admit(self):
+        """Moves waiting requests into free slots, oldest first."""
+        while True:
+            with self.cv:
+                while not self.queue and not self.stop:
+                    self.cv.wait(0.05)
+                if self.stop and not self.queue:
+                    return
+                r = self.queue[0]
+            try:
+                if len(r.seq) > self.dev.slot_bases:
+                    search(self.fallback, self.index, [r], self.p)
+                    with self.cv:
+                        self.queue.popleft()
+                    self._done([r])
+                    continue
+                slot = self.dev.submit(r.seq)
+            except Exception as e:  # the request fails, admission goes on
+                r.error = f"{type(e).__name__}: {e}"
+                with self.cv:
+                    self.queue.popleft()
+                self._done([r])
+                continue
+            if slot is None:  # every slot is busy: wait for one to free up
+                time.sleep(0.0002)
+                continue
+            with self.cv:
+                self.queue.popleft()
+                self.inflight[slot] = r
+                self.cv.notify_all()
+
+    def _complete(self):
+        """Finishes every request whose windows the kernel has filtered."""
+        while True:
+            with self.cv:
+                if self.stop and not self.queue and not self.inflight:
+                    return
+            try:
+                slot = self.dev.poll(0.002)
+            except Exception as e:
+                with self.cv:
+                    failed = list(self.inflight.values())
+                    self.inflight.clear()
+                for r in failed:
+                    r.error = f"{type(e).__name__}: {e}"
+                self._done(failed)
+                continue
+            if slot is None:
+                continue
+            with self.cv:
+                # the admission thread records the slot right after submit
+                # returns; a short request can be filtered before that
+                give_up = time.perf_counter() + 5.0
+                while slot not in self.inflight and time.perf_counter() < give_up:
+                    self.cv.wait(0.001)
+                r = self.inflight.pop(slot, None)
+            if r is None:
+                self.dev.finish(slot)  # an orphan (cannot happen): free its slot
+                continue
+            try:
+                c = self.dev.finish(slot)
+                c["qseq"] = 0
+                r.cands = c
+            except Exception as e:
+                r.error = f"{type(e).__name__}: {e}"
+                r.cands = None
+            self._done([r])
+
+    # -- host workers ------------------------------------------------------
+
     def _work(self, ctx):
         while True:
             with self.cv:
@@ -201,12 +330,7 @@ class Server:
                     r.cands = None
             finally:
                 self.admission.release(reqs)
-            now = time.perf_counter()
-            with self.cv:
-                for r in reqs:
-                    r.done = now
-                self.completed.extend(reqs)
-                self.batches += 1
+            self._done(reqs)
 
     def close(self):
         with self.cv:
@@ -215,6 +339,9 @@ class Server:
         for t in self.threads:
             if t.is_alive():
                 t.join()
+        if self.device_queue:
+            self.dev.close()
+            self.fallback.close()
         for c in self.ctxs:
             c.close()
 

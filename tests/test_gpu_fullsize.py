@@ -187,15 +187,12 @@ def test_human_3gbp_sampled(ctx):
     del d
     recs = oracle.sketch(g.seq, g.offsets, pd, threads=os.cpu_count() or 1)
     assert_rows_equal(rec_rows(out["rec"]), recs, "sketch")
-    # index: the (checked) records sorted by (hash, position); offsets over
-    # every hash (the oracle's index is checked at smaller sizes)
-    rec = binding.to_numpy_records(out["rec"])
-    srt = binding.to_numpy_records(out["sorted"])
-    assert np.array_equal(srt, np.sort(rec))
-    h = (srt >> np.uint64(33)).astype(np.int64)
-    want_off = np.searchsorted(h, np.arange((1 << (2 * pd["k"])) + 1)).astype(np.uint32)
-    assert np.array_equal(out["off"].cpu().numpy().view(np.uint32), want_off)
-    del rec, srt, h, want_off
+    # index: the whole sorted index and the offsets of every hash against
+    # the oracle's
+    idx_rows, idx_off = oracle.index(recs, pd["k"])
+    assert_rows_equal(rec_rows(out["sorted"]), idx_rows, "index")
+    assert np.array_equal(out["off"].cpu().numpy().view(np.uint32), idx_off)
+    del idx_rows, idx_off
     win = sample_windows(g, pd, seed=13, n_random=100, n_planted=50)
     runs = oracle.filter_runs(recs, g.offsets, recs, g.offsets, pd, windows=win)
     got = run_rows(out["runs"])
@@ -205,3 +202,20 @@ def test_human_3gbp_sampled(ctx):
     gch = chain_rows(out["chains"])
     assert_rows_equal(gch[np.isin(gch[:, 0], win)], chains, "chains of sampled windows")
     check_candidate_properties(gch, cand_rows_global(out["cands"], g.offsets))
+    # serving against this resident index (the device work queue): 24
+    # requests cut from the genome with mutation, each equal to the oracle's
+    # non-self search of the region against the whole genome
+    from paper_1807_00205_gb300 import serve
+    from tests.test_gpu_serve import oracle_cands, served_rows
+    index = serve.ResidentIndex.from_arrays(out["rec"], out["sorted"], out["off"], g.offsets, p)
+    for key in ("runs", "chains", "cands", "packed", "mask", "nbits"):
+        out.pop(key, None)
+    pool = synth.query_regions(g, 24, seed=21, len_lo=10_000, len_hi=60_000)
+    srv = serve.Server(index, p, batching=True, slots=6, slot_bases=100_000)
+    srv.start()
+    serve.run_load(srv, pool, rate=500.0, count=len(pool), seed=3)
+    srv.close()
+    got = {r.rid: r.cands for r in srv.completed}
+    assert len(got) == len(pool)
+    for k, q in enumerate(pool):
+        assert_rows_equal(served_rows(got[k], g), oracle_cands(q, g, recs), f"served request {k}")

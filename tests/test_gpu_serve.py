@@ -88,3 +88,74 @@ def test_index_blob_round_trip():
     with pytest.raises(binding.SedefError):
         serve.ResidentIndex(ctx, None, None, p, blob=bytes(bad))
     ctx.close()
+
+
+def _alone(ctx, index, pool, p):
+    out = []
+    for k, q in enumerate(pool):
+        r = serve.Request(rid=k, seq=q)
+        serve.search(ctx, index, [r], p)
+        out.append(r.cands)
+    return out
+
+
+def test_device_queue_more_requests_than_slots():
+    """Two slots, fourteen requests arriving at once: requests wait for a
+    slot, join the running kernel as slots free up, and each result equals
+    the request searched alone."""
+    need_gpu()
+    g = synth.small_case(88, lengths=(400_000, 150_000), n_sd=8, sd_lo=2000, sd_hi=12000,
+                         id_lo=0.85, mask_frac=0.2, n_gaps=True)
+    ctx = binding.Context(0)
+    p = binding.params()
+    index = serve.ResidentIndex(ctx, g.seq, g.offsets, p)
+    pool = synth.query_regions(g, 14, seed=5, len_lo=3_000, len_hi=40_000)
+    alone = _alone(ctx, index, pool, p)
+    srv = serve.Server(index, p, batching=True, slots=2, slot_bases=50_000)
+    assert srv.device_queue and srv.nslots == 2
+    srv.start()
+    serve.run_load(srv, pool, rate=1e6, count=len(pool), seed=2)
+    srv.close()
+    got = {r.rid: r.cands for r in srv.completed}
+    for k in range(len(pool)):
+        assert np.array_equal(got[k], alone[k]), k
+    assert sum(len(a) for a in alone) > 0
+    ctx.close()
+
+
+def test_device_queue_idle_wait_times_out_and_restarts():
+    """The persistent kernel's wait for work is bounded: with nothing
+    submitted for longer than the idle limit it leaves and the server reports
+    SEDEF_ERR_TIMEOUT; the next request launches it again and is served
+    correctly."""
+    import time
+    need_gpu()
+    g = synth.small_case(89, lengths=(200_000,), n_sd=4, sd_lo=2000, sd_hi=8000, id_lo=0.9)
+    ctx = binding.Context(0)
+    p = binding.params()
+    index = serve.ResidentIndex(ctx, g.seq, g.offsets, p)
+    pool = synth.query_regions(g, 2, seed=7, len_lo=5_000, len_hi=20_000)
+    alone = _alone(ctx, index, pool, p)
+    dev = binding.DeviceServer(ctx, index.trec, index.tsorted, index.toff, index.offsets, p,
+                               slots=2, slot_bases=50_000, idle_timeout_s=0.2)
+
+    def one(q):
+        slot = dev.submit(q)
+        assert slot is not None
+        done = None
+        t0 = time.time()
+        while done is None and time.time() - t0 < 30:
+            done = dev.poll(0.01)
+        assert done == slot
+        c = dev.finish(slot)
+        c["qseq"] = 0
+        return c
+
+    assert np.array_equal(one(pool[0]), alone[0])
+    time.sleep(1.0)  # nothing to do for five idle limits
+    st = dev.status()
+    assert st == {"status": -4, "running": False, "timed_out": True}
+    assert np.array_equal(one(pool[1]), alone[1])  # relaunched
+    assert dev.status()["status"] in (0, -4)
+    dev.close()
+    ctx.close()
