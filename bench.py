@@ -388,6 +388,58 @@ def serve_arm(args):
     ctx.close()
 
 
+# -------------------------------------------- f1 extension, f2 chaining --
+
+def measure_extension(ctx, out, W, p, d_seq, stream, max_seeds=2048, reps=2):
+    """Section 3.2 (sedef_extend) and Section 3.3 (sedef_chain2) on an
+    evenly spaced sample of at most max_seeds kept seeds of the pass, timed
+    with CUDA events (best of `reps`).  Extending every kept seed of a large
+    workload takes minutes: each seed of a duplication grows past it until
+    the estimate falls, so the work grows with the square of the
+    duplications' lengths."""
+    import torch
+    from paper_1807_00205_gb300 import binding
+    runs = binding.struct_view(out["runs"], binding.RUN_DTYPE).copy()
+    kept = np.nonzero(runs["keep"] == 1)[0]
+    if len(kept) == 0:
+        return None
+    pick = kept[np.linspace(0, len(kept) - 1, min(max_seeds, len(kept))).astype(np.int64)]
+    sel = np.zeros(len(runs), dtype=bool)
+    sel[pick] = True
+    runs["keep"] = np.where(sel, runs["keep"], 0)
+    pa = binding.params_from_struct(p, min_unmasked=0)
+    with torch.cuda.stream(stream):
+        d_runs = torch.from_numpy(runs.view(np.uint8)).to(d_seq.device)
+        ext = ctx.sedef_sketch(out["packed"], out["mask"], out["nbits"], W.offsets, pa)
+
+    def timed(fn):
+        best, res = None, None
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                res = fn()
+                e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        return best, res
+
+    ems, (regions, nreg) = timed(lambda: ctx.sedef_extend(d_runs, len(runs), ext, W.offsets, ext,
+                                                          W.offsets, p))
+    cms, (sds, nsd) = timed(lambda: ctx.sedef_chain2(out["packed"], out["nbits"], W.length, regions,
+                                                     nreg, p))
+    reg = binding.struct_view(regions, binding.REGION_DTYPE)
+    span = (reg["qb"].astype(np.int64) - reg["qa"]).sum()
+    return {"seeds": int(nreg), "kept_seeds_in_pass": int(len(kept)),
+            "sample": f"{int(nreg)} evenly spaced of {len(kept)} kept seeds",
+            "extend_ms": ems, "extend_seeds_per_s": nreg / (ems / 1000),
+            "region_bases": int(span), "mean_region_bases": float(span / max(nreg, 1)),
+            "chain2_ms": cms, "chain2_regions_per_s": nreg / (cms / 1000),
+            "chain2_query_mbp_s": span / (cms / 1000) / 1e6, "sds": int(nsd)}
+
+
 # ------------------------------------------------------------- main arm --
 
 def timed_steps(stream, flush, steps, warmup, fn):
@@ -513,6 +565,11 @@ def run_workload(args):
     kept = int((binding.struct_view(out["runs"], binding.RUN_DTYPE)["keep"] == 1).sum())
     qgram_info = {"q": 4, "p_gap": 0.005, "ms": sum(qms) / len(qms), "kept_seeds": kept,
                   "passed": int(npass), "bytes_per_seed": 2 * p.n // 4}
+    # ---- the next steps of the method on a sample of the pass's seeds
+    try:
+        ext_info = None if args.no_extension else measure_extension(ctx, out, W, p, d_seq, stream)
+    except binding.SedefError as e:
+        ext_info = {"error": str(e)}
 
     # ---- the same pass as one captured graph (sedef_graph_*)
     graph_info = None
@@ -635,6 +692,7 @@ def run_workload(args):
         "clocks": clk,
         "graph": graph_info,
         "qgram": qgram_info,
+        "extension_and_chain2": ext_info,
         "kernels": kernels,
     }
     print(json.dumps(line), flush=True)
@@ -659,6 +717,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-graph", action="store_true", help="skip the captured-graph measurement")
     ap.add_argument("--no-plain", action="store_true", help="batch: skip the one-pass-per-genome form")
+    ap.add_argument("--no-extension", action="store_true",
+                    help="skip the extension / two-tier chaining measurement")
     ap.add_argument("--genomes", type=int, default=None,
                     help="batch: only the first N genomes of the batch (smaller runs, e.g. profiling)")
     ap.add_argument("--variant", type=int, default=None,
