@@ -200,6 +200,21 @@ int sedef_set_stream(sedef_ctx* ctx, void* stream);
 int sedef_set_scratch_limit(sedef_ctx* ctx, int64_t bytes);
 
 /*
+ * Caps the shared memory per CTA that the filter's shared-memory tiers of
+ * this context may ask for (< 0: no cap, the default).  The second wide
+ * tier (about 213 KB per CTA) is left out when it is above the cap, and the
+ * wide tier hands the windows it cannot hold straight to the global path,
+ * so the results do not change.  The other tiers need at most 100 KB per CTA
+ * and always run: a cap below 100 KB (102,400 bytes) is refused with
+ * SEDEF_ERR_UNSUPPORTED.  For a context whose
+ * kernels run beside a persistent kernel (sedef_server_create): an SM keeps
+ * its L1 / shared-memory split while any CTA stays on it, so a kernel that
+ * needs more shared memory than the persistent kernel leaves waits until
+ * that kernel exits.  No GPU work.
+ */
+int sedef_set_tier_smem_limit(sedef_ctx* ctx, int64_t bytes);
+
+/*
  * Tracing.  While enabled, every kernel the context launches is bracketed by
  * CUDA events on the context's stream.  sedef_trace_report synchronizes the
  * stream and writes one line per kernel name, "name launches total_ms", in
@@ -537,8 +552,18 @@ int sedef_graph_destroy(sedef_graph* g);
  * leaves; when all have left that way sedef_server_status returns
  * SEDEF_ERR_TIMEOUT (running = 0, timed_out = 1), and the next submit or
  * poll launches the kernel again.  submit may run on one host thread while
- * poll and finish run on another; each of the three is not reentrant.
+ * poll runs on another; submit and poll are not reentrant.  finish may run
+ * on several threads at once for different slots: up to three calls work at
+ * the same time, each on its own stream, and further calls wait for one of
+ * them to return.  The kernel keeps a window with more than 4,096 hits for
+ * finish, which runs the wide shared-memory tier over such windows.
  * sedef_server_destroy stops the kernel and frees the server.
+ * The persistent kernel asks for the largest L1 / shared-memory split and
+ * keeps 62 KB of shared memory on every SM while it runs; a kernel of
+ * another stream that needs more than what is left waits for it to leave.
+ * sedef_server_smem_left gives that bound (bytes per CTA); finish keeps its
+ * own filter tiers within it, and a context that runs beside the server
+ * should do the same (sedef_set_tier_smem_limit).
  */
 typedef struct sedef_server sedef_server;
 int sedef_server_create(sedef_ctx* ctx, const uint64_t* d_trec, const uint64_t* d_tsorted,
@@ -550,6 +575,7 @@ int sedef_server_poll(sedef_server* s, double wait_s, int32_t* slot_out);
 int sedef_server_finish(sedef_server* s, int32_t slot, sedef_cand_t* h_cands, int64_t cap,
                         int64_t* h_ncands);
 int sedef_server_status(sedef_server* s, int32_t* running, int32_t* timed_out);
+int sedef_server_smem_left(sedef_server* s, int64_t* bytes);
 int sedef_server_destroy(sedef_server* s);
 
 #ifdef __cplusplus

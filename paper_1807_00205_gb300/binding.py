@@ -45,7 +45,8 @@ class Params(ctypes.Structure):
 
 
 EXPORTS = ["sedef_default_params", "sedef_last_error", "sedef_create", "sedef_destroy",
-           "sedef_set_stream", "sedef_set_scratch_limit", "sedef_trace_enable", "sedef_trace_report", "sedef_launch_count", "sedef_filter_stats",
+           "sedef_set_stream", "sedef_set_scratch_limit", "sedef_set_tier_smem_limit",
+           "sedef_trace_enable", "sedef_trace_report", "sedef_launch_count", "sedef_filter_stats",
            "sedef_threshold_table", "sedef_pack", "sedef_sketch", "sedef_sketch_noalloc",
            "sedef_index", "sedef_filter", "sedef_filter_autotune", "sedef_filter_variant",
            "sedef_chain", "sedef_extend", "sedef_chain2", "sedef_merge", "sedef_selfsearch",
@@ -54,7 +55,8 @@ EXPORTS = ["sedef_default_params", "sedef_last_error", "sedef_create", "sedef_de
            "sedef_index_save", "sedef_index_blob_info", "sedef_index_load", "sedef_graph_create",
            "sedef_graph_launch", "sedef_graph_wait", "sedef_graph_nodes", "sedef_graph_destroy",
            "sedef_qgram", "sedef_server_create", "sedef_server_submit", "sedef_server_poll",
-           "sedef_server_finish", "sedef_server_status", "sedef_server_destroy"]
+           "sedef_server_finish", "sedef_server_status", "sedef_server_smem_left",
+           "sedef_server_destroy"]
 
 CAP_NAMES = ["records", "slow_hits", "runs", "anchors", "chains", "cands"]
 
@@ -88,6 +90,7 @@ def load(build_if_missing: bool = True):
     lib.sedef_destroy.argtypes = [vp]
     lib.sedef_set_stream.argtypes = [vp, vp]
     lib.sedef_set_scratch_limit.argtypes = [vp, i64]
+    lib.sedef_set_tier_smem_limit.argtypes = [vp, i64]
     lib.sedef_threshold_table.argtypes = [P, vp, i32, ctypes.POINTER(ctypes.c_double)]
     lib.sedef_pack.argtypes = [vp, vp, i64, vp, vp, vp]
     lib.sedef_sketch.argtypes = [vp, vp, vp, vp, vp, i32, P, vp, i64, ctypes.POINTER(i64)]
@@ -127,6 +130,7 @@ def load(build_if_missing: bool = True):
     lib.sedef_server_poll.argtypes = [vp, ctypes.c_double, ctypes.POINTER(i32)]
     lib.sedef_server_finish.argtypes = [vp, i32, vp, i64, ctypes.POINTER(i64)]
     lib.sedef_server_status.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.sedef_server_smem_left.argtypes = [vp, ctypes.POINTER(i64)]
     lib.sedef_server_destroy.argtypes = [vp]
     lib.sedef_trace_enable.argtypes = [vp, ctypes.c_int]
     lib.sedef_trace_report.argtypes = [vp, ctypes.c_char_p, i64, ctypes.c_int]
@@ -222,6 +226,10 @@ class Context:
     def sedef_set_scratch_limit(self, nbytes: int):
         """Caps the context's device scratch (< 0: no cap)."""
         _check(self.lib.sedef_set_scratch_limit(self.handle, int(nbytes)))
+
+    def sedef_set_tier_smem_limit(self, nbytes: int):
+        """Caps the shared memory per CTA of the filter tiers (< 0: no cap)."""
+        _check(self.lib.sedef_set_tier_smem_limit(self.handle, int(nbytes)))
 
     # -- tracing ----------------------------------------------------------------
 
@@ -660,6 +668,13 @@ class DeviceServer:
         run, tmo = ctypes.c_int32(), ctypes.c_int32()
         st = self.lib.sedef_server_status(self.handle, ctypes.byref(run), ctypes.byref(tmo))
         return {"status": st, "running": bool(run.value), "timed_out": bool(tmo.value)}
+
+    def smem_left(self) -> int:
+        """Shared memory per CTA that kernels of other streams find beside
+        the persistent kernel."""
+        n = ctypes.c_int64()
+        _check(self.lib.sedef_server_smem_left(self.handle, ctypes.byref(n)))
+        return n.value
 
     def close(self):
         if self.handle:

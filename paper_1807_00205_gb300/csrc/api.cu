@@ -4,6 +4,10 @@
 #include <cstring>
 #include <string>
 
+#include <mutex>
+#include <set>
+#include <tuple>
+
 #include "common.cuh"
 
 #include <atomic>
@@ -28,6 +32,9 @@ struct sedef_ctx {
   std::vector<cudaEvent_t> spare;  // recycled events
   int64_t filter_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int filter_variant = 0;  // first-tier filter shape (sedef_filter_autotune)
+  // shared memory a filter tier's CTA may ask for (a context whose kernels
+  // run beside a persistent kernel leaves out the tiers that cannot fit)
+  size_t tier_smem_cap = SIZE_MAX;
   // run count of the last whole self-search (its run buffer's first size
   // next time, so that a repeated search does not rerun the filter)
   int64_t last_runs = 0;
@@ -99,6 +106,19 @@ void Pool::release() {
   blocks.clear();
 }
 
+int ensure_smem_attr(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::set<std::tuple<int, const void*, size_t>> done;
+  int dev = 0;
+  SEDEF_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> g(mu);
+  const auto key = std::make_tuple(dev, kernel, bytes);
+  if (done.count(key)) return SEDEF_OK;
+  SEDEF_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  done.insert(key);
+  return SEDEF_OK;
+}
+
 static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -151,6 +171,8 @@ const char* ctx_set_stage(sedef_ctx* ctx, const char* stage) {
 
 int ctx_filter_variant(sedef_ctx* ctx) { return ctx->filter_variant; }
 void ctx_set_filter_variant(sedef_ctx* ctx, int v) { ctx->filter_variant = v; }
+size_t ctx_tier_smem_cap(sedef_ctx* ctx) { return ctx->tier_smem_cap; }
+void ctx_set_tier_smem_cap(sedef_ctx* ctx, size_t bytes) { ctx->tier_smem_cap = bytes; }
 
 void ctx_set_stats(sedef_ctx* ctx, const int64_t* v, int n) {
   for (int x = 0; x < 7; ++x) ctx->filter_stats[x] = x < n ? v[x] : 0;
@@ -357,6 +379,16 @@ int sedef_set_scratch_limit(sedef_ctx* ctx, int64_t bytes) {
     ctx->io.release();
   }
   ctx->scratch_limit = bytes < 0 ? SIZE_MAX : (size_t)bytes;
+  return SEDEF_OK;
+}
+
+int sedef_set_tier_smem_limit(sedef_ctx* ctx, int64_t bytes) {
+  if (!ctx) return fail(SEDEF_ERR_INVALID, "ctx is NULL");
+  if (bytes >= 0 && bytes < kTierSmemFloor)
+    return fail(SEDEF_ERR_UNSUPPORTED,
+                "sedef_set_tier_smem_limit: the filter tiers other than the second wide tier "
+                "need up to 100 KB per CTA");
+  ctx->tier_smem_cap = bytes < 0 ? SIZE_MAX : (size_t)bytes;
   return SEDEF_OK;
 }
 

@@ -280,4 +280,15 @@ void ctx_set_stats(sedef_ctx* ctx, const int64_t* v, int n);  // last sedef_filt
 void ctx_set_anchor_total(sedef_ctx* ctx, int64_t a);         // last sedef_chain call
 int ctx_filter_variant(sedef_ctx* ctx);
 void ctx_set_filter_variant(sedef_ctx* ctx, int v);
+// Largest shared memory per CTA that run_filter's tiers may use (default:
+// no limit); a tier above it is left out and its windows go on to the next.
+// Sets a kernel's dynamic shared-memory limit on the current device the
+// first time it is asked for there (thread-safe; the attribute belongs to
+// the device's context, so each device is set once).
+int ensure_smem_attr(const void* kernel, size_t bytes);
+size_t ctx_tier_smem_cap(sedef_ctx* ctx);
+// Every tier but the second wide one fits in this much shared memory per CTA
+// (checked where the tiers are defined).
+constexpr int64_t kTierSmemFloor = 100 * 1024;
+void ctx_set_tier_smem_cap(sedef_ctx* ctx, size_t bytes);
 }  // namespace sedef

@@ -536,7 +536,7 @@ int run_extend(sedef_ctx* ctx, const sedef_run_t* runs, int64_t nruns, const uin
   a.next = next;
   a.out = out;
   const size_t sm = (size_t)kExtWarps * (a.sum_words * 4 + sizeof(ExtSmem));
-  SEDEF_CUDA(cudaFuncSetAttribute(k_extend, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  SEDEF_TRY(ensure_smem_attr((const void*)k_extend, sm));
   SEDEF_KERNEL(ctx, "k_extend", k_extend<<<(int)ctas, 32 * kExtWarps, sm, st>>>(a));
   SEDEF_CUDA(cudaStreamSynchronize(st));
   return SEDEF_OK;

@@ -32,6 +32,7 @@
 // breakpoint.  Runs whose domain exceeds the batched kernel's slots go to
 // k_refine (one warp per run, bitsets over the sorted domain).
 #include <chrono>
+#include <condition_variable>
 #include <cstring>
 #include <mutex>
 #include <thread>
@@ -878,12 +879,7 @@ __global__ void __launch_bounds__(32 * kWWarps) k_filter_warp(FArgs a, TierIO io
 int launch_warp_tier(sedef_ctx* ctx, const FArgs& a, const TierIO& io, int64_t max_windows,
                      const char* name) {
   const size_t sm = sizeof(WarpSmem) * kWWarps;
-  static bool attr = false;
-  if (!attr) {
-    SEDEF_CUDA(cudaFuncSetAttribute(k_filter_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)sm));
-    attr = true;
-  }
+  SEDEF_TRY(ensure_smem_attr((const void*)k_filter_warp, sm));
   int per_sm = 0;
   SEDEF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_filter_warp, 32 * kWWarps, sm));
   if (per_sm < 1) per_sm = 1;
@@ -2021,12 +2017,7 @@ int launch_fast(sedef_ctx* ctx, const FArgs& a, const TierIO& io_in, int64_t max
   const size_t sm = sizeof(FastSmemT<TPB, LCAP, GCAP, SLOTS>);
   static_assert(sizeof(FastSmemT<TPB, LCAP, GCAP, SLOTS>) <= 227 * 1024,
                 "a filter tier must fit one CTA's shared memory");
-  static bool attr = false;  // one per instantiation
-  if (!attr) {
-    SEDEF_CUDA(cudaFuncSetAttribute(k_filter_fast<TPB, LCAP, GCAP, SLOTS>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    attr = true;
-  }
+  SEDEF_TRY(ensure_smem_attr((const void*)k_filter_fast<TPB, LCAP, GCAP, SLOTS>, sm));
   // a table of SLOTS counters keeps its aliasing low up to 2 * SLOTS hits;
   // windows with more go on (to the wide tier when the caller names one)
   TierIO io = io_in;
@@ -2063,6 +2054,10 @@ constexpr int kNumTier2 = 3;
 constexpr int kWideSlots = 32768;
 const FastLaunch kTierWide = launch_fast<512, 2048, 512, kWideSlots>;
 const FastLaunch kTierWide2 = launch_fast<512, 16384, 1024, kWideSlots>;
+static_assert(sizeof(FastSmemT<512, 8192, 2048, 2048>) <= kTierSmemFloor &&
+                  sizeof(FastSmemT<512, 2048, 512, kWideSlots>) <= kTierSmemFloor &&
+                  sizeof(WarpSmem) * kWWarps <= kTierSmemFloor,
+              "a tier that always runs needs more shared memory than a tier cap may be");
 // variant = (warp tier off) * 12 + t1 * kNumTier2 + t2
 constexpr int kNumShapes = kNumTier1 * kNumTier2;
 constexpr int kNumVariants = 2 * kNumShapes;
@@ -2151,15 +2146,9 @@ int order_and_refine(sedef_ctx* ctx, const FArgs& a, const Derived& D, int nqseq
                      const uint32_t* toff, unsigned long long* counters, sedef_run_t* raw,
                      int64_t total, sedef_run_t* runs, const uint32_t* druns, const uint32_t* dnt) {
   cudaStream_t st = ctx_stream(ctx);
-  static bool attr = false;  // the refine kernels' shared memory, once per process
-  if (!attr) {
-    SEDEF_CUDA(cudaFuncSetAttribute(k_refine_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(sizeof(BatchWarp) * kBWarps)));
-    SEDEF_CUDA(cudaFuncSetAttribute(k_refine<kMaxWindowRecs, 1024, false>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(sizeof(RefineWarpT<kMaxWindowRecs, 1024>) * kRWarpsBig)));
-    attr = true;
-  }
+  SEDEF_TRY(ensure_smem_attr((const void*)k_refine_batch, sizeof(BatchWarp) * kBWarps));
+  SEDEF_TRY(ensure_smem_attr((const void*)k_refine<kMaxWindowRecs, 1024, false>,
+                             sizeof(RefineWarpT<kMaxWindowRecs, 1024>) * kRWarpsBig));
   // order runs by (i, o); the sweep emits each window's runs in j order
   ctx_set_stage(ctx, "runsort");
   uint64_t* keys = (uint64_t*)ctx_alloc(ctx, (size_t)total * 8);
@@ -2429,12 +2418,15 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
     io2.wide_list = ovlw;
     io2.wide_count = (unsigned int*)(counters + 14);
     SEDEF_TRY(kTier2[sh % kNumTier2](ctx, a, io2, nwin, "k_filter_mid"));
-    TierIO iow{ovlw, (const unsigned int*)(counters + 14), ovlw2, (unsigned int*)(counters + 16),
-               (unsigned int*)(counters + 15), 1};
+    // the second wide tier is left out where its CTA would not fit; the
+    // wide tier then hands its leftovers straight to the global path
+    const bool wide2 = sizeof(FastSmemT<512, 16384, 1024, kWideSlots>) <= ctx_tier_smem_cap(ctx);
+    TierIO iow{ovlw, (const unsigned int*)(counters + 14), wide2 ? ovlw2 : ovl,
+               (unsigned int*)(counters + (wide2 ? 16 : 1)), (unsigned int*)(counters + 15), 1};
     SEDEF_TRY(kTierWide(ctx, a, iow, nwin, "k_filter_wide"));
     TierIO iow2{ovlw2, (const unsigned int*)(counters + 16), ovl, (unsigned int*)(counters + 1),
                 (unsigned int*)(counters + 17), 1};
-    SEDEF_TRY(kTierWide2(ctx, a, iow2, nwin, "k_filter_wide2"));
+    if (wide2) SEDEF_TRY(kTierWide2(ctx, a, iow2, nwin, "k_filter_wide2"));
   }
 
   unsigned long long* h_cnt = nullptr;
@@ -2559,6 +2551,13 @@ constexpr int kServeMaxSlots = 64;
 // which would otherwise wait for the persistent kernel to leave.
 constexpr int kServeTPB = 256, kServeLCap = 2048, kServeGCap = 512, kServeSlots = 16384;
 using ServeSmem = FastSmemT<kServeTPB, kServeLCap, kServeGCap, kServeSlots>;
+// Windows with more hits than this go to the slot's wide list before their
+// hits are enumerated; the finishing call runs the wide tier (512 threads,
+// 32,768 counters) over them as an ordinary launch beside k_serve, as the
+// first tier of a whole-genome pass hands them on.
+constexpr uint32_t kServeHlim = 2 * kSlots;
+// Finishing calls that may run at once (each on its own stream and context).
+constexpr int kServeFinishers = 3;
 
 struct ServeItem {
   uint32_t slot, window;
@@ -2578,6 +2577,8 @@ struct ServeCtl {
 struct SlotDev {
   FArgs a;              // the slot's query, windows and outputs
   unsigned int* done;   // windows finished (reset at admission)
+  uint32_t* wide_list;  // windows with more hits than k_serve keeps (for the wide tier)
+  unsigned int* wide_count;
 };
 
 struct ServeArgs {
@@ -2652,6 +2653,9 @@ __global__ void __launch_bounds__(kServeTPB) k_serve(ServeArgs sv) {
     io.out_count = sd.a.nov;
     io.next = nullptr;
     io.stats = 1;
+    io.hlim = kServeHlim;
+    io.wide_list = sd.wide_list;
+    io.wide_count = sd.wide_count;
     fast_window<kServeTPB, kServeLCap, kServeGCap, kServeSlots>(sd.a, io, S, (int64_t)s_window);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -2683,10 +2687,17 @@ struct Server {
   const uint32_t* toff = nullptr;
   int64_t nt = 0;
   std::vector<int64_t> h_toff;
-  // streams and contexts: admission, the persistent kernel, finishing
-  cudaStream_t s_prep = nullptr, s_kern = nullptr, s_fin = nullptr;
+  // streams and contexts: admission, the persistent kernel, finishing (one
+  // stream and context per concurrent sedef_server_finish call)
+  cudaStream_t s_prep = nullptr, s_kern = nullptr;
   sedef_ctx* c_prep = nullptr;
-  sedef_ctx* c_fin = nullptr;
+  struct Finisher {
+    cudaStream_t stream = nullptr;
+    sedef_ctx* ctx = nullptr;
+    bool busy = false;
+  };
+  std::vector<Finisher> fins;
+  std::condition_variable fin_cv;
   cudaEvent_t kern_done = nullptr;
   bool kern_launched = false;
   char* d_shared = nullptr;  // target offsets and the m table
@@ -2705,7 +2716,7 @@ struct Server {
     uint32_t *packed = nullptr, *mask = nullptr, *nbits = nullptr;
     uint64_t* qrec = nullptr;
     int64_t rec_cap = 0;
-    uint32_t *wi = nullptr, *wqa = nullptr, *wqb = nullptr, *ov = nullptr;
+    uint32_t *wi = nullptr, *wqa = nullptr, *wqb = nullptr, *ov = nullptr, *wl = nullptr;
     int32_t* wseq = nullptr;
     int64_t win_cap = 0;
     sedef_run_t* raw = nullptr;
@@ -2727,6 +2738,13 @@ struct Server {
 };
 
 namespace {
+
+// Shared memory per CTA that other kernels find on an SM beside one k_serve
+// CTA: the largest split (228 KB) less k_serve's block and the 1 KB the SM
+// reserves for each of the two CTAs.
+int64_t server_smem_left() { return 228 * 1024 - (int64_t)sizeof(ServeSmem) - 2 * 1024; }
+static_assert(228 * 1024 - sizeof(ServeSmem) - 2 * 1024 >= kTierSmemFloor,
+              "the finishing tiers must fit beside k_serve");
 
 int server_alloc(Server* s, void** p, size_t bytes) {
   if (cudaMalloc(p, bytes ? bytes : 256) != cudaSuccess) {
@@ -2754,9 +2772,7 @@ int server_kick(Server* s) {
   sv.ctl = s->d_ctl;
   sv.head = s->d_head;
   sv.idle_ns = (unsigned long long)(s->idle_s * 1e9);
-  const size_t sm = sizeof(ServeSmem);
-  SEDEF_CUDA(cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_serve<<<ctx_sm_count(s->c_prep), kServeTPB, sm, s->s_kern>>>(sv);
+  k_serve<<<ctx_sm_count(s->c_prep), kServeTPB, sizeof(ServeSmem), s->s_kern>>>(sv);
   count_launch();
   SEDEF_LAUNCHED("k_serve");
   SEDEF_CUDA(cudaEventRecord(s->kern_done, s->s_kern));
@@ -2818,16 +2834,19 @@ int sedef_server_destroy(sedef_server* srv) {
     if (s->kern_launched) cudaEventSynchronize(s->kern_done);
   }
   if (s->s_prep) cudaStreamSynchronize(s->s_prep);
-  if (s->s_fin) cudaStreamSynchronize(s->s_fin);
+  for (auto& F : s->fins)
+    if (F.stream) cudaStreamSynchronize(F.stream);
   if (s->c_prep) sedef_destroy(s->c_prep);
-  if (s->c_fin) sedef_destroy(s->c_fin);
+  for (auto& F : s->fins)
+    if (F.ctx) sedef_destroy(F.ctx);
   for (void* p : s->dev_allocs) cudaFree(p);
   if (s->ctl) cudaFreeHost(s->ctl);
   if (s->ring) cudaFreeHost(s->ring);
   if (s->kern_done) cudaEventDestroy(s->kern_done);
   if (s->s_prep) cudaStreamDestroy(s->s_prep);
   if (s->s_kern) cudaStreamDestroy(s->s_kern);
-  if (s->s_fin) cudaStreamDestroy(s->s_fin);
+  for (auto& F : s->fins)
+    if (F.stream) cudaStreamDestroy(F.stream);
   delete s;
   return SEDEF_OK;
 }
@@ -2873,23 +2892,43 @@ int sedef_server_create(sedef_ctx* ctx, const uint64_t* d_trec, const uint64_t* 
   s->h_toff.assign(h_toff, h_toff + ntseq + 1);
   s->mtab.resize(kMaxWindowRecs + 1);
   mtable(p, s->mtab.data(), kMaxWindowRecs, nullptr);
-  if (cudaStreamCreateWithFlags(&s->s_prep, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->s_kern, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->s_fin, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s->kern_done, cudaEventDisableTiming) != cudaSuccess) {
+  s->fins.resize(kServeFinishers);
+  bool made = cudaStreamCreateWithFlags(&s->s_prep, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&s->s_kern, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&s->kern_done, cudaEventDisableTiming) == cudaSuccess;
+  for (auto& F : s->fins)
+    made = made && cudaStreamCreateWithFlags(&F.stream, cudaStreamNonBlocking) == cudaSuccess;
+  if (!made) {
     cudaGetLastError();
     return bail(fail(SEDEF_ERR_CUDA, "sedef_server_create: stream or event creation failed"));
   }
   int st = sedef_create(s->device, s->s_prep, &s->c_prep);
-  if (st == SEDEF_OK) st = sedef_create(s->device, s->s_fin, &s->c_fin);
   if (st == SEDEF_OK) st = sedef_set_scratch_limit(s->c_prep, ctx_scratch_limit(ctx));
-  if (st == SEDEF_OK) st = sedef_set_scratch_limit(s->c_fin, ctx_scratch_limit(ctx));
   // admission and finishing run beside the persistent kernel: nothing they
   // allocate may wait for it
   if (st == SEDEF_OK) st = ctx_use_stream_ordered_alloc(s->c_prep);
-  if (st == SEDEF_OK) st = ctx_use_stream_ordered_alloc(s->c_fin);
+  for (auto& F : s->fins) {
+    if (st == SEDEF_OK) st = sedef_create(s->device, F.stream, &F.ctx);
+    if (st == SEDEF_OK) st = sedef_set_scratch_limit(F.ctx, ctx_scratch_limit(ctx));
+    if (st == SEDEF_OK) st = ctx_use_stream_ordered_alloc(F.ctx);
+    if (st != SEDEF_OK) break;
+    ctx_set_filter_variant(F.ctx, ctx_filter_variant(ctx));
+    // the finishing tiers keep to the shared memory left beside k_serve
+    ctx_set_tier_smem_cap(F.ctx, (size_t)server_smem_left());
+  }
   if (st != SEDEF_OK) return bail(st);
-  ctx_set_filter_variant(s->c_fin, ctx_filter_variant(ctx));
+  // An SM splits its unified L1 / shared memory when a CTA arrives on an
+  // idle SM and keeps the split while any CTA stays.  The persistent kernel
+  // stays, so it asks for the largest shared-memory split: the other
+  // streams' kernels then find 228 - 63 KB per SM (the large refine kernel
+  // takes 125 KB) instead of waiting for the persistent kernel to leave.
+  if (cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(ServeSmem)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_serve, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(SEDEF_ERR_CUDA, "sedef_server_create: kernel attributes refused"));
+  }
   const size_t up = (size_t)(ntseq + 1) * 8 + (size_t)(kMaxWindowRecs + 1) * 4;
   if ((st = server_alloc(s, (void**)&s->d_shared, up)) != SEDEF_OK) return bail(st);
   if (cudaMemcpy(s->d_shared, h_toff, (size_t)(ntseq + 1) * 8, cudaMemcpyHostToDevice) !=
@@ -2934,14 +2973,15 @@ int sedef_server_create(sedef_ctx* ctx, const uint64_t* d_trec, const uint64_t* 
     SALLOC(mask, uint32_t*, ((slot_bases + 31) / 32) * 4);
     SALLOC(nbits, uint32_t*, ((slot_bases + 31) / 32) * 4);
     SALLOC(qrec, uint64_t*, L.rec_cap * 8);
-    SALLOC(wi, uint32_t*, win_cap * 4 * 5);
+    SALLOC(wi, uint32_t*, win_cap * 4 * 6);
     SALLOC(raw, sedef_run_t*, L.run_cap * (int64_t)sizeof(sedef_run_t));
     SALLOC(counters, unsigned long long*, 256 + 64 + 64);
 #undef SALLOC
     L.wqa = L.wi + win_cap;
     L.wqb = L.wqa + win_cap;
     L.ov = L.wqb + win_cap;
-    L.wseq = (int32_t*)(L.ov + win_cap);
+    L.wl = L.ov + win_cap;
+    L.wseq = (int32_t*)(L.wl + win_cap);
     L.done = (unsigned int*)((char*)L.counters + 256);
     L.d_up = (char*)L.counters + 256 + 64;
     FArgs& a = L.a;
@@ -2975,6 +3015,8 @@ int sedef_server_create(sedef_ctx* ctx, const uint64_t* d_trec, const uint64_t* 
     a.stats = L.counters + 4;
     sdev[k].a = a;
     sdev[k].done = L.done;
+    sdev[k].wide_list = L.wl;
+    sdev[k].wide_count = (unsigned int*)(L.counters + 14);
   }
   if (cudaMemcpy(s->d_slots, sdev.data(), sizeof(SlotDev) * slots, cudaMemcpyHostToDevice) !=
       cudaSuccess)
@@ -3081,8 +3123,32 @@ int sedef_server_finish(sedef_server* srv, int32_t slot, sedef_cand_t* h_cands, 
     return SEDEF_OK;
   }
   SEDEF_CUDA(cudaSetDevice(s->device));
-  sedef_ctx* c = s->c_fin;
-  cudaStream_t st = s->s_fin;
+  // a free finishing stream and context, held for the whole call
+  struct FinLease {
+    Server* s;
+    Server::Finisher* f = nullptr;
+    explicit FinLease(Server* sv) : s(sv) {
+      std::unique_lock<std::mutex> g(s->mu);
+      s->fin_cv.wait(g, [&] {
+        for (auto& F : s->fins)
+          if (!F.busy) {
+            F.busy = true;
+            f = &F;
+            return true;
+          }
+        return false;
+      });
+    }
+    ~FinLease() {
+      {
+        std::lock_guard<std::mutex> g(s->mu);
+        f->busy = false;
+      }
+      s->fin_cv.notify_one();
+    }
+  } lease(s);
+  sedef_ctx* c = lease.f->ctx;
+  cudaStream_t st = lease.f->stream;
   ctx_pool_reset(c);
   auto release = [&](int status) {
     std::lock_guard<std::mutex> g(s->mu);
@@ -3092,6 +3158,16 @@ int sedef_server_finish(sedef_server* srv, int32_t slot, sedef_cand_t* h_cands, 
   const int64_t qoff[2] = {0, L.len};
   int64_t nc = 0;
   if (L.nwin > 0) {
+    {
+      // the windows k_serve handed on for their many hits: the wide tier,
+      // as an ordinary launch beside k_serve; what it cannot hold joins the
+      // slot's overflow list
+      StageScope stage(c, "filter");
+      TierIO iow{L.wl, (const unsigned int*)(L.counters + 14), L.ov,
+                 (unsigned int*)(L.counters + 1), (unsigned int*)(L.counters + 15), 1};
+      const int wst = kTierWide(c, L.a, iow, L.nwin, "k_filter_wide");
+      if (wst != SEDEF_OK) return release(wst);
+    }
     unsigned long long* h_cnt = (unsigned long long*)ctx_host(c, 64);
     if (!h_cnt) return release(SEDEF_ERR_OOM);
     if (cudaMemcpyAsync(h_cnt, L.counters, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -3169,6 +3245,12 @@ int sedef_server_finish(sedef_server* srv, int32_t slot, sedef_cand_t* h_cands, 
     return release(fail(SEDEF_ERR_CUDA, "sedef_server_finish: stream failed"));
   *h_ncands = nc;
   return release(SEDEF_OK);
+}
+
+int sedef_server_smem_left(sedef_server* srv, int64_t* bytes) {
+  if (!srv || !bytes) return sedef::fail(SEDEF_ERR_INVALID, "NULL argument");
+  *bytes = sedef::server_smem_left();
+  return SEDEF_OK;
 }
 
 int sedef_server_status(sedef_server* srv, int32_t* running, int32_t* timed_out) {

@@ -140,12 +140,7 @@ extern "C" int sedef_qgram(sedef_ctx* ctx, const uint32_t* d_packed, const uint3
   SEDEF_CUDA(cudaMemsetAsync(cnt, 0, 8, st));
   A.npass = cnt;
   const size_t smem = (size_t)kQgWarps * 2 * (size_t(1) << (2 * q)) * 4;
-  static bool attr = false;
-  if (!attr) {
-    SEDEF_CUDA(cudaFuncSetAttribute(k_qgram, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(kQgWarps * 2 * kMaxBins * 4)));
-    attr = true;
-  }
+  SEDEF_TRY(ensure_smem_attr((const void*)k_qgram, (size_t)kQgWarps * 2 * kMaxBins * 4));
   int64_t grid = (nruns + kQgWarps - 1) / kQgWarps;
   if (grid > (int64_t)ctx_sm_count(ctx) * 8) grid = (int64_t)ctx_sm_count(ctx) * 8;
   SEDEF_KERNEL(ctx, "k_qgram", k_qgram<<<(int)grid, 32 * kQgWarps, smem, st>>>(A));

@@ -270,13 +270,8 @@ int radix_sort_u64(sedef_ctx* ctx, const uint64_t* keys_in, const uint32_t* vals
   uint64_t* ktmp = (uint64_t*)ctx_alloc(ctx, (size_t)n * 8);
   uint32_t* vtmp = vals_out ? (uint32_t*)ctx_alloc(ctx, (size_t)n * 4) : nullptr;
   if (!hist || !hoff || !ktmp || (vals_out && !vtmp)) return SEDEF_ERR_OOM;
-  static bool attr_set = false;
   const size_t smem = sizeof(RsSmem);
-  if (!attr_set) {
-    SEDEF_CUDA(cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-    attr_set = true;
-  }
+  SEDEF_TRY(ensure_smem_attr((const void*)k_rs_scatter, smem));
   int64_t grid = ntiles;
   const int64_t maxgrid = (int64_t)ctx_sm_count(ctx) * 3;
   if (grid > maxgrid) grid = maxgrid;

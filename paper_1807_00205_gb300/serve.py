@@ -8,9 +8,12 @@ library's server (sedef_server_*).  A persistent filter kernel drains a work
 queue of query windows; an admission thread moves waiting requests into free
 request slots as slots free up (the slots are sized once, from free device
 memory), so a request that arrives while others are on the GPU joins the
-running kernel at once; a completion thread finishes every request whose
-windows are done (global path, refine, chaining, merging) on its own stream
-while the kernel keeps filtering the others.
+running kernel at once.  The kernel keeps the windows with at most 4,096
+hits and hands the heavier ones on; a completion thread polls for requests
+whose windows are done and passes each to one of three finishing threads,
+which run the rest on their own streams (the wide tier over the handed-on
+windows, the global path, refine, chaining, merging) while the kernel keeps
+filtering the others.
 
 Plain form (batching=False): one request per pass (pack ... merge) on one
 worker.  With several workers and batching=False each worker takes every
@@ -22,6 +25,7 @@ window is compared with the whole target independently of the others.
 from __future__ import annotations
 
 import collections
+import concurrent.futures
 import dataclasses
 import threading
 import time
@@ -144,6 +148,7 @@ class Server:
     (batching=True) or host workers (batching=False; see the module notes)."""
 
     SLOT_BYTES_PER_BASE = 32  # device bytes a request slot holds per query base
+    FINISHERS = 3             # sedef_server_finish calls that run at once
 
     def __init__(self, index: ResidentIndex, p: "binding.Params", workers: int = 2,
                  batching: bool = True, max_batch_bases: int = 64 << 20,
@@ -173,11 +178,14 @@ class Server:
                                             index.offsets, p, slots=self.nslots,
                                             slot_bases=slot_bases, idle_timeout_s=idle_timeout_s)
             self.inflight = {}
+            self.finishing = concurrent.futures.ThreadPoolExecutor(self.FINISHERS)
             self.threads = [threading.Thread(target=self._admit, daemon=True),
                             threading.Thread(target=self._complete, daemon=True)]
             self.ctxs = [self.ctx]
-            # a request longer than a slot goes through one plain pass
+            # a request longer than a slot goes through one plain pass, with
+            # filter tiers that fit beside the persistent kernel
             self.fallback = binding.Context(device, stream=torch.cuda.Stream(device))
+            self.fallback.sedef_set_tier_smem_limit(self.dev.smem_left())
             return
         self.admission = Admission(max_batch_bases if batching else 1, reserve_bytes,
                                    free_bytes_fn)
@@ -300,14 +308,20 @@ class Server:
             if r is None:
                 self.dev.finish(slot)  # an orphan (cannot happen): free its slot
                 continue
-            try:
-                c = self.dev.finish(slot)
-                c["qseq"] = 0
-                r.cands = c
-            except Exception as e:
-                r.error = f"{type(e).__name__}: {e}"
-                r.cands = None
-            self._done([r])
+            # finishing runs on its own threads (the library runs up to
+            # FINISHERS of them at once, each on its own stream), so polling
+            # goes on meanwhile
+            self.finishing.submit(self._finish_one, slot, r)
+
+    def _finish_one(self, slot: int, r: Request):
+        try:
+            c = self.dev.finish(slot)
+            c["qseq"] = 0
+            r.cands = c
+        except Exception as e:
+            r.error = f"{type(e).__name__}: {e}"
+            r.cands = None
+        self._done([r])
 
     # -- host workers ------------------------------------------------------
 
@@ -340,6 +354,7 @@ class Server:
             if t.is_alive():
                 t.join()
         if self.device_queue:
+            self.finishing.shutdown(wait=True)
             self.dev.close()
             self.fallback.close()
         for c in self.ctxs:

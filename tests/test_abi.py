@@ -101,6 +101,7 @@ def test_null_handles_are_refused_without_a_gpu():
                                                                    ctypes.byref(n64)),
         "sedef_set_stream": lambda: lib.sedef_set_stream(N, N),
         "sedef_set_scratch_limit": lambda: lib.sedef_set_scratch_limit(N, 0),
+        "sedef_set_tier_smem_limit": lambda: lib.sedef_set_tier_smem_limit(N, 0),
         "sedef_trace_enable": lambda: lib.sedef_trace_enable(N, 1),
         "sedef_trace_report": lambda: lib.sedef_trace_report(N, N, 0, 0),
         "sedef_index_save": lambda: lib.sedef_index_save(N, N, N, N, 0, 12, off, 1, N, 0),
@@ -115,6 +116,7 @@ def test_null_handles_are_refused_without_a_gpu():
         "sedef_server_poll": lambda: lib.sedef_server_poll(N, 0.0, ctypes.byref(n32)),
         "sedef_server_finish": lambda: lib.sedef_server_finish(N, 0, N, 0, ctypes.byref(n64)),
         "sedef_server_status": lambda: lib.sedef_server_status(N, N, N),
+        "sedef_server_smem_left": lambda: lib.sedef_server_smem_left(N, N),
         "sedef_threshold_table": lambda: lib.sedef_threshold_table(N, N, 0, N),
         "sedef_index_blob_info": lambda: lib.sedef_index_blob_info(N, 0, N, N, N),
     }

@@ -226,6 +226,22 @@ def test_wide_tier_long_postings(ctx):
                                    g.offsets, p)
         assert_rows_equal(run_rows(runs), ref["runs"], f"runs (shape {v})")
     ctx.sedef_filter_variant(0)
+    # with the second wide tier left out (the shared-memory cap of a context
+    # that runs beside the serving kernel) its windows go to the global path
+    with pytest.raises(binding.SedefError) as e:
+        ctx.sedef_set_tier_smem_limit(64 * 1024)
+    assert e.value.status == -5
+    for cap, wide2 in [(-1, True), (160 * 1024, False)]:
+        ctx.sedef_set_tier_smem_limit(cap)
+        ctx.sedef_trace_enable(True)
+        ctx.sedef_trace_report(reset=True)
+        runs, _ = ctx.sedef_filter(out["rec"], g.offsets, out["rec"], out["sorted"], out["off"],
+                                   g.offsets, p)
+        names = ctx.sedef_trace_report(reset=True)
+        ctx.sedef_trace_enable(False)
+        assert any(n.endswith("k_filter_wide2") for n in names) == wide2, sorted(names)
+        assert_rows_equal(run_rows(runs), ref["runs"], f"runs (tier cap {cap})")
+    ctx.sedef_set_tier_smem_limit(-1)
 
 
 def test_chain_refuses_degenerate_seeds(ctx):

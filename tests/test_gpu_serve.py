@@ -159,3 +159,40 @@ def test_device_queue_idle_wait_times_out_and_restarts():
     assert dev.status()["status"] in (0, -4)
     dev.close()
     ctx.close()
+
+
+def test_device_queue_finish_runs_beside_the_kernel():
+    """Dense winnowing (w = 5) sends runs to the refine kernel with the
+    largest shared-memory block (about 122 KB per CTA).  It must run on the
+    SMs beside the persistent kernel rather than wait for that kernel to
+    leave: with a 20 s idle limit the request still finishes in seconds, with
+    the result of the request searched alone."""
+    import time
+    need_gpu()
+    g = synth.small_case(90, lengths=(120_000,), n_sd=4, sd_lo=2000, sd_hi=6000, id_lo=0.92,
+                         mask_frac=0.1)
+    ctx = binding.Context(0)
+    p = binding.params(w=5)
+    index = serve.ResidentIndex(ctx, g.seq, g.offsets, p)
+    pool = synth.query_regions(g, 2, seed=11, len_lo=20_000, len_hi=40_000, mut_hi=0.05)
+    alone = _alone(ctx, index, pool, p)
+    assert ctx.sedef_filter_stats()["big_refine"] > 0
+    dev = binding.DeviceServer(ctx, index.trec, index.tsorted, index.toff, index.offsets, p,
+                               slots=2, slot_bases=50_000, idle_timeout_s=20.0)
+    assert dev.smem_left() >= 100 * 1024
+    for q, want in zip(pool, alone):
+        slot = dev.submit(q)
+        assert slot is not None
+        done = None
+        t0 = time.time()
+        while done is None and time.time() - t0 < 30:
+            done = dev.poll(0.01)
+        assert done == slot
+        c = dev.finish(slot)
+        took = time.time() - t0
+        assert dev.status()["running"]  # the kernel is still resident
+        c["qseq"] = 0
+        assert np.array_equal(c, want)
+        assert took < 5.0, took
+    dev.close()
+    ctx.close()
