@@ -201,10 +201,13 @@ int sedef_set_scratch_limit(sedef_ctx* ctx, int64_t bytes);
 
 /*
  * Caps the shared memory per CTA that the filter's shared-memory tiers of
- * this context may ask for (< 0: no cap, the default).  The second wide
- * tier (about 213 KB per CTA) is left out when it is above the cap, and the
- * wide tier hands the windows it cannot hold straight to the global path,
- * so the results do not change.  The other tiers need at most 100 KB per CTA
+ * this context may ask for (< 0: no cap, the default).  When the second
+ * wide tier (16,384 collected hits, about 213 KB per CTA) is above the cap,
+ * a form of it that holds 8,192 collected hits (about 150 KB) takes its
+ * place, and when that is above the cap too the wide tier hands the windows
+ * it cannot hold straight to the global path; the windows a smaller tier
+ * cannot hold go to the global path, so the results do not change.  The
+ * other tiers need at most 100 KB per CTA
  * and always run: a cap below 100 KB (102,400 bytes) is refused with
  * SEDEF_ERR_UNSUPPORTED.  For a context whose
  * kernels run beside a persistent kernel (sedef_server_create): an SM keeps
@@ -553,7 +556,7 @@ int sedef_graph_destroy(sedef_graph* g);
  * SEDEF_ERR_TIMEOUT (running = 0, timed_out = 1), and the next submit or
  * poll launches the kernel again.  submit may run on one host thread while
  * poll runs on another; submit and poll are not reentrant.  finish may run
- * on several threads at once for different slots: up to three calls work at
+ * on several threads at once for different slots: up to five calls work at
  * the same time, each on its own stream, and further calls wait for one of
  * them to return.  The kernel keeps a window with more than 4,096 hits for
  * finish, which runs the wide shared-memory tier over such windows.

@@ -2054,6 +2054,11 @@ constexpr int kNumTier2 = 3;
 constexpr int kWideSlots = 32768;
 const FastLaunch kTierWide = launch_fast<512, 2048, 512, kWideSlots>;
 const FastLaunch kTierWide2 = launch_fast<512, 16384, 1024, kWideSlots>;
+// The second wide tier in the form that fits beside the serving kernel
+// (8,192 collected hits instead of 16,384), for a context whose tier cap
+// leaves the full one out.
+const FastLaunch kTierWideMid = launch_fast<512, 8192, 1024, kWideSlots>;
+using WideMidSmem = FastSmemT<512, 8192, 1024, kWideSlots>;
 static_assert(sizeof(FastSmemT<512, 8192, 2048, 2048>) <= kTierSmemFloor &&
                   sizeof(FastSmemT<512, 2048, 512, kWideSlots>) <= kTierSmemFloor &&
                   sizeof(WarpSmem) * kWWarps <= kTierSmemFloor,
@@ -2418,15 +2423,20 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
     io2.wide_list = ovlw;
     io2.wide_count = (unsigned int*)(counters + 14);
     SEDEF_TRY(kTier2[sh % kNumTier2](ctx, a, io2, nwin, "k_filter_mid"));
-    // the second wide tier is left out where its CTA would not fit; the
-    // wide tier then hands its leftovers straight to the global path
-    const bool wide2 = sizeof(FastSmemT<512, 16384, 1024, kWideSlots>) <= ctx_tier_smem_cap(ctx);
-    TierIO iow{ovlw, (const unsigned int*)(counters + 14), wide2 ? ovlw2 : ovl,
-               (unsigned int*)(counters + (wide2 ? 16 : 1)), (unsigned int*)(counters + 15), 1};
+    // where the second wide tier's CTA would pass the context's cap, its
+    // 8,192-hit form takes its place, or, where that would pass it too, the
+    // wide tier hands its leftovers straight to the global path
+    const size_t scap = ctx_tier_smem_cap(ctx);
+    const bool wide2 = sizeof(FastSmemT<512, 16384, 1024, kWideSlots>) <= scap;
+    const bool mid = !wide2 && sizeof(WideMidSmem) <= scap;
+    const bool second = wide2 || mid;
+    TierIO iow{ovlw, (const unsigned int*)(counters + 14), second ? ovlw2 : ovl,
+               (unsigned int*)(counters + (second ? 16 : 1)), (unsigned int*)(counters + 15), 1};
     SEDEF_TRY(kTierWide(ctx, a, iow, nwin, "k_filter_wide"));
     TierIO iow2{ovlw2, (const unsigned int*)(counters + 16), ovl, (unsigned int*)(counters + 1),
                 (unsigned int*)(counters + 17), 1};
     if (wide2) SEDEF_TRY(kTierWide2(ctx, a, iow2, nwin, "k_filter_wide2"));
+    if (mid) SEDEF_TRY(kTierWideMid(ctx, a, iow2, nwin, "k_filter_widemid"));
   }
 
   unsigned long long* h_cnt = nullptr;
@@ -2557,7 +2567,7 @@ using ServeSmem = FastSmemT<kServeTPB, kServeLCap, kServeGCap, kServeSlots>;
 // first tier of a whole-genome pass hands them on.
 constexpr uint32_t kServeHlim = 2 * kSlots;
 // Finishing calls that may run at once (each on its own stream and context).
-constexpr int kServeFinishers = 3;
+constexpr int kServeFinishers = 5;
 
 struct ServeItem {
   uint32_t slot, window;
@@ -2579,6 +2589,8 @@ struct SlotDev {
   unsigned int* done;   // windows finished (reset at admission)
   uint32_t* wide_list;  // windows with more hits than k_serve keeps (for the wide tier)
   unsigned int* wide_count;
+  uint32_t* mid_list;   // windows k_serve could not hold (for the 8,192-hit tier)
+  unsigned int* mid_count;
 };
 
 struct ServeArgs {
@@ -2649,8 +2661,8 @@ __global__ void __launch_bounds__(kServeTPB) k_serve(ServeArgs sv) {
     TierIO io;
     io.in_list = nullptr;
     io.in_count = nullptr;
-    io.out_list = sd.a.ov_list;
-    io.out_count = sd.a.nov;
+    io.out_list = sd.mid_list;
+    io.out_count = sd.mid_count;
     io.next = nullptr;
     io.stats = 1;
     io.hlim = kServeHlim;
@@ -2716,7 +2728,8 @@ struct Server {
     uint32_t *packed = nullptr, *mask = nullptr, *nbits = nullptr;
     uint64_t* qrec = nullptr;
     int64_t rec_cap = 0;
-    uint32_t *wi = nullptr, *wqa = nullptr, *wqb = nullptr, *ov = nullptr, *wl = nullptr;
+    uint32_t *wi = nullptr, *wqa = nullptr, *wqb = nullptr, *ov = nullptr, *wl = nullptr,
+             *ml = nullptr;
     int32_t* wseq = nullptr;
     int64_t win_cap = 0;
     sedef_run_t* raw = nullptr;
@@ -2743,7 +2756,8 @@ namespace {
 // CTA: the largest split (228 KB) less k_serve's block and the 1 KB the SM
 // reserves for each of the two CTAs.
 int64_t server_smem_left() { return 228 * 1024 - (int64_t)sizeof(ServeSmem) - 2 * 1024; }
-static_assert(228 * 1024 - sizeof(ServeSmem) - 2 * 1024 >= kTierSmemFloor,
+static_assert(228 * 1024 - sizeof(ServeSmem) - 2 * 1024 >= kTierSmemFloor &&
+                  228 * 1024 - sizeof(ServeSmem) - 2 * 1024 >= sizeof(WideMidSmem),
               "the finishing tiers must fit beside k_serve");
 
 int server_alloc(Server* s, void** p, size_t bytes) {
@@ -2973,7 +2987,7 @@ int sedef_server_create(sedef_ctx* ctx, const uint64_t* d_trec, const uint64_t* 
     SALLOC(mask, uint32_t*, ((slot_bases + 31) / 32) * 4);
     SALLOC(nbits, uint32_t*, ((slot_bases + 31) / 32) * 4);
     SALLOC(qrec, uint64_t*, L.rec_cap * 8);
-    SALLOC(wi, uint32_t*, win_cap * 4 * 6);
+    SALLOC(wi, uint32_t*, win_cap * 4 * 7);
     SALLOC(raw, sedef_run_t*, L.run_cap * (int64_t)sizeof(sedef_run_t));
     SALLOC(counters, unsigned long long*, 256 + 64 + 64);
 #undef SALLOC
@@ -2981,7 +2995,8 @@ int sedef_server_create(sedef_ctx* ctx, const uint64_t* d_trec, const uint64_t* 
     L.wqb = L.wqa + win_cap;
     L.ov = L.wqb + win_cap;
     L.wl = L.ov + win_cap;
-    L.wseq = (int32_t*)(L.wl + win_cap);
+    L.ml = L.wl + win_cap;
+    L.wseq = (int32_t*)(L.ml + win_cap);
     L.done = (unsigned int*)((char*)L.counters + 256);
     L.d_up = (char*)L.counters + 256 + 64;
     FArgs& a = L.a;
@@ -3017,6 +3032,8 @@ int sedef_server_create(sedef_ctx* ctx, const uint64_t* d_trec, const uint64_t* 
     sdev[k].done = L.done;
     sdev[k].wide_list = L.wl;
     sdev[k].wide_count = (unsigned int*)(L.counters + 14);
+    sdev[k].mid_list = L.ml;
+    sdev[k].mid_count = (unsigned int*)(L.counters + 16);
   }
   if (cudaMemcpy(s->d_slots, sdev.data(), sizeof(SlotDev) * slots, cudaMemcpyHostToDevice) !=
       cudaSuccess)
@@ -3160,12 +3177,16 @@ int sedef_server_finish(sedef_server* srv, int32_t slot, sedef_cand_t* h_cands, 
   if (L.nwin > 0) {
     {
       // the windows k_serve handed on for their many hits: the wide tier,
-      // as an ordinary launch beside k_serve; what it cannot hold joins the
-      // slot's overflow list
+      // as an ordinary launch beside k_serve; what it cannot hold, and what
+      // k_serve could not hold, goes through the 8,192-hit wide tier, and
+      // what that cannot hold joins the slot's overflow list
       StageScope stage(c, "filter");
-      TierIO iow{L.wl, (const unsigned int*)(L.counters + 14), L.ov,
-                 (unsigned int*)(L.counters + 1), (unsigned int*)(L.counters + 15), 1};
-      const int wst = kTierWide(c, L.a, iow, L.nwin, "k_filter_wide");
+      TierIO iow{L.wl, (const unsigned int*)(L.counters + 14), L.ml,
+                 (unsigned int*)(L.counters + 16), (unsigned int*)(L.counters + 15), 1};
+      int wst = kTierWide(c, L.a, iow, L.nwin, "k_filter_wide");
+      TierIO iom{L.ml, (const unsigned int*)(L.counters + 16), L.ov,
+                 (unsigned int*)(L.counters + 1), (unsigned int*)(L.counters + 17), 1};
+      if (wst == SEDEF_OK) wst = kTierWideMid(c, L.a, iom, L.nwin, "k_filter_widemid");
       if (wst != SEDEF_OK) return release(wst);
     }
     unsigned long long* h_cnt = (unsigned long long*)ctx_host(c, 64);

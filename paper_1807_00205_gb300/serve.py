@@ -10,7 +10,7 @@ request slots as slots free up (the slots are sized once, from free device
 memory), so a request that arrives while others are on the GPU joins the
 running kernel at once.  The kernel keeps the windows with at most 4,096
 hits and hands the heavier ones on; a completion thread polls for requests
-whose windows are done and passes each to one of three finishing threads,
+whose windows are done and passes each to one of five finishing threads,
 which run the rest on their own streams (the wide tier over the handed-on
 windows, the global path, refine, chaining, merging) while the kernel keeps
 filtering the others.
@@ -148,7 +148,7 @@ class Server:
     (batching=True) or host workers (batching=False; see the module notes)."""
 
     SLOT_BYTES_PER_BASE = 32  # device bytes a request slot holds per query base
-    FINISHERS = 3             # sedef_server_finish calls that run at once
+    FINISHERS = 5             # sedef_server_finish calls that run at once
 
     def __init__(self, index: ResidentIndex, p: "binding.Params", workers: int = 2,
                  batching: bool = True, max_batch_bases: int = 64 << 20,

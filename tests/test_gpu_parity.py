@@ -226,12 +226,14 @@ def test_wide_tier_long_postings(ctx):
                                    g.offsets, p)
         assert_rows_equal(run_rows(runs), ref["runs"], f"runs (shape {v})")
     ctx.sedef_filter_variant(0)
-    # with the second wide tier left out (the shared-memory cap of a context
-    # that runs beside the serving kernel) its windows go to the global path
+    # under the shared-memory cap of a context that runs beside the serving
+    # kernel the second wide tier's smaller form takes its place, and under
+    # a lower cap its windows go to the global path
     with pytest.raises(binding.SedefError) as e:
         ctx.sedef_set_tier_smem_limit(64 * 1024)
     assert e.value.status == -5
-    for cap, wide2 in [(-1, True), (160 * 1024, False)]:
+    for cap, wide2, mid in [(-1, True, False), (160 * 1024, False, True),
+                            (100 * 1024, False, False)]:
         ctx.sedef_set_tier_smem_limit(cap)
         ctx.sedef_trace_enable(True)
         ctx.sedef_trace_report(reset=True)
@@ -240,6 +242,7 @@ def test_wide_tier_long_postings(ctx):
         names = ctx.sedef_trace_report(reset=True)
         ctx.sedef_trace_enable(False)
         assert any(n.endswith("k_filter_wide2") for n in names) == wide2, sorted(names)
+        assert any(n.endswith("k_filter_widemid") for n in names) == mid, sorted(names)
         assert_rows_equal(run_rows(runs), ref["runs"], f"runs (tier cap {cap})")
     ctx.sedef_set_tier_smem_limit(-1)
 
