@@ -159,9 +159,9 @@ __device__ __forceinline__ int64_t live_n(int64_t n, const uint32_t* d) {
 }
 
 // Record field access (layout in sedef.h).
-__device__ __forceinline__ uint32_t rec_hash(uint64_t r) { return (uint32_t)(r >> 33); }
-__device__ __forceinline__ uint32_t rec_pos(uint64_t r) { return (uint32_t)(r >> 1); }
-__device__ __forceinline__ uint32_t rec_strand(uint64_t r) { return (uint32_t)(r & 1u); }
+__host__ __device__ __forceinline__ uint32_t rec_hash(uint64_t r) { return (uint32_t)(r >> 33); }
+__host__ __device__ __forceinline__ uint32_t rec_pos(uint64_t r) { return (uint32_t)(r >> 1); }
+__host__ __device__ __forceinline__ uint32_t rec_strand(uint64_t r) { return (uint32_t)(r & 1u); }
 
 // Index of the sequence containing global position pos (offsets has nseq+1
 // entries, offsets[0] = 0).

@@ -61,6 +61,10 @@ struct FArgs {
   const uint32_t* win_qa;  // first query record of the window
   const uint32_t* win_qb;  // one past the last
   const int32_t* win_seq;  // query sequence of the window
+  // per query record: its hash's posting range narrowed to the record's own
+  // genome (batch self-search), or (kNone, 0) when the list passes max_occ;
+  // nullptr when the tiers look postings up themselves
+  const uint2* qpost;
   int64_t nwin;
   int ntseq, nqseq;
   int64_t ttotal;  // target total length
@@ -303,21 +307,118 @@ struct QBuild {
 
 // Postings of hash h restricted to target positions [lo, hi) (binary
 // searches inside the posting list, which is sorted by position).
-__device__ __forceinline__ void posting_window(const uint64_t* idx, uint32_t* st, uint32_t* len,
-                                               int64_t lo, int64_t hi) {
-  uint32_t a0 = *st, a1 = *st + *len;
-  uint32_t l = a0, h = a1;
-  while (l < h) {
-    const uint32_t mid = (l + h) >> 1;
-    if ((int64_t)rec_pos(idx[mid]) < lo) l = mid + 1; else h = mid;
+// First x in [a0, a1) whose record position is >= key (a1 when none): the
+// same answer as a binary search, found with fewer dependent loads.  A
+// posting list of a batch spans every genome with positions spread over the
+// whole target, so one interpolation probe lands near the answer; a gallop
+// from it brackets the answer and a binary search finishes inside the
+// bracket.  Invariant: pos(lo) < key <= pos(hi).
+__host__ __device__ __forceinline__ uint32_t pos_lower_bound(const uint64_t* idx, uint32_t a0,
+                                                             uint32_t a1, int64_t key) {
+  if (a0 >= a1) return a0;
+  const int64_t pf = rec_pos(idx[a0]), pl = rec_pos(idx[a1 - 1]);
+  if (pf >= key) return a0;
+  if (pl < key) return a1;
+  uint32_t lo = a0, hi = a1 - 1;
+  if (hi - lo > 1) {
+    // (key - pf) / (pl - pf) is in (0, 1]; any probe strictly inside the
+    // bracket is correct, so a single-precision estimate clamped into it
+    // will do (an integer division here costs more than a search step)
+    const float f = (float)(key - pf) / (float)(pl - pf) * (float)(hi - lo - 1);
+    const uint32_t g = lo + 1 + (f < (float)(hi - lo - 2) ? (uint32_t)f : hi - lo - 2);
+    uint32_t step = 1;
+    if ((int64_t)rec_pos(idx[g]) >= key) {
+      hi = g;
+      while (hi - lo > 1) {  // gallop down
+        const uint32_t c = hi - lo > step ? hi - step : lo;
+        if (c == lo) break;
+        if ((int64_t)rec_pos(idx[c]) >= key) {
+          hi = c;
+          step <<= 1;
+        } else {
+          lo = c;
+          break;
+        }
+      }
+    } else {
+      lo = g;
+      while (hi - lo > 1) {  // gallop up
+        const uint32_t c = hi - lo > step ? lo + step : hi;
+        if (c == hi) break;
+        if ((int64_t)rec_pos(idx[c]) < key) {
+          lo = c;
+          step <<= 1;
+        } else {
+          hi = c;
+          break;
+        }
+      }
+    }
   }
-  uint32_t l2 = l, h2 = a1;
-  while (l2 < h2) {
-    const uint32_t mid = (l2 + h2) >> 1;
-    if ((int64_t)rec_pos(idx[mid]) < hi) l2 = mid + 1; else h2 = mid;
+  while (hi - lo > 1) {
+    const uint32_t mid = lo + ((hi - lo) >> 1);
+    if ((int64_t)rec_pos(idx[mid]) >= key) hi = mid; else lo = mid;
   }
+  return hi;
+}
+
+// First x in [a0, a1) whose record position is >= key, galloping forward
+// from a0: the answer is expected a few entries on (the postings of one
+// genome of a batch).
+__host__ __device__ __forceinline__ uint32_t pos_gallop_forward(const uint64_t* idx, uint32_t a0,
+                                                                uint32_t a1, int64_t key) {
+  if (a0 >= a1 || (int64_t)rec_pos(idx[a0]) >= key) return a0;
+  uint32_t lo = a0, hi = a1;  // pos(lo) < key; pos(hi) >= key, or hi = a1
+  uint32_t step = 1;
+  while (hi - lo > 1) {
+    const uint32_t c = hi - lo > step ? lo + step : hi;
+    if (c == hi) break;
+    if ((int64_t)rec_pos(idx[c]) < key) {
+      lo = c;
+      step <<= 1;
+    } else {
+      hi = c;
+      break;
+    }
+  }
+  while (hi - lo > 1) {
+    const uint32_t mid = lo + ((hi - lo) >> 1);
+    if ((int64_t)rec_pos(idx[mid]) >= key) hi = mid; else lo = mid;
+  }
+  return hi;
+}
+
+// Narrows a posting list [*st, *st + *len) to the positions in [lo, hi)
+// (one genome of a batch).
+__host__ __device__ __forceinline__ void posting_window(const uint64_t* idx, uint32_t* st,
+                                                        uint32_t* len, int64_t lo, int64_t hi) {
+  const uint32_t a0 = *st, a1 = *st + *len;
+  const uint32_t l = pos_lower_bound(idx, a0, a1, lo);
+  const uint32_t l2 = pos_gallop_forward(idx, l, a1, hi);
   *st = l;
   *len = l2 - l;
+}
+
+// Posting range of every query record of a batch self-search, resolved once
+// per record rather than once per window that holds it (a record lies in
+// n / step windows), by threads that each follow one record's chain of
+// dependent loads.  Records are sorted by position, so neighbouring threads
+// share a genome and often a hash.
+__global__ void k_qpost(FArgs a, int64_t nq, const uint32_t* dnq, uint2* out) {
+  const int64_t n = dnq ? (int64_t)*dnq : nq;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t r = a.qrec[x];
+    const uint32_t h = rec_hash(r);
+    uint32_t st = a.toff[h], len = a.toff[h + 1] - st;
+    if (a.max_occ > 0 && (int)len > a.max_occ) {
+      out[x] = make_uint2(kNone, 0u);
+      continue;
+    }
+    const int sq = seq_of(a.qseq, a.nqseq, (int64_t)rec_pos(r));
+    posting_window(a.tsorted, &st, &len, a.tseq[sq], a.tseq[sq + 1]);
+    out[x] = make_uint2(st, len);
+  }
 }
 
 __device__ int build_wq(const FArgs& a, QBuild q, int c, int64_t seq_lo = 0, int64_t seq_hi = 0) {
@@ -636,6 +737,7 @@ __global__ void __launch_bounds__(TPB) k_filter_fast(FArgs a, TierIO io) {
 // and swept exactly by lane 0.  Windows past any limit go to the next tier.
 
 constexpr int kWQ = 128;        // query records
+static_assert(kWQ <= 128, "the warp tier's sort keys carry a record offset in 7 bits");
 constexpr int kWSlots = 1024;   // (bin, o) 16-bit counters (512 bins)
 constexpr int kWL = 256;        // collected hits
 constexpr int kWG = 64;         // dense groups
@@ -702,12 +804,18 @@ __global__ void __launch_bounds__(32 * kWWarps) k_filter_warp(FArgs a, TierIO io
       hand_over(wdx);
       continue;
     }
+    // keys sort by (hash, strand); with precomputed posting ranges a key
+    // also carries the record's offset in the window in its low 7 bits
+    // (hashes have at most 24 bits there), to find the record's range
+    const bool packed = a.qpost != nullptr;
+    const int ksh = packed ? 8 : 1;
     const int np = next_pow2(c < 2 ? 2 : c);
     for (int x = lane; x < np; x += 32) {
       uint32_t key = kNone;
       if (x < c) {
         const uint64_t r = __ldg(a.qrec + qa + x);
-        key = (rec_hash(r) << 1) | rec_strand(r);
+        key = packed ? (rec_hash(r) << 8) | (rec_strand(r) << 7) | (uint32_t)x
+                     : (rec_hash(r) << 1) | rec_strand(r);
       }
       S.qkey[x] = key;
     }
@@ -726,13 +834,21 @@ __global__ void __launch_bounds__(32 * kWWarps) k_filter_warp(FArgs a, TierIO io
       bool keep = false;
       uint32_t st = 0, len = 0, mask = 0;
       if (x < c) {
-        const uint32_t h = S.qkey[x] >> 1;
-        if (x == 0 || (S.qkey[x - 1] >> 1) != h) {
-          for (int y = x; y < c && (S.qkey[y] >> 1) == h; ++y) mask |= 1u << (S.qkey[y] & 1u);
-          st = a.toff[h];
-          len = a.toff[h + 1] - st;
-          keep = !(a.max_occ > 0 && (int)len > a.max_occ);
-          if (keep && a.self_mode == 2) posting_window(a.tsorted, &st, &len, seq_lo, seq_hi);
+        const uint32_t h = S.qkey[x] >> ksh;
+        if (x == 0 || (S.qkey[x - 1] >> ksh) != h) {
+          for (int y = x; y < c && (S.qkey[y] >> ksh) == h; ++y)
+            mask |= 1u << ((S.qkey[y] >> (ksh - 1)) & 1u);
+          if (packed) {
+            const uint2 pp = a.qpost[qa + (S.qkey[x] & 127u)];
+            st = pp.x;
+            len = pp.y;
+            keep = pp.x != kNone;
+          } else {
+            st = a.toff[h];
+            len = a.toff[h + 1] - st;
+            keep = !(a.max_occ > 0 && (int)len > a.max_occ);
+            if (keep && a.self_mode == 2) posting_window(a.tsorted, &st, &len, seq_lo, seq_hi);
+          }
         }
       }
       const unsigned km = __ballot_sync(0xffffffffu, keep);
@@ -766,13 +882,32 @@ __global__ void __launch_bounds__(32 * kWWarps) k_filter_warp(FArgs a, TierIO io
     for (int x = lane; x < kWSlots / 2; x += 32) S.slots[x] = 0;
     if (lane == 0) S.nhit = 0;
     __syncwarp();
+    // Hits in chunks of 32 consecutive ones.  The list holding hit e is the
+    // last x with pre[x] <= e: for the chunk at base it is cur (the list
+    // holding the previous chunk's last hit) plus the number of lists after
+    // cur that start at or before e, found by a 5-step search over the next
+    // 32 lists' starts (pre is nondecreasing) instead of a search per hit.
     auto each_hit = [&](auto f) {
-      for (int e = lane; e < (int)H; e += 32) {
-        int lo = 0, hi = s;
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if ((int)S.pre[mid] <= e) lo = mid; else hi = mid;
+      int cur = 0;
+      for (int base = 0; base < (int)H; base += 32) {
+        const int e = base + lane;
+        int lo = cur;
+        for (int from = cur + 1;; from += 32) {
+          const int x = from + lane;
+          const int d = x < s ? (int)S.pre[x] - base : INT_MAX;
+          int n = 0;  // lists among from .. from + 30 starting at or before e
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1) {
+            const int v = __shfl_sync(0xffffffffu, d, n + step - 1);
+            if (v <= lane) n += step;
+          }
+          const int d31 = __shfl_sync(0xffffffffu, d, 31);
+          if (d31 <= lane) n = 32;
+          if (n > 0) lo = from + n - 1;
+          if (d31 > 31) break;  // no list past these starts inside the chunk
         }
+        cur = __shfl_sync(0xffffffffu, lo, 31);
+        if (e >= (int)H) continue;
         const uint64_t r = __ldg(a.tsorted + S.pst[lo] + (uint32_t)(e - (int)S.pre[lo]));
         const uint32_t t = rec_pos(r), st = rec_strand(r);
         if (a.self_mode && (int64_t)t >= i && (int64_t)t <= i + a.span) continue;
@@ -2329,6 +2464,18 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   a.next_window = (unsigned int*)(counters + 2);
   a.stats = counters + 4;
 
+  a.qpost = nullptr;
+  if (D.self_mode == 2 && 2 * D.k <= 24) {
+    // batch self-search: every query record's posting range in its own
+    // genome, once (the warp tier reads them; its sort keys carry a
+    // record's offset beside a hash of at most 24 bits)
+    uint2* qp = (uint2*)ctx_alloc(ctx, (size_t)nq * sizeof(uint2));
+    if (!qp) return SEDEF_ERR_OOM;
+    int64_t g = (nq + 255) / 256;
+    if (g > (int64_t)ctx_sm_count(ctx) * 16) g = (int64_t)ctx_sm_count(ctx) * 16;
+    SEDEF_KERNEL(ctx, "k_qpost", k_qpost<<<(int)g, 256, 0, st>>>(a, nq, dnq, qp));
+    a.qpost = qp;
+  }
   SEDEF_KERNEL(ctx, "k_windows",
                k_windows<<<(int)((nwin + 255) / 256), 256, 0, st>>>(
                    qrec, nq, a.qseq, nqseq, (const int64_t*)(d_up + ow), nwin, D.step, D.span, wi,
