@@ -65,6 +65,7 @@ struct FArgs {
   // genome (batch self-search), or (kNone, 0) when the list passes max_occ;
   // nullptr when the tiers look postings up themselves
   const uint2* qpost;
+  const uint32_t* tsamp;  // positions of every kSampleStride-th index entry, or nullptr
   int64_t nwin;
   int ntseq, nqseq;
   int64_t ttotal;  // target total length
@@ -388,15 +389,57 @@ __host__ __device__ __forceinline__ uint32_t pos_gallop_forward(const uint64_t* 
   return hi;
 }
 
+// Record positions of every kSampleStride-th entry of the sorted index
+// (samp[k] = pos(idx[k * kSampleStride])): a search first brackets its
+// answer between two samples, an array small enough to stay in L2, and then
+// reads one stretch of kSampleStride index entries (one 128-byte line).
+constexpr int kSampleShift = 4, kSampleStride = 1 << kSampleShift;
+
+// pos_lower_bound over the samples, then over the bracketed stretch.
+__host__ __device__ __forceinline__ uint32_t pos_lower_bound_sampled(const uint64_t* idx,
+                                                                     const uint32_t* samp,
+                                                                     uint32_t a0, uint32_t a1,
+                                                                     int64_t key) {
+  uint32_t lo = a0, hi = a1;  // pos(x) < key below lo; pos(x) >= key from hi (or hi = a1)
+  if (a0 < a1) {
+    const uint32_t k0 = (a0 + kSampleStride - 1) >> kSampleShift, k1 = (a1 - 1) >> kSampleShift;
+    if (k0 <= k1) {  // samples inside the list: the first one at or past key
+      uint32_t l = k0, h = k1 + 1;
+      while (l < h) {
+        const uint32_t m = l + ((h - l) >> 1);
+        if ((int64_t)samp[m] >= key) h = m; else l = m + 1;
+      }
+      if (l <= k1) hi = l << kSampleShift;
+      if (l > k0) lo = ((l - 1) << kSampleShift) + 1;
+    }
+  }
+  while (lo < hi) {
+    const uint32_t m = lo + ((hi - lo) >> 1);
+    if ((int64_t)rec_pos(idx[m]) >= key) hi = m; else lo = m + 1;
+  }
+  return lo;
+}
+
 // Narrows a posting list [*st, *st + *len) to the positions in [lo, hi)
 // (one genome of a batch).
-__host__ __device__ __forceinline__ void posting_window(const uint64_t* idx, uint32_t* st,
-                                                        uint32_t* len, int64_t lo, int64_t hi) {
+__host__ __device__ __forceinline__ void posting_window(const uint64_t* idx, const uint32_t* samp,
+                                                        uint32_t* st, uint32_t* len, int64_t lo,
+                                                        int64_t hi) {
   const uint32_t a0 = *st, a1 = *st + *len;
-  const uint32_t l = pos_lower_bound(idx, a0, a1, lo);
+  const uint32_t l =
+      samp ? pos_lower_bound_sampled(idx, samp, a0, a1, lo) : pos_lower_bound(idx, a0, a1, lo);
   const uint32_t l2 = pos_gallop_forward(idx, l, a1, hi);
   *st = l;
   *len = l2 - l;
+}
+
+__global__ void k_sample_pos(const uint64_t* __restrict__ idx, int64_t nt, const uint32_t* dnt,
+                             uint32_t* __restrict__ samp) {
+  const int64_t n = dnt ? (int64_t)*dnt : nt;
+  const int64_t ns = (n + kSampleStride - 1) >> kSampleShift;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ns;
+       k += (int64_t)gridDim.x * blockDim.x)
+    samp[k] = rec_pos(idx[k << kSampleShift]);
 }
 
 // Posting range of every query record of a batch self-search, resolved once
@@ -416,7 +459,7 @@ __global__ void k_qpost(FArgs a, int64_t nq, const uint32_t* dnq, uint2* out) {
       continue;
     }
     const int sq = seq_of(a.qseq, a.nqseq, (int64_t)rec_pos(r));
-    posting_window(a.tsorted, &st, &len, a.tseq[sq], a.tseq[sq + 1]);
+    posting_window(a.tsorted, a.tsamp, &st, &len, a.tseq[sq], a.tseq[sq + 1]);
     out[x] = make_uint2(st, len);
   }
 }
@@ -443,7 +486,8 @@ __device__ int build_wq(const FArgs& a, QBuild q, int c, int64_t seq_lo = 0, int
         len = a.toff[h + 1] - st;
         keep = (a.max_occ > 0 && (int)len > a.max_occ) ? 0 : 1;
         // independent genomes: only the query's own sequence can hold targets
-        if (keep && a.self_mode == 2) posting_window(a.tsorted, &st, &len, seq_lo, seq_hi);
+        if (keep && a.self_mode == 2)
+          posting_window(a.tsorted, a.tsamp, &st, &len, seq_lo, seq_hi);
       }
     }
     int tot;
@@ -847,7 +891,8 @@ __global__ void __launch_bounds__(32 * kWWarps) k_filter_warp(FArgs a, TierIO io
             st = a.toff[h];
             len = a.toff[h + 1] - st;
             keep = !(a.max_occ > 0 && (int)len > a.max_occ);
-            if (keep && a.self_mode == 2) posting_window(a.tsorted, &st, &len, seq_lo, seq_hi);
+            if (keep && a.self_mode == 2)
+          posting_window(a.tsorted, a.tsamp, &st, &len, seq_lo, seq_hi);
           }
         }
       }
@@ -2465,6 +2510,17 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   a.stats = counters + 4;
 
   a.qpost = nullptr;
+  a.tsamp = nullptr;
+  if (D.self_mode == 2) {
+    // every posting search of a batch self-search starts from the samples
+    const int64_t ns = (nt + kSampleStride - 1) >> kSampleShift;
+    uint32_t* samp = (uint32_t*)ctx_alloc(ctx, (size_t)ns * 4);
+    if (!samp) return SEDEF_ERR_OOM;
+    int64_t g = (ns + 255) / 256;
+    if (g > (int64_t)ctx_sm_count(ctx) * 16) g = (int64_t)ctx_sm_count(ctx) * 16;
+    SEDEF_KERNEL(ctx, "k_sample_pos", k_sample_pos<<<(int)g, 256, 0, st>>>(tsorted, nt, dnt, samp));
+    a.tsamp = samp;
+  }
   if (D.self_mode == 2 && 2 * D.k <= 24) {
     // batch self-search: every query record's posting range in its own
     // genome, once (the warp tier reads them; its sort keys carry a
