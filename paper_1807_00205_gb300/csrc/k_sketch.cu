@@ -112,20 +112,106 @@ struct SketchArgs {
   int64_t ntiles;
 };
 
-template <bool kWrite>
-__global__ void __launch_bounds__(kSkThreads) k_sketch(SketchArgs a, uint32_t* __restrict__ tile_count,
+// Single-pass form: each CTA takes tiles in ticket order, publishes its
+// tile's record count, and adds up its predecessors' counts (decoupled
+// look-back) until one has published its inclusive prefix.  A tile's
+// predecessors were all taken before it by CTAs that publish their count
+// before they wait on anyone, so every wait ends; it is bounded all the
+// same, and a wait that gives up raises *err for the host.
+struct LookBack {
+  unsigned long long* status;  // per tile: flag (2 bits) and value (62 bits); zeroed
+  unsigned int* ticket;        // next tile to take; zeroed
+  unsigned long long* total;   // records of all tiles (written by the last tile)
+  int* err;                    // set when a wait gives up; zeroed
+};
+
+constexpr unsigned long long kLbAggregate = 1ull << 62, kLbPrefix = 2ull << 62;
+constexpr unsigned long long kLbValue = (1ull << 62) - 1;
+constexpr unsigned int kLbSpins = 1u << 20;  // polls of one predecessor before giving up
+
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Records before tile `tile`; warp 0 of the CTA calls it once per tile.  The
+// warp reads the status of the 32 tiles below its window at once: the
+// nearest one that has published its inclusive prefix ends the walk, and
+// the counts of the tiles above it are summed by the warp (a look-back one
+// tile at a time falls behind the tiles that are in flight).
+__device__ long long look_back(const LookBack& lb, int64_t tile, int64_t ntiles,
+                               unsigned long long count) {
+  const int lane = threadIdx.x & 31;
+  long long before = 0;
+  if (tile > 0) {
+    if (lane == 0) st_release_gpu(lb.status + tile, kLbAggregate | count);
+    int64_t j = tile - 1;  // the walk's top tile
+    unsigned int spins = 0;
+    while (true) {
+      const int64_t at = j - lane;
+      // below tile 0 reads as a published prefix of zero
+      const unsigned long long v = at >= 0 ? ld_acquire_gpu(lb.status + at) : kLbPrefix;
+      const unsigned long long flag = v & ~kLbValue;
+      const unsigned prefix = __ballot_sync(0xffffffffu, flag == kLbPrefix);
+      const int p = prefix ? __ffs(prefix) - 1 : 31;  // lanes 0..p take part
+      const unsigned need = p == 31 ? 0xffffffffu : ((1u << (p + 1)) - 1u);
+      const unsigned waiting = __ballot_sync(0xffffffffu, flag == 0) & need;
+      if (waiting) {
+        if (++spins > kLbSpins) {
+          if (lane == 0) atomicExch(lb.err, 1);
+          break;
+        }
+        __nanosleep(64);
+        continue;
+      }
+      spins = 0;
+      long long part = lane <= p ? (long long)(v & kLbValue) : 0;
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+      before += part;
+      if (prefix) break;
+      j -= 32;
+    }
+  }
+  if (lane == 0) {
+    st_release_gpu(lb.status + tile, kLbPrefix | ((unsigned long long)before + count));
+    if (tile == ntiles - 1) *lb.total = (unsigned long long)before + count;
+  }
+  return before;
+}
+
+// kMode 0: count the records of each tile; 1: write them at the tile
+// offsets given; 2: one pass, offsets by look-back.  Four CTAs per SM (64
+// registers a thread): while one CTA's warp 0 walks back, the others compute.
+template <int kMode>
+__global__ void __launch_bounds__(kSkThreads, 4) k_sketch(SketchArgs a, uint32_t* __restrict__ tile_count,
                                                        const uint32_t* __restrict__ tile_offset,
-                                                       uint64_t* __restrict__ out, int64_t cap) {
+                                                       uint64_t* __restrict__ out, int64_t cap,
+                                                       LookBack lb) {
   __shared__ uint32_t s_pk[kSkWords16];
   __shared__ uint32_t s_mk[kSkWords32];
   __shared__ uint32_t s_nb[kSkWords32];
   __shared__ uint32_t s_h[kSkHashes];
   __shared__ uint8_t s_sg[kSkHashes];
   __shared__ int s_tmp[33];
+  __shared__ long long s_tile, s_base;
 
   const int k = a.k, w = a.w;
   const int tid = threadIdx.x;
-  for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+  for (int64_t it = blockIdx.x;; it += gridDim.x) {
+    int64_t tile = it;
+    if (kMode == 2) {
+      __syncthreads();  // s_tile of the last tile is read
+      if (tid == 0) s_tile = (long long)atomicAdd(lb.ticket, 1u);
+      __syncthreads();
+      tile = s_tile;
+    }
+    if (tile >= a.ntiles) break;
     const int64_t Q0 = tile * kSkTile;
     const int64_t HB = Q0 - 1;                    // first hash position of the tile
     const int nh = kSkTile + w;                   // hash positions [HB, HB + nh)
@@ -247,10 +333,17 @@ __global__ void __launch_bounds__(kSkThreads) k_sketch(SketchArgs a, uint32_t* _
     const int cnt = __popc(flags);
     int total;
     const int excl = block_exclusive_sum(cnt, s_tmp, &total);
-    if (!kWrite) {
+    if (kMode == 0) {
       if (tid == 0) tile_count[tile] = (uint32_t)total;
     } else {
-      int64_t o = (int64_t)tile_offset[tile] + excl;
+      if (kMode == 2) {
+        if (tid < 32) {
+          const long long before = look_back(lb, tile, a.ntiles, (unsigned long long)total);
+          if (tid == 0) s_base = before;
+        }
+        __syncthreads();
+      }
+      int64_t o = (kMode == 2 ? (int64_t)s_base : (int64_t)tile_offset[tile]) + excl;
 #pragma unroll
       for (int t = 1; t <= kSkWPT; ++t) {
         if (flags >> t & 1u) {
@@ -302,9 +395,7 @@ int run_sketch(sedef_ctx* ctx, const uint32_t* packed, const uint32_t* mask, con
   const int64_t nwin = N;  // window starts q in [0, N)
   a.ntiles = (nwin + kSkTile - 1) / kSkTile;
   int64_t* d_off = (int64_t*)ctx_alloc(ctx, (size_t)(nseq + 1) * 8);
-  uint32_t* cnt = (uint32_t*)ctx_alloc(ctx, (size_t)(a.ntiles + 1) * 4);
-  uint32_t* toff = (uint32_t*)ctx_alloc(ctx, (size_t)(a.ntiles + 1) * 4);
-  if (!d_off || !cnt || !toff) return SEDEF_ERR_OOM;
+  if (!d_off) return SEDEF_ERR_OOM;
   if (pl) {
     int64_t* h = (int64_t*)host_buf(ctx, pl, (size_t)(nseq + 1) * 8);
     if (!h) return SEDEF_ERR_OOM;
@@ -318,28 +409,45 @@ int run_sketch(sedef_ctx* ctx, const uint32_t* packed, const uint32_t* mask, con
   int64_t grid = a.ntiles;
   const int64_t maxgrid = (int64_t)ctx_sm_count(ctx) * 8;
   if (grid > maxgrid) grid = maxgrid;
-  SEDEF_KERNEL(ctx, "k_sketch_count",
-               k_sketch<false><<<(int)grid, kSkThreads, 0, st>>>(a, cnt, nullptr, nullptr, 0));
-  SEDEF_TRY(scan_exclusive_u32(ctx, cnt, toff, a.ntiles, toff + a.ntiles));
-  if (pl) {
-    // the write pass stores the records below the capacity; the exact
-    // total stays on the device
-    pl->n_rec = toff + a.ntiles;
-    SEDEF_TRY(plan_check(ctx, pl, toff + a.ntiles, cap, 0));
-    *nrec = cap;
-    SEDEF_KERNEL(ctx, "k_sketch_write",
-                 k_sketch<true><<<(int)grid, kSkThreads, 0, st>>>(a, nullptr, toff, rec, cap));
+  if (!pl) {
+    // one pass: record offsets by look-back over the tiles
+    if (a.ntiles == 0) {
+      *nrec = 0;
+      return SEDEF_OK;
+    }
+    unsigned long long* status = (unsigned long long*)ctx_alloc(ctx, (size_t)(a.ntiles + 4) * 8);
+    if (!status) return SEDEF_ERR_OOM;
+    LookBack lb;
+    lb.status = status + 4;
+    lb.ticket = (unsigned int*)status;
+    lb.total = status + 1;
+    lb.err = (int*)(status + 2);
+    SEDEF_CUDA(cudaMemsetAsync(status, 0, (size_t)(a.ntiles + 4) * 8, st));
+    SEDEF_KERNEL(ctx, "k_sketch",
+                 k_sketch<2><<<(int)grid, kSkThreads, 0, st>>>(a, nullptr, nullptr, rec, cap, lb));
+    unsigned long long* h = (unsigned long long*)ctx_host(ctx, 16);
+    if (!h) return SEDEF_ERR_OOM;
+    SEDEF_CUDA(cudaMemcpyAsync(h, status + 1, 16, cudaMemcpyDeviceToHost, st));
+    SEDEF_CUDA(cudaStreamSynchronize(st));
+    if ((int)h[1] != 0) return fail(SEDEF_ERR_TIMEOUT, "sedef_sketch: a tile's offset wait gave up");
+    *nrec = (int64_t)h[0];
+    if (*nrec > cap) return fail(SEDEF_ERR_CAPACITY, "sedef_sketch: record buffer too small");
     return SEDEF_OK;
   }
-  uint32_t* h_total = (uint32_t*)ctx_host(ctx, 8);
-  if (!h_total) return SEDEF_ERR_OOM;
-  SEDEF_CUDA(cudaMemcpyAsync(h_total, toff + a.ntiles, 4, cudaMemcpyDeviceToHost, st));
-  SEDEF_CUDA(cudaStreamSynchronize(st));
-  *nrec = *h_total;
-  if (*nrec > cap) return fail(SEDEF_ERR_CAPACITY, "sedef_sketch: record buffer too small");
+  // planned pass (one CUDA graph, no waits between CTAs): count, scan and
+  // write; the write pass stores the records below the capacity and the
+  // exact total stays on the device
+  uint32_t* cnt = (uint32_t*)ctx_alloc(ctx, (size_t)(a.ntiles + 1) * 4);
+  uint32_t* toff = (uint32_t*)ctx_alloc(ctx, (size_t)(a.ntiles + 1) * 4);
+  if (!cnt || !toff) return SEDEF_ERR_OOM;
+  SEDEF_KERNEL(ctx, "k_sketch_count",
+               k_sketch<0><<<(int)grid, kSkThreads, 0, st>>>(a, cnt, nullptr, nullptr, 0, LookBack{}));
+  SEDEF_TRY(scan_exclusive_u32(ctx, cnt, toff, a.ntiles, toff + a.ntiles));
+  pl->n_rec = toff + a.ntiles;
+  SEDEF_TRY(plan_check(ctx, pl, toff + a.ntiles, cap, 0));
+  *nrec = cap;
   SEDEF_KERNEL(ctx, "k_sketch_write",
-               k_sketch<true><<<(int)grid, kSkThreads, 0, st>>>(a, nullptr, toff, rec, cap));
-  SEDEF_CUDA(cudaStreamSynchronize(st));
+               k_sketch<1><<<(int)grid, kSkThreads, 0, st>>>(a, nullptr, toff, rec, cap, LookBack{}));
   return SEDEF_OK;
 }
 
@@ -444,7 +552,7 @@ extern "C" int sedef_sketch_noalloc(const uint32_t* d_packed, const uint32_t* d_
   int sms = 0;
   SEDEF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   int64_t grid = a.ntiles < (int64_t)sms * 8 ? a.ntiles : (int64_t)sms * 8;
-  k_sketch<false><<<(int)grid, kSkThreads, 0, st>>>(a, cnt, nullptr, nullptr, 0);
+  k_sketch<0><<<(int)grid, kSkThreads, 0, st>>>(a, cnt, nullptr, nullptr, 0, LookBack{});
   count_launch();
   SEDEF_LAUNCHED("k_sketch_count");
   k_scan_one_block<<<1, 1024, 0, st>>>(cnt, toff, a.ntiles);
@@ -455,7 +563,7 @@ extern "C" int sedef_sketch_noalloc(const uint32_t* d_packed, const uint32_t* d_
   SEDEF_CUDA(cudaStreamSynchronize(st));
   *h_nrec = total;
   if ((int64_t)total > rec_cap) return fail(SEDEF_ERR_CAPACITY, "record buffer too small");
-  k_sketch<true><<<(int)grid, kSkThreads, 0, st>>>(a, nullptr, toff, d_rec, rec_cap);
+  k_sketch<1><<<(int)grid, kSkThreads, 0, st>>>(a, nullptr, toff, d_rec, rec_cap, LookBack{});
   count_launch();
   SEDEF_LAUNCHED("k_sketch_write");
   SEDEF_CUDA(cudaStreamSynchronize(st));
