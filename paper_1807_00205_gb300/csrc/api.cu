@@ -107,15 +107,17 @@ void Pool::release() {
 }
 
 int ensure_smem_attr(const void* kernel, size_t bytes) {
+  // The attribute is one maximum per kernel and device: it is only ever
+  // raised, so a launch with fewer bytes after a larger one stays valid.
   static std::mutex mu;
-  static std::set<std::tuple<int, const void*, size_t>> done;
+  static std::map<std::pair<int, const void*>, size_t> raised;
   int dev = 0;
   SEDEF_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> g(mu);
-  const auto key = std::make_tuple(dev, kernel, bytes);
-  if (done.count(key)) return SEDEF_OK;
+  size_t& cur = raised[std::make_pair(dev, kernel)];
+  if (bytes <= cur) return SEDEF_OK;
   SEDEF_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  done.insert(key);
+  cur = bytes;
   return SEDEF_OK;
 }
 
