@@ -632,32 +632,39 @@ def run_workload(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = float(clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0)
     issue_peak = sms * 4 * mhz / 1000.0  # G warp instructions per second
+    # per-unit ncu counters of the family (one capture on this workload and
+    # filter shape, scaled by this pass's units: hits for the filter, runs
+    # for the refine, bases for the streaming families)
+    units = {"filter": int(fstats["hits"]), "refine": int(out["nruns"]),
+             "runsort": int(out["nruns"]), "chain": int(out["nruns"]),
+             "merge": int(out["nchains"]), "sketch": N, "pack": N, "index": N}.get(dom, 0)
+    e = counters_entry(f"{dom} family", W.name, variant)
+    issue = None
+    traffic = None
+    if e and units:
+        inst = e["warp_instructions_per_unit"] * units
+        a_i = inst / (fam_ms[dom] / 1000) / 1e9
+        issue = {"achieved": a_i, "peak": issue_peak, "unit": "G warp-instructions/s",
+                 "frac": a_i / issue_peak, "instructions_per_step": inst,
+                 "peak_from": f"{sms} SMs x 4 schedulers x {mhz:.0f} MHz (median sampled)"}
+        if e.get("dram_bytes_per_unit"):
+            traffic = int(e["dram_bytes_per_unit"] * units)
     if dom in algo:
         a = algo[dom] / (fam_ms[dom] / 1000) / 1e9
         roof = {"kernel": f"{dom} family", "bound": "hbm", "achieved": a, "peak": peak,
                 "unit": "GB/s", "frac": a / peak, "peak_source": peak_kind,
                 "algorithmic_bytes_per_step": algo[dom], "ms_per_step": fam_ms[dom],
-                "traffic": None}
+                "traffic": traffic, "issue": issue}
     else:
-        # plain integer work bound by instruction issue: warp instructions per
-        # unit (one ncu capture on this workload and filter shape) x units of
-        # this pass, against 4 schedulers x SMs x the sampled SM clock
-        units = {"refine": int(out["nruns"]), "runsort": int(out["nruns"]),
-                 "chain": int(out["nruns"]), "merge": int(out["nchains"])}.get(dom, 0)
-        kname = {"refine": "k_refine_batch"}.get(dom, dom)
-        e = counters_entry(kname, W.name, variant)
+        # plain integer work bound by instruction issue: warp instructions
+        # against 4 schedulers x SMs x the sampled SM clock
         roof = {"kernel": f"{dom} family", "bound": "alu", "peak": issue_peak,
-                "unit": "G warp-instructions/s", "peak_from": f"{sms} SMs x 4 schedulers x "
-                f"{mhz:.0f} MHz (median sampled)", "ms_per_step": fam_ms[dom],
-                "achieved": None, "frac": None, "traffic": None}
-        if e and units:
-            inst = e["warp_instructions_per_unit"] * units
-            a = inst / (fam_ms[dom] / 1000) / 1e9
-            roof.update({"achieved": a, "frac": a / issue_peak,
-                         "instructions_per_step": inst,
-                         "traffic": int(e["dram_bytes_per_unit"] * units)
-                         if e.get("dram_bytes_per_unit") else None,
-                         "counters_from": e.get("profile")})
+                "unit": "G warp-instructions/s", "ms_per_step": fam_ms[dom],
+                "achieved": issue["achieved"] if issue else None,
+                "frac": issue["frac"] if issue else None, "traffic": traffic, "issue": issue}
+    if e:
+        roof["counters_from"] = e.get("profile")
+        roof["counters_units"] = f"{units} {e.get('unit', 'units')}"
     kernels = {k: {"launches_per_step": c / nsteps, "ms_per_step": t / nsteps}
                for k, (c, t) in sorted(trace.items(), key=lambda kv: -kv[1][1])}
     if args.trace:

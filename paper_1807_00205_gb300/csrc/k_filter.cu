@@ -787,6 +787,8 @@ constexpr int kWL = 256;        // collected hits
 constexpr int kWG = 64;         // dense groups
 constexpr int kWH = 4096;       // enumerated hits
 constexpr int kWWarps = 8;
+constexpr int kWTab = 2 * kWL;   // W_Q hash-table slots (u32, over the hit buffer)
+static_assert(kWTab >= 2 * kWQ && kWTab <= kWSlots / 2, "the W_Q table and its masks must fit");
 
 struct WarpSmem {
   uint32_t qkey[kWQ];
@@ -848,52 +850,72 @@ __global__ void __launch_bounds__(32 * kWWarps) k_filter_warp(FArgs a, TierIO io
       hand_over(wdx);
       continue;
     }
-    // keys sort by (hash, strand); with precomputed posting ranges a key
-    // also carries the record's offset in the window in its low 7 bits
-    // (hashes have at most 24 bits there), to find the record's range
-    const bool packed = a.qpost != nullptr;
-    const int ksh = packed ? 8 : 1;
-    const int np = next_pow2(c < 2 ? 2 : c);
-    for (int x = lane; x < np; x += 32) {
-      uint32_t key = kNone;
-      if (x < c) {
-        const uint64_t r = __ldg(a.qrec + qa + x);
-        key = packed ? (rec_hash(r) << 8) | (rec_strand(r) << 7) | (uint32_t)x
-                     : (rec_hash(r) << 1) | rec_strand(r);
-      }
-      S.qkey[x] = key;
+    // W_Q: the window's distinct hashes, by insertion into an open-addressing
+    // table (key hash + 1, linear probing from the hash's low bits) laid
+    // over the hit buffer, with each hash's strand mask beside it in the
+    // counter table (both are rebuilt later for the hits).  The order of W_Q
+    // plays no part in the counts, so no sort is needed.  A record that
+    // inserts its hash first owns it.
+    uint32_t* tab = reinterpret_cast<uint32_t*>(S.hits);
+    uint32_t* tmask = S.slots;
+    for (int x = lane; x < kWTab; x += 32) {
+      tab[x] = 0u;
+      tmask[x] = 0u;
     }
     __syncwarp();
-    warp_sort(S.qkey, np);
-    // distinct hashes in sorted order (the order build_wq gives)
+    const bool packed = a.qpost != nullptr;
+    uint32_t own_slot[kWQ / 32], own_h[kWQ / 32];
+    unsigned owner = 0;
+#pragma unroll
+    for (int ch = 0; ch < kWQ / 32; ++ch) {
+      const int x = ch * 32 + lane;
+      own_slot[ch] = 0;
+      own_h[ch] = 0;
+      if (x < c) {
+        const uint64_t r = __ldg(a.qrec + qa + x);
+        const uint32_t h = rec_hash(r);
+        uint32_t slot = h & (kWTab - 1);
+        while (true) {  // at most kWQ keys in kWTab slots: a free slot is always found
+          const uint32_t old = atomicCAS(&tab[slot], 0u, h + 1u);
+          if (old == 0u) {
+            owner |= 1u << ch;
+            break;
+          }
+          if (old == h + 1u) break;
+          slot = (slot + 1u) & (kWTab - 1);
+        }
+        atomicOr(&tmask[slot], 1u << rec_strand(r));
+        own_slot[ch] = slot;
+        own_h[ch] = h;
+      }
+    }
     int64_t seq_lo = 0, seq_hi = 0;
     if (a.self_mode == 2) {
       const int sq = a.win_seq[wdx];
       seq_lo = a.tseq[sq];
       seq_hi = a.tseq[sq + 1];
     }
+    __syncwarp();
     int s = 0;
-    for (int base = 0; base < c; base += 32) {
-      const int x = base + lane;
+#pragma unroll
+    for (int ch = 0; ch < kWQ / 32; ++ch) {
+      if (ch * 32 >= c) break;
+      const int x = ch * 32 + lane;
       bool keep = false;
       uint32_t st = 0, len = 0, mask = 0;
-      if (x < c) {
-        const uint32_t h = S.qkey[x] >> ksh;
-        if (x == 0 || (S.qkey[x - 1] >> ksh) != h) {
-          for (int y = x; y < c && (S.qkey[y] >> ksh) == h; ++y)
-            mask |= 1u << ((S.qkey[y] >> (ksh - 1)) & 1u);
-          if (packed) {
-            const uint2 pp = a.qpost[qa + (S.qkey[x] & 127u)];
-            st = pp.x;
-            len = pp.y;
-            keep = pp.x != kNone;
-          } else {
-            st = a.toff[h];
-            len = a.toff[h + 1] - st;
-            keep = !(a.max_occ > 0 && (int)len > a.max_occ);
-            if (keep && a.self_mode == 2)
-          posting_window(a.tsorted, a.tsamp, &st, &len, seq_lo, seq_hi);
-          }
+      if ((owner >> ch) & 1u) {
+        const uint32_t h = own_h[ch];
+        mask = tmask[own_slot[ch]];
+        if (packed) {
+          const uint2 pp = a.qpost[qa + x];
+          st = pp.x;
+          len = pp.y;
+          keep = pp.x != kNone;
+        } else {
+          st = a.toff[h];
+          len = a.toff[h + 1] - st;
+          keep = !(a.max_occ > 0 && (int)len > a.max_occ);
+          if (keep && a.self_mode == 2) posting_window(a.tsorted, a.tsamp, &st, &len, seq_lo, seq_hi);
         }
       }
       const unsigned km = __ballot_sync(0xffffffffu, keep);

@@ -82,6 +82,11 @@ constexpr int kSkWPT = 8;                          // windows per thread
 constexpr int kSkTile = kSkThreads * kSkWPT;       // windows per CTA
 constexpr int kSkMaxW = 256;
 constexpr int kSkHashes = kSkTile + kSkMaxW;       // hash slots (tile + halo)
+// Hash slot x lives at x + x/8: a thread's windows start kSkWPT = 8 slots
+// after its neighbour's, and the padding turns that stride into 9 words, so
+// the lanes of a warp read distinct banks.
+constexpr int kSkHashesP = kSkHashes + kSkHashes / 8 + 1;
+__device__ __forceinline__ int hslot(int x) { return x + (x >> 3); }
 constexpr int kSkWords16 = (kSkHashes + 16) / 16 + 4;
 constexpr int kSkWords32 = (kSkHashes + 16) / 32 + 4;
 
@@ -185,6 +190,24 @@ __device__ long long look_back(const LookBack& lb, int64_t tile, int64_t ntiles,
   return before;
 }
 
+// Exclusive sum over the CTA.  Unlike block_exclusive_sum it ends without a
+// barrier: the next tile reaches s_tmp only after at least two more.
+__device__ __forceinline__ int tile_exclusive_sum(int v, int* tmp, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int inc = warp_inclusive_sum(v);
+  if (lane == 31) tmp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const int x = lane < kSkThreads / 32 ? tmp[lane] : 0;
+    const int xi = warp_inclusive_sum(x);
+    if (lane < kSkThreads / 32) tmp[lane] = xi - x;
+    if (lane == 31) tmp[32] = xi;
+  }
+  __syncthreads();
+  *total = tmp[32];
+  return tmp[warp] + inc - v;
+}
+
 // kMode 0: count the records of each tile; 1: write them at the tile
 // offsets given; 2: one pass, offsets by look-back.  Four CTAs per SM (64
 // registers a thread): while one CTA's warp 0 walks back, the others compute.
@@ -196,17 +219,19 @@ __global__ void __launch_bounds__(kSkThreads, 4) k_sketch(SketchArgs a, uint32_t
   __shared__ uint32_t s_pk[kSkWords16];
   __shared__ uint32_t s_mk[kSkWords32];
   __shared__ uint32_t s_nb[kSkWords32];
-  __shared__ uint32_t s_h[kSkHashes];
-  __shared__ uint8_t s_sg[kSkHashes];
+  __shared__ uint32_t s_h[kSkHashesP];
+  __shared__ uint8_t s_sg[kSkHashesP];
   __shared__ int s_tmp[33];
   __shared__ long long s_tile, s_base;
+  __shared__ long long s_seg_lo, s_seg_hi;  // the sequence holding the tile's first position
 
   const int k = a.k, w = a.w;
   const int tid = threadIdx.x;
   for (int64_t it = blockIdx.x;; it += gridDim.x) {
     int64_t tile = it;
     if (kMode == 2) {
-      __syncthreads();  // s_tile of the last tile is read
+      // every thread read the last tile's s_tile before the barriers of
+      // that tile's body, so tid 0 may overwrite it now
       if (tid == 0) s_tile = (long long)atomicAdd(lb.ticket, 1u);
       __syncthreads();
       tile = s_tile;
@@ -221,7 +246,13 @@ __global__ void __launch_bounds__(kSkThreads, 4) k_sketch(SketchArgs a, uint32_t
     const int64_t last = HB + nh + k;             // one past the last base read
     const int n16 = (int)(((last + 15) >> 4) - wb16 + 1);
     const int n32 = (int)(((last + 31) >> 5) - wb32 + 1);
-    __syncthreads();
+    // no barrier here: the staging buffers were last read in the previous
+    // tile's hash stage, which a barrier ends
+    if (tid == 0) {
+      const int s = seq_of(a.off, a.nseq, b_lo);
+      s_seg_lo = a.off[s];
+      s_seg_hi = a.off[s + 1];
+    }
     for (int x = tid; x < n16; x += kSkThreads) {
       const int64_t g = wb16 + x;
       s_pk[x] = g < nw16 ? __ldg(a.packed + g) : 0u;
@@ -237,7 +268,7 @@ __global__ void __launch_bounds__(kSkThreads, 4) k_sketch(SketchArgs a, uint32_t
     {
       const int per = (nh + kSkThreads - 1) / kSkThreads;
       const int x0 = tid * per;
-      int64_t segend = -1, segstart = 0;
+      int64_t segend = s_seg_hi, segstart = s_seg_lo;
       for (int r = 0; r < per; ++r) {
         const int x = x0 + r;
         if (x >= nh) break;
@@ -271,8 +302,8 @@ __global__ void __launch_bounds__(kSkThreads, 4) k_sketch(SketchArgs a, uint32_t
             }
           }
         }
-        s_h[x] = h;
-        s_sg[x] = (uint8_t)sg;
+        s_h[hslot(x)] = h;
+        s_sg[hslot(x)] = (uint8_t)sg;
       }
     }
     __syncthreads();
@@ -281,7 +312,7 @@ __global__ void __launch_bounds__(kSkThreads, 4) k_sketch(SketchArgs a, uint32_t
     const int B = tid * kSkWPT;
     uint64_t key[kSkWPT + 1];
     auto kx = [&](int x) -> uint64_t {
-      return ((uint64_t)s_h[x] << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)x);
+      return ((uint64_t)s_h[hslot(x)] << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)x);
     };
     if (w <= kSkWPT) {
 #pragma unroll
@@ -309,7 +340,7 @@ __global__ void __launch_bounds__(kSkThreads, 4) k_sketch(SketchArgs a, uint32_t
     // validity and selection flags for windows t = 1..8
     uint32_t flags = 0;
     {
-      int64_t segend = -1, segstart = 0;
+      int64_t segend = s_seg_hi, segstart = s_seg_lo;
       bool prev_ok = false;
       uint32_t prev_arg = 0;
 #pragma unroll
@@ -332,7 +363,7 @@ __global__ void __launch_bounds__(kSkThreads, 4) k_sketch(SketchArgs a, uint32_t
     }
     const int cnt = __popc(flags);
     int total;
-    const int excl = block_exclusive_sum(cnt, s_tmp, &total);
+    const int excl = tile_exclusive_sum(cnt, s_tmp, &total);
     if (kMode == 0) {
       if (tid == 0) tile_count[tile] = (uint32_t)total;
     } else {
@@ -350,7 +381,7 @@ __global__ void __launch_bounds__(kSkThreads, 4) k_sketch(SketchArgs a, uint32_t
           const uint32_t x = 0xFFFFFFFFu - (uint32_t)key[t];
           const uint64_t pos = (uint64_t)(HB + x);
           if (o < cap)
-            out[o] = ((uint64_t)s_h[x] << 33) | (pos << 1) | (uint64_t)s_sg[x];
+            out[o] = ((uint64_t)s_h[hslot((int)x)] << 33) | (pos << 1) | (uint64_t)s_sg[hslot((int)x)];
           ++o;
         }
       }
