@@ -691,7 +691,7 @@ def run_workload(args):
         "e2e": {"value": ws * N / (e2e_ms / 1000) / 1e6, "unit": "Mbp/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(N + 8 * len(W.offsets)),
                 "d2h_bytes_per_step": int(nc_host * 40),
-                "call": "sedef_selfsearch_host (pinned host input, candidates copied back)"},
+                "call": "sedef_selfsearch_host (page-locked host input read in place by the pack kernel over the host link, candidates copied back)"},
         "roofline": roof,
         "families": families,
         "cpu_baseline": cpu,

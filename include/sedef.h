@@ -478,10 +478,13 @@ int sedef_selfsearch(sedef_ctx* ctx, const uint8_t* d_seq, const int64_t* h_seq_
                      int64_t* h_ncands);
 
 /*
- * Whole self-search through host buffers: copies h_seq (total bytes
+ * Whole self-search through host buffers: brings h_seq (total bytes
  * h_seq_off[nseq]) to the device, runs sedef_selfsearch's stages on the
- * context's stream, and copies the candidates back to h_cands.  Device
- * memory comes from the context.  Synchronizes.
+ * context's stream, and copies the candidates back to h_cands.  Page-locked
+ * h_seq (cudaHostAlloc / cudaHostRegister) is read once by the packing
+ * kernel through its device mapping; pageable h_seq is copied to device
+ * memory first.  Either way h_seq must stay unchanged until the call
+ * returns.  Device memory comes from the context.  Synchronizes.
  */
 int sedef_selfsearch_host(sedef_ctx* ctx, const uint8_t* h_seq, const int64_t* h_seq_off,
                           int32_t nseq, const sedef_params* p, sedef_cand_t* h_cands, int64_t cap,

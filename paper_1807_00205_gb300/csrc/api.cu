@@ -776,11 +776,23 @@ int sedef_selfsearch_host(sedef_ctx* ctx, const uint8_t* h_seq, const int64_t* h
   const int64_t N = h_seq_off[nseq];
   cudaStream_t st = ctx->stream;
   ctx->io.reset();
-  uint8_t* seq = (uint8_t*)ctx->io.alloc((size_t)N);
-  if (!seq) return fail(SEDEF_ERR_OOM, "selfsearch: device allocation failed");
-  if (cudaMemcpyAsync(seq, h_seq, (size_t)N, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-    cudaStreamSynchronize(st);
-    return fail(SEDEF_ERR_CUDA, "selfsearch: H2D copy failed");
+  // Page-locked input is read by the pack kernel in place, through its
+  // device mapping (one pass over the host link, no staging copy); any other
+  // host memory is copied to the device first.
+  const uint8_t* seq = nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, h_seq) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+      at.devicePointer != nullptr) {
+    seq = (const uint8_t*)at.devicePointer;
+  } else {
+    cudaGetLastError();
+    uint8_t* d = (uint8_t*)ctx->io.alloc((size_t)N);
+    if (!d) return fail(SEDEF_ERR_OOM, "selfsearch: device allocation failed");
+    if (cudaMemcpyAsync(d, h_seq, (size_t)N, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      cudaStreamSynchronize(st);
+      return fail(SEDEF_ERR_CUDA, "selfsearch: H2D copy failed");
+    }
+    seq = d;
   }
   sedef_cand_t* cands = nullptr;
   int64_t nc = 0;
