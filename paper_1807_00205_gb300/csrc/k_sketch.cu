@@ -208,10 +208,43 @@ __device__ __forceinline__ int tile_exclusive_sum(int v, int* tmp, int* total) {
   return tmp[warp] + inc - v;
 }
 
+// Window minima for the windows starting at local slot B + t, t in
+// [0, kSkWPT]: key[t] = min over slots [B + t, B + t + w) of kx(slot).
+template <typename K, typename KX>
+__device__ __forceinline__ void window_minima(int w, int B, KX kx, K (&key)[kSkWPT + 1]) {
+  const K inf = ~K(0);
+  if (w <= kSkWPT) {
+#pragma unroll
+    for (int t = 0; t <= kSkWPT; ++t) {
+      K m = inf;
+      for (int x = B + t; x < B + t + w; ++x) m = min(m, kx(x));
+      key[t] = m;
+    }
+  } else {
+    // suffix minima over [B+t, B+7], middle over [B+8, B+w-1], prefix
+    // minima over [B+w, B+w+t-1]
+    K suf[kSkWPT + 1];
+    suf[kSkWPT] = inf;
+#pragma unroll
+    for (int t = kSkWPT - 1; t >= 0; --t) suf[t] = min(suf[t + 1], kx(B + t));
+    K mid = inf;
+    for (int x = B + kSkWPT; x < B + w; ++x) mid = min(mid, kx(x));
+    K pre = inf;
+#pragma unroll
+    for (int t = 0; t <= kSkWPT; ++t) {
+      if (t > 0) pre = min(pre, kx(B + w + t - 1));
+      key[t] = min(min(suf[t], mid), pre);
+    }
+  }
+}
+
 // kMode 0: count the records of each tile; 1: write them at the tile
 // offsets given; 2: one pass, offsets by look-back.  Four CTAs per SM (64
 // registers a thread): while one CTA's warp 0 walks back, the others compute.
-template <int kMode>
+// kNarrow (2k <= 24 and w + kSkWPT <= 128): a window key is 32 bits, the
+// hash (ineligible as 2^24) over 7 bits of the slot's reversed offset from
+// the thread's first slot, so that equal hashes still go to the rightmost.
+template <int kMode, bool kNarrow>
 __global__ void __launch_bounds__(kSkThreads, 4) k_sketch(SketchArgs a, uint32_t* __restrict__ tile_count,
                                                        const uint32_t* __restrict__ tile_offset,
                                                        uint64_t* __restrict__ out, int64_t cap,
@@ -269,18 +302,22 @@ __global__ void __launch_bounds__(kSkThreads, 4) k_sketch(SketchArgs a, uint32_t
       const int per = (nh + kSkThreads - 1) / kSkThreads;
       const int x0 = tid * per;
       int64_t segend = s_seg_hi, segstart = s_seg_lo;
+      // every k-mer of this thread inside the tile's first sequence: no
+      // per-position bounds checks
+      const int xe = min(x0 + per, nh);
+      const bool inside = HB + x0 >= segstart && HB + xe - 1 + k <= segend;
       for (int r = 0; r < per; ++r) {
         const int x = x0 + r;
         if (x >= nh) break;
         const int64_t p = HB + x;
         uint32_t h = kInfHash, sg = 0;
-        if (p >= 0 && p + k <= a.N) {
-          if (p >= segend || p < segstart) {
+        if (inside || (p >= 0 && p + k <= a.N)) {
+          if (!inside && (p >= segend || p < segstart)) {
             const int s = seq_of(a.off, a.nseq, p);
             segstart = a.off[s];
             segend = a.off[s + 1];
           }
-          if (p + k <= segend) {
+          if (inside || p + k <= segend) {
             const int64_t lp = p - (wb16 << 4);
             const int wi = (int)(lp >> 4), sh = (int)(lp & 15) * 2;
             const uint64_t pair = (uint64_t)s_pk[wi] | ((uint64_t)s_pk[wi + 1] << 32);
@@ -310,52 +347,57 @@ __global__ void __launch_bounds__(kSkThreads, 4) k_sketch(SketchArgs a, uint32_t
 
     // ---- windows q = HB + B + t, t in [0, 9): local hash range [B + t, B + t + w)
     const int B = tid * kSkWPT;
-    uint64_t key[kSkWPT + 1];
-    auto kx = [&](int x) -> uint64_t {
-      return ((uint64_t)s_h[hslot(x)] << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)x);
-    };
-    if (w <= kSkWPT) {
+    uint32_t xs[kSkWPT + 1];  // slot of each window's minimizer
+    uint32_t inf = 0;         // bit t: window t's minimum is ineligible
+    if (kNarrow) {
+      uint32_t key[kSkWPT + 1];
+      auto kx = [&](int x) -> uint32_t {
+        return (min(s_h[hslot(x)], 1u << 24) << 7) | (uint32_t)(127 - (x - B));
+      };
+      window_minima(w, B, kx, key);
 #pragma unroll
       for (int t = 0; t <= kSkWPT; ++t) {
-        uint64_t m = ~0ull;
-        for (int x = B + t; x < B + t + w; ++x) m = min(m, kx(x));
-        key[t] = m;
+        xs[t] = (uint32_t)(B + 127) - (key[t] & 127u);
+        if ((key[t] >> 7) >= (1u << 24)) inf |= 1u << t;
       }
     } else {
-      // suffix minima over [B+t, B+7], middle over [B+8, B+w-1], prefix
-      // minima over [B+w, B+w+t-1]
-      uint64_t suf[kSkWPT + 1];
-      suf[kSkWPT] = ~0ull;
-#pragma unroll
-      for (int t = kSkWPT - 1; t >= 0; --t) suf[t] = min(suf[t + 1], kx(B + t));
-      uint64_t mid = ~0ull;
-      for (int x = B + kSkWPT; x < B + w; ++x) mid = min(mid, kx(x));
-      uint64_t pre = ~0ull;
+      uint64_t key[kSkWPT + 1];
+      auto kx = [&](int x) -> uint64_t {
+        return ((uint64_t)s_h[hslot(x)] << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)x);
+      };
+      window_minima(w, B, kx, key);
 #pragma unroll
       for (int t = 0; t <= kSkWPT; ++t) {
-        if (t > 0) pre = min(pre, kx(B + w + t - 1));
-        key[t] = min(min(suf[t], mid), pre);
+        xs[t] = 0xFFFFFFFFu - (uint32_t)key[t];
+        if ((uint32_t)(key[t] >> 32) == kInfHash) inf |= 1u << t;
       }
     }
     // validity and selection flags for windows t = 1..8
     uint32_t flags = 0;
     {
       int64_t segend = s_seg_hi, segstart = s_seg_lo;
+      // all nine windows inside the tile's first sequence
+      const bool inside = HB + B >= segstart && HB + B + kSkWPT + w + k - 1 <= segend;
       bool prev_ok = false;
       uint32_t prev_arg = 0;
 #pragma unroll
       for (int t = 0; t <= kSkWPT; ++t) {
         const int64_t q = HB + B + t;
-        bool ok = false;
-        if (q >= 0 && q + w + k - 1 <= a.N) {
-          if (q >= segend || q < segstart) {
-            const int s = seq_of(a.off, a.nseq, q);
-            segstart = a.off[s];
-            segend = a.off[s + 1];
+        bool ok;
+        if (inside) {
+          ok = !((inf >> t) & 1u);
+        } else {
+          ok = false;
+          if (q >= 0 && q + w + k - 1 <= a.N) {
+            if (q >= segend || q < segstart) {
+              const int s = seq_of(a.off, a.nseq, q);
+              segstart = a.off[s];
+              segend = a.off[s + 1];
+            }
+            ok = (q + w + k - 1 <= segend) && !((inf >> t) & 1u);
           }
-          ok = (q + w + k - 1 <= segend) && ((uint32_t)(key[t] >> 32) != kInfHash);
         }
-        const uint32_t arg = 0xFFFFFFFFu - (uint32_t)key[t];
+        const uint32_t arg = xs[t];
         if (t > 0 && ok && !(prev_ok && prev_arg == arg)) flags |= 1u << t;
         prev_ok = ok;
         prev_arg = arg;
@@ -378,7 +420,7 @@ __global__ void __launch_bounds__(kSkThreads, 4) k_sketch(SketchArgs a, uint32_t
 #pragma unroll
       for (int t = 1; t <= kSkWPT; ++t) {
         if (flags >> t & 1u) {
-          const uint32_t x = 0xFFFFFFFFu - (uint32_t)key[t];
+          const uint32_t x = xs[t];
           const uint64_t pos = (uint64_t)(HB + x);
           if (o < cap)
             out[o] = ((uint64_t)s_h[hslot((int)x)] << 33) | (pos << 1) | (uint64_t)s_sg[hslot((int)x)];
@@ -388,6 +430,9 @@ __global__ void __launch_bounds__(kSkThreads, 4) k_sketch(SketchArgs a, uint32_t
     }
   }
 }
+
+// The 32-bit window keys hold a hash of 2k bits and a 7-bit slot offset.
+bool narrow_keys(const Derived& D) { return 2 * D.k <= 24 && D.w + kSkWPT <= 128; }
 
 }  // namespace
 
@@ -437,6 +482,7 @@ int run_sketch(sedef_ctx* ctx, const uint32_t* packed, const uint32_t* mask, con
     SEDEF_CUDA(cudaStreamSynchronize(st));  // h_off is caller memory: copy before returning
   }
   a.off = d_off;
+  const bool narrow = narrow_keys(D);
   int64_t grid = a.ntiles;
   const int64_t maxgrid = (int64_t)ctx_sm_count(ctx) * 8;
   if (grid > maxgrid) grid = maxgrid;
@@ -454,8 +500,12 @@ int run_sketch(sedef_ctx* ctx, const uint32_t* packed, const uint32_t* mask, con
     lb.total = status + 1;
     lb.err = (int*)(status + 2);
     SEDEF_CUDA(cudaMemsetAsync(status, 0, (size_t)(a.ntiles + 4) * 8, st));
-    SEDEF_KERNEL(ctx, "k_sketch",
-                 k_sketch<2><<<(int)grid, kSkThreads, 0, st>>>(a, nullptr, nullptr, rec, cap, lb));
+    if (narrow)
+      SEDEF_KERNEL(ctx, "k_sketch",
+                   k_sketch<2, true><<<(int)grid, kSkThreads, 0, st>>>(a, nullptr, nullptr, rec, cap, lb));
+    else
+      SEDEF_KERNEL(ctx, "k_sketch",
+                   k_sketch<2, false><<<(int)grid, kSkThreads, 0, st>>>(a, nullptr, nullptr, rec, cap, lb));
     unsigned long long* h = (unsigned long long*)ctx_host(ctx, 16);
     if (!h) return SEDEF_ERR_OOM;
     SEDEF_CUDA(cudaMemcpyAsync(h, status + 1, 16, cudaMemcpyDeviceToHost, st));
@@ -471,14 +521,22 @@ int run_sketch(sedef_ctx* ctx, const uint32_t* packed, const uint32_t* mask, con
   uint32_t* cnt = (uint32_t*)ctx_alloc(ctx, (size_t)(a.ntiles + 1) * 4);
   uint32_t* toff = (uint32_t*)ctx_alloc(ctx, (size_t)(a.ntiles + 1) * 4);
   if (!cnt || !toff) return SEDEF_ERR_OOM;
-  SEDEF_KERNEL(ctx, "k_sketch_count",
-               k_sketch<0><<<(int)grid, kSkThreads, 0, st>>>(a, cnt, nullptr, nullptr, 0, LookBack{}));
+  if (narrow)
+    SEDEF_KERNEL(ctx, "k_sketch_count",
+                 k_sketch<0, true><<<(int)grid, kSkThreads, 0, st>>>(a, cnt, nullptr, nullptr, 0, LookBack{}));
+  else
+    SEDEF_KERNEL(ctx, "k_sketch_count",
+                 k_sketch<0, false><<<(int)grid, kSkThreads, 0, st>>>(a, cnt, nullptr, nullptr, 0, LookBack{}));
   SEDEF_TRY(scan_exclusive_u32(ctx, cnt, toff, a.ntiles, toff + a.ntiles));
   pl->n_rec = toff + a.ntiles;
   SEDEF_TRY(plan_check(ctx, pl, toff + a.ntiles, cap, 0));
   *nrec = cap;
-  SEDEF_KERNEL(ctx, "k_sketch_write",
-               k_sketch<1><<<(int)grid, kSkThreads, 0, st>>>(a, nullptr, toff, rec, cap, LookBack{}));
+  if (narrow)
+    SEDEF_KERNEL(ctx, "k_sketch_write",
+                 k_sketch<1, true><<<(int)grid, kSkThreads, 0, st>>>(a, nullptr, toff, rec, cap, LookBack{}));
+  else
+    SEDEF_KERNEL(ctx, "k_sketch_write",
+                 k_sketch<1, false><<<(int)grid, kSkThreads, 0, st>>>(a, nullptr, toff, rec, cap, LookBack{}));
   return SEDEF_OK;
 }
 
@@ -583,7 +641,10 @@ extern "C" int sedef_sketch_noalloc(const uint32_t* d_packed, const uint32_t* d_
   int sms = 0;
   SEDEF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   int64_t grid = a.ntiles < (int64_t)sms * 8 ? a.ntiles : (int64_t)sms * 8;
-  k_sketch<0><<<(int)grid, kSkThreads, 0, st>>>(a, cnt, nullptr, nullptr, 0, LookBack{});
+  if (narrow_keys(D))
+    k_sketch<0, true><<<(int)grid, kSkThreads, 0, st>>>(a, cnt, nullptr, nullptr, 0, LookBack{});
+  else
+    k_sketch<0, false><<<(int)grid, kSkThreads, 0, st>>>(a, cnt, nullptr, nullptr, 0, LookBack{});
   count_launch();
   SEDEF_LAUNCHED("k_sketch_count");
   k_scan_one_block<<<1, 1024, 0, st>>>(cnt, toff, a.ntiles);
@@ -594,7 +655,10 @@ extern "C" int sedef_sketch_noalloc(const uint32_t* d_packed, const uint32_t* d_
   SEDEF_CUDA(cudaStreamSynchronize(st));
   *h_nrec = total;
   if ((int64_t)total > rec_cap) return fail(SEDEF_ERR_CAPACITY, "record buffer too small");
-  k_sketch<1><<<(int)grid, kSkThreads, 0, st>>>(a, nullptr, toff, d_rec, rec_cap, LookBack{});
+  if (narrow_keys(D))
+    k_sketch<1, true><<<(int)grid, kSkThreads, 0, st>>>(a, nullptr, toff, d_rec, rec_cap, LookBack{});
+  else
+    k_sketch<1, false><<<(int)grid, kSkThreads, 0, st>>>(a, nullptr, toff, d_rec, rec_cap, LookBack{});
   count_launch();
   SEDEF_LAUNCHED("k_sketch_write");
   SEDEF_CUDA(cudaStreamSynchronize(st));
