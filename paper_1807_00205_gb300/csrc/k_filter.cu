@@ -306,89 +306,6 @@ struct QBuild {
   int* tmp;
 };
 
-// Postings of hash h restricted to target positions [lo, hi) (binary
-// searches inside the posting list, which is sorted by position).
-// First x in [a0, a1) whose record position is >= key (a1 when none): the
-// same answer as a binary search, found with fewer dependent loads.  A
-// posting list of a batch spans every genome with positions spread over the
-// whole target, so one interpolation probe lands near the answer; a gallop
-// from it brackets the answer and a binary search finishes inside the
-// bracket.  Invariant: pos(lo) < key <= pos(hi).
-__host__ __device__ __forceinline__ uint32_t pos_lower_bound(const uint64_t* idx, uint32_t a0,
-                                                             uint32_t a1, int64_t key) {
-  if (a0 >= a1) return a0;
-  const int64_t pf = rec_pos(idx[a0]), pl = rec_pos(idx[a1 - 1]);
-  if (pf >= key) return a0;
-  if (pl < key) return a1;
-  uint32_t lo = a0, hi = a1 - 1;
-  if (hi - lo > 1) {
-    // (key - pf) / (pl - pf) is in (0, 1]; any probe strictly inside the
-    // bracket is correct, so a single-precision estimate clamped into it
-    // will do (an integer division here costs more than a search step)
-    const float f = (float)(key - pf) / (float)(pl - pf) * (float)(hi - lo - 1);
-    const uint32_t g = lo + 1 + (f < (float)(hi - lo - 2) ? (uint32_t)f : hi - lo - 2);
-    uint32_t step = 1;
-    if ((int64_t)rec_pos(idx[g]) >= key) {
-      hi = g;
-      while (hi - lo > 1) {  // gallop down
-        const uint32_t c = hi - lo > step ? hi - step : lo;
-        if (c == lo) break;
-        if ((int64_t)rec_pos(idx[c]) >= key) {
-          hi = c;
-          step <<= 1;
-        } else {
-          lo = c;
-          break;
-        }
-      }
-    } else {
-      lo = g;
-      while (hi - lo > 1) {  // gallop up
-        const uint32_t c = hi - lo > step ? lo + step : hi;
-        if (c == hi) break;
-        if ((int64_t)rec_pos(idx[c]) < key) {
-          lo = c;
-          step <<= 1;
-        } else {
-          hi = c;
-          break;
-        }
-      }
-    }
-  }
-  while (hi - lo > 1) {
-    const uint32_t mid = lo + ((hi - lo) >> 1);
-    if ((int64_t)rec_pos(idx[mid]) >= key) hi = mid; else lo = mid;
-  }
-  return hi;
-}
-
-// First x in [a0, a1) whose record position is >= key, galloping forward
-// from a0: the answer is expected a few entries on (the postings of one
-// genome of a batch).
-__host__ __device__ __forceinline__ uint32_t pos_gallop_forward(const uint64_t* idx, uint32_t a0,
-                                                                uint32_t a1, int64_t key) {
-  if (a0 >= a1 || (int64_t)rec_pos(idx[a0]) >= key) return a0;
-  uint32_t lo = a0, hi = a1;  // pos(lo) < key; pos(hi) >= key, or hi = a1
-  uint32_t step = 1;
-  while (hi - lo > 1) {
-    const uint32_t c = hi - lo > step ? lo + step : hi;
-    if (c == hi) break;
-    if ((int64_t)rec_pos(idx[c]) < key) {
-      lo = c;
-      step <<= 1;
-    } else {
-      hi = c;
-      break;
-    }
-  }
-  while (hi - lo > 1) {
-    const uint32_t mid = lo + ((hi - lo) >> 1);
-    if ((int64_t)rec_pos(idx[mid]) >= key) hi = mid; else lo = mid;
-  }
-  return hi;
-}
-
 // Record positions of every kSampleStride-th entry of the sorted index
 // (samp[k] = pos(idx[k * kSampleStride])): a search first brackets its
 // answer between two samples, an array small enough to stay in L2, and then
@@ -1790,13 +1707,16 @@ __global__ void __launch_bounds__(32 * (kLean ? kRWarps : kRWarpsBig)) k_refine(
 // A warp sets up runs one at a time (cooperatively) into slots of a per-warp
 // arena, then every lane rolls its own run through its slot, so many rolls
 // proceed side by side.  Setup per run: the span records are read once
-// (hash, W_Q membership, candidate flag); the domain is W_Q (already
-// sorted) merged by rank with the sorted distinct non-W_Q kept hashes, so
-// W_Q is never re-sorted; slots keep 16-bit offsets of positions and one
-// counter per domain hash (presence for non-W_Q hashes, sharedness for W_Q
-// hashes).  Transient setup data lives in the arena above the new slot.
-// Runs beyond the lean limits (more than 256 query records, 512 span
-// records or a span of 65,536 bases) go to the large kernel.
+// (hash, rank among W_Q, W_Q membership, candidate flag); the domain is W_Q
+// (already sorted) merged by rank with the sorted distinct non-W_Q kept
+// hashes, so a kept record's domain index is its rank among W_Q plus its
+// rank among those hashes.  A slot holds one 32-bit event per kept record
+// (offset of its position from j_a, domain index, W_Q flag) and one counter
+// per domain hash (presence for non-W_Q hashes, sharedness for W_Q hashes).
+// Transient setup data (the span records' hashes, sort buffers) lives at the
+// top of the arena, slots grow from the bottom.  Runs beyond the lean limits
+// (more than 256 query records, 512 span records or a span of 65,536 bases)
+// go to the large kernel.
 
 constexpr int kBWarps = 4;
 constexpr int kBQC = 256, kBRC = 512;
@@ -1805,60 +1725,50 @@ constexpr int kArenaWords = 2816;  // 11 KB per warp
 struct BatchWarp {
   uint32_t arena[kArenaWords];
   uint32_t wq_h[kBQC];
-  uint16_t wq_dom[kBQC];  // domain index of each W_Q hash (current run)
   uint8_t wq_m[kBQC];
-  uint8_t rflag[kBRC];    // span record: bit0 strand, bit1 in W_Q, bit2 candidate, bit3 kept
+  // span record: bit0 strand, bit1 in W_Q, bit2 candidate, bit3 kept,
+  // bits 4.. its hash's rank among W_Q (lower bound)
+  uint16_t rinfo[kBRC];
   uint32_t h_off[32];     // slot start (words)
   uint32_t h_run[32];     // run index
   uint16_t h_nrel[32], h_D[32], h_dmax[32], h_s[32];
 };
 
 struct Slot {
-  uint16_t* tpos;  // position - j_a
-  uint16_t* tdx;   // domain index
-  uint8_t* tsh;    // 1: a W_Q hash (shared-compatible occurrence); 0: a non-W_Q hash
+  uint32_t* ev;    // per kept record: position - j_a (bits 0-15), domain index (16-25), W_Q (31)
   uint16_t* cnt;   // per domain hash: occurrences in the window
-  uint8_t* qm;     // nonzero for W_Q hashes
   uint32_t* pb;    // present
   uint32_t* sb;    // shared
 };
 
 __device__ __forceinline__ int slot_words(int nrel, int dmax) {
-  return (nrel + 1) / 2 + (nrel + 1) / 2 + (nrel + 3) / 4 + (dmax + 1) / 2 + (dmax + 3) / 4 +
-         2 * ((dmax + 31) / 32);
+  return nrel + (dmax + 1) / 2 + 2 * ((dmax + 31) / 32);
 }
 
 __device__ __forceinline__ Slot slot_at(uint32_t* base, int nrel, int dmax) {
   Slot sl;
-  uint32_t* p = base;
-  sl.tpos = reinterpret_cast<uint16_t*>(p);
-  p += (nrel + 1) / 2;
-  sl.tdx = reinterpret_cast<uint16_t*>(p);
-  p += (nrel + 1) / 2;
-  sl.tsh = reinterpret_cast<uint8_t*>(p);
-  p += (nrel + 3) / 4;
-  sl.cnt = reinterpret_cast<uint16_t*>(p);
-  p += (dmax + 1) / 2;
-  sl.qm = reinterpret_cast<uint8_t*>(p);
-  p += (dmax + 3) / 4;
-  sl.pb = p;
-  sl.sb = p + (dmax + 31) / 32;
+  sl.ev = base;
+  sl.cnt = reinterpret_cast<uint16_t*>(base + nrel);
+  sl.pb = base + nrel + (dmax + 1) / 2;
+  sl.sb = sl.pb + (dmax + 31) / 32;
   return sl;
 }
 
-// Rolls one run (single lane): enters the first window's records, finds
-// theta (s-th present hash) and est by scanning the bitsets, then keeps both
-// exact through every enter/leave (as in the large kernel).
-__device__ void roll_run(const Slot& sl, int nrel, int D, int s, int mx, int64_t plo, int64_t phi,
-                         int span, int* best_out, int64_t* jstar_out) {
+// Rolls one run (single lane) over target starts j_a + [0, jend]: enters the
+// first window's records, finds theta (s-th present hash) and est by
+// scanning the bitsets, then keeps both exact through every enter/leave (as
+// in the large kernel).  Offsets from j_a fit in 16 bits, so the roll runs
+// in 32-bit arithmetic.
+__device__ void roll_run(const Slot& sl, int nrel, int D, int s, int mx, int jend, int span,
+                         int* best_out, int* jstar_out) {
   const int nwords = (D + 31) >> 5;
-  const int64_t base = plo;
-  int e = 0, l = 0;
-  int64_t j = plo;
-  while (e < nrel && base + sl.tpos[e] <= j + span) {
-    const int d = sl.tdx[e];
+  auto pos = [&](int x) { return (int)(sl.ev[x] & 0xFFFFu); };
+  int e = 0, l = 0, j = 0;
+  while (e < nrel && pos(e) <= j + span) {
+    const uint32_t v = sl.ev[e];
+    const int d = (int)((v >> 16) & 0x3FFu);
     if (sl.cnt[d]++ == 0) {
-      if (sl.tsh[e]) sl.sb[d >> 5] |= 1u << (d & 31);
+      if (v >> 31) sl.sb[d >> 5] |= 1u << (d & 31);
       else sl.pb[d >> 5] |= 1u << (d & 31);
     }
     ++e;
@@ -1894,23 +1804,23 @@ __device__ void roll_run(const Slot& sl, int nrel, int D, int s, int mx, int64_t
     while (bits == 0 && w + 1 < nwords) bits = sl.pb[++w];
     return bits ? w * 32 + __ffs(bits) - 1 : d;
   };
-  int best = -1;
-  int64_t jstar = plo;
+  int best = -1, jstar = 0;
   while (true) {
     if (est > best) {
       best = est;
       jstar = j;
       if (best >= mx) break;
     }
-    const int64_t ne = e < nrel ? base + sl.tpos[e] - span : INT64_MAX;
-    const int64_t nl = l < e ? base + sl.tpos[l] + 1 : INT64_MAX;
-    const int64_t nx = min(ne, nl);
-    if (nx > phi) break;
+    const int ne = e < nrel ? pos(e) - span : INT_MAX;
+    const int nl = l < e ? pos(l) + 1 : INT_MAX;
+    const int nx = min(ne, nl);
+    if (nx > jend) break;
     j = nx;
-    while (l < e && base + sl.tpos[l] + 1 <= j) {
-      const int d = sl.tdx[l];
+    while (l < e && pos(l) + 1 <= j) {
+      const uint32_t v = sl.ev[l];
+      const int d = (int)((v >> 16) & 0x3FFu);
       if (--sl.cnt[d] == 0) {
-        if (sl.tsh[l]) {
+        if (v >> 31) {
           sl.sb[d >> 5] &= ~(1u << (d & 31));
           if (d <= theta) --est;
         } else {
@@ -1923,10 +1833,11 @@ __device__ void roll_run(const Slot& sl, int nrel, int D, int s, int mx, int64_t
       }
       ++l;
     }
-    while (e < nrel && base + sl.tpos[e] - span <= j) {
-      const int d = sl.tdx[e];
+    while (e < nrel && pos(e) - span <= j) {
+      const uint32_t v = sl.ev[e];
+      const int d = (int)((v >> 16) & 0x3FFu);
       if (sl.cnt[d]++ == 0) {
-        if (sl.tsh[e]) {
+        if (v >> 31) {
           sl.sb[d >> 5] |= 1u << (d & 31);
           if (d <= theta) ++est;
         } else {
@@ -1972,13 +1883,12 @@ __global__ void __launch_bounds__(32 * kBWarps) k_refine_batch(RefineArgs a) {
       const sedef_run_t run = a.runs[ri];
       const int nrel = B.h_nrel[lane], D = B.h_D[lane], sq = B.h_s[lane];
       const Slot sl = slot_at(B.arena + B.h_off[lane], nrel, B.h_dmax[lane]);
-      int best;
-      int64_t jstar;
-      roll_run(sl, nrel, D, sq, run.max_shared, run.j_a, run.j_b, a.span, &best, &jstar);
+      int best, jstar;
+      roll_run(sl, nrel, D, sq, run.max_shared, (int)(run.j_b - run.j_a), a.span, &best, &jstar);
       sedef_run_t& out = a.runs[ri];
       out.est = (uint16_t)(best < 0 ? 0 : best);
       out.den = (uint16_t)sq;
-      out.j_star = (uint32_t)jstar;
+      out.j_star = run.j_a + (uint32_t)jstar;
       out.keep = (best >= a.mtab[sq]) ? 1 : 0;
     }
     __syncwarp();
@@ -2004,13 +1914,14 @@ __global__ void __launch_bounds__(32 * kBWarps) k_refine_batch(RefineArgs a) {
         if (lane == 0) a.big[atomicAdd(a.nbig, 1u)] = (uint32_t)ri;
         continue;
       }
-      // ---- W_Q (kept from the previous run of the same window)
+      // ---- W_Q (kept from the previous run of the same window); sorted in
+      // a transient buffer at the top of the arena
       if (qa != prev_qa || qb != prev_qb) {
         prev_qa = qa;
         prev_qb = qb;
         const int npq = next_pow2(c < 2 ? 2 : c);
         if (used + npq > kArenaWords) flush();
-        uint32_t* buf = B.arena + used;  // sort space above the slots (transient)
+        uint32_t* buf = B.arena + kArenaWords - npq;
         for (int x = lane; x < npq; x += 32) {
           uint32_t key = kNone;
           if (x < c) {
@@ -2044,16 +1955,12 @@ __global__ void __launch_bounds__(32 * kBWarps) k_refine_batch(RefineArgs a) {
         }
         __syncwarp();
       }
-      auto wq_find = [&](uint32_t h) {
-        const int lo2 = lb_u32(B.wq_h, s, h);
-        return (lo2 < s && B.wq_h[lo2] == h) ? lo2 : -1;
-      };
-      // ---- space: the slot's worst case plus transient hashes and sort buffer
-      const int slot_bound = slot_words(nr, s + nr);
-      const int need = slot_bound + nr + next_pow2(nr < 2 ? 2 : nr);
-      if (nslots == 32 || used + need > kArenaWords) flush();
-      // ---- pass over the span records: hash (transient), flags, max(C)
-      uint32_t* th = B.arena + used + slot_bound;  // transient: hashes of the span records
+      // ---- space: the span records' hashes and the largest sort buffer at
+      // the top of the arena (the slot's exact size is checked below)
+      const int npr = next_pow2(nr < 2 ? 2 : nr);
+      if (nslots == 32 || used + nr + npr > kArenaWords) flush();
+      uint32_t* th = B.arena + kArenaWords - nr;  // transient: hashes of the span records
+      // ---- pass over the span records: hash, rank among W_Q, flags, max(C)
       uint32_t cmax = 0;
       bool have_c = false;
       for (int base = 0; base < nr; base += 32) {
@@ -2064,11 +1971,12 @@ __global__ void __launch_bounds__(32 * kBWarps) k_refine_batch(RefineArgs a) {
           const uint64_t r = a.trec[rlo + x];
           h = rec_hash(r);
           const uint32_t t = rec_pos(r), st = rec_strand(r);
-          const int q = wq_find(h);
+          const int q = lb_u32(B.wq_h, s, h);
+          const bool member = q < s && B.wq_h[q] == h;
           const bool self = a.self_mode && (int64_t)t >= i && (int64_t)t <= i + a.span;
-          cand = q >= 0 && !self && ((B.wq_m[q] >> (st ^ (uint32_t)o)) & 1u);
+          cand = member && !self && ((B.wq_m[q] >> (st ^ (uint32_t)o)) & 1u);
           th[x] = h;
-          B.rflag[x] = (uint8_t)(st | ((q >= 0) ? 2u : 0u) | (cand ? 4u : 0u));
+          B.rinfo[x] = (uint16_t)(st | (member ? 2u : 0u) | (cand ? 4u : 0u) | ((uint32_t)q << 4));
         }
         uint32_t hm = cand ? h : 0u;
         const bool any = __any_sync(0xffffffffu, cand);
@@ -2086,19 +1994,20 @@ __global__ void __launch_bounds__(32 * kBWarps) k_refine_batch(RefineArgs a) {
         const int x = base + lane;
         bool keep = false, nonq = false;
         if (x < nr) {
-          const uint32_t f = B.rflag[x];
+          const uint32_t f = B.rinfo[x];
           nonq = !(f & 2u) && th[x] < cmax;
           keep = (f & 4u) || nonq;
-          if (keep) B.rflag[x] = (uint8_t)(f | 8u);
+          if (keep) B.rinfo[x] = (uint16_t)(f | 8u);
         }
         nrel += __popc(__ballot_sync(0xffffffffu, keep));
         n1 += __popc(__ballot_sync(0xffffffffu, nonq));
       }
       __syncwarp();
       const int dmax = s + n1;
-      const Slot sl = slot_at(B.arena + used, nrel, dmax);
-      uint32_t* u1 = th + nr;  // transient sort buffer of the non-W_Q kept hashes
       const int np1 = next_pow2(n1 < 2 ? 2 : n1);
+      uint32_t* u1 = th - np1;  // transient sort buffer of the non-W_Q kept hashes
+      if (used + slot_words(nrel, dmax) > kArenaWords - nr - np1) flush();
+      const Slot sl = slot_at(B.arena + used, nrel, dmax);
       {
         int y = 0, z = 0;
         for (int base = 0; base < nr && nrel > 0; base += 32) {
@@ -2106,7 +2015,7 @@ __global__ void __launch_bounds__(32 * kBWarps) k_refine_batch(RefineArgs a) {
           bool keep = false, nonq = false;
           uint32_t f = 0;
           if (x < nr) {
-            f = B.rflag[x];
+            f = B.rinfo[x];
             keep = (f & 8u) != 0;
             nonq = keep && !(f & 2u);
           }
@@ -2114,8 +2023,7 @@ __global__ void __launch_bounds__(32 * kBWarps) k_refine_batch(RefineArgs a) {
           const unsigned bn = __ballot_sync(0xffffffffu, nonq);
           if (keep) {
             const int yy = y + __popc(bk & lanemask_lt());
-            sl.tpos[yy] = (uint16_t)(rec_pos(a.trec[rlo + x]) - run.j_a);
-            sl.tsh[yy] = (f & 2u) ? 1 : 0;
+            sl.ev[yy] = (rec_pos(a.trec[rlo + x]) - run.j_a) | ((f & 2u) ? 0x80000000u : 0u);
           }
           if (nonq) u1[z + __popc(bn & lanemask_lt())] = th[x];
           y += __popc(bk);
@@ -2137,36 +2045,30 @@ __global__ void __launch_bounds__(32 * kBWarps) k_refine_batch(RefineArgs a) {
         u += __popc(bal);
       }
       const int D = s + u;
-      for (int k = lane; k < s; k += 32) B.wq_dom[k] = (uint16_t)(k + lb_u32(u1, u, B.wq_h[k]));
-      __syncwarp();
+      // domain index of a kept record: its hash's rank among W_Q plus its
+      // rank among the distinct non-W_Q kept hashes
       {
         int y = 0;
         for (int base = 0; base < nr && nrel > 0; base += 32) {
           const int x = base + lane;
-          const bool keep = x < nr && (B.rflag[x] & 8u);
+          const uint32_t f = x < nr ? B.rinfo[x] : 0u;
+          const bool keep = (f & 8u) != 0;
           const unsigned bk = __ballot_sync(0xffffffffu, keep);
           if (keep) {
-            const uint32_t h = th[x];
-            int d;
-            if (B.rflag[x] & 2u) d = B.wq_dom[wq_find(h)];
-            else d = lb_u32(u1, u, h) + lb_u32(B.wq_h, s, h);
-            sl.tdx[y + __popc(bk & lanemask_lt())] = (uint16_t)d;
+            const uint32_t d = (f >> 4) + (uint32_t)lb_u32(u1, u, th[x]);
+            sl.ev[y + __popc(bk & lanemask_lt())] |= d << 16;
           }
           y += __popc(bk);
         }
       }
-      for (int x = lane; x < dmax; x += 32) {
-        sl.cnt[x] = 0;
-        sl.qm[x] = 0;
-      }
+      for (int x = lane; x < dmax; x += 32) sl.cnt[x] = 0;
       for (int x = lane; x < (dmax + 31) / 32; x += 32) {
         sl.pb[x] = 0;
         sl.sb[x] = 0;
       }
       __syncwarp();
       for (int k = lane; k < s; k += 32) {
-        const int d = B.wq_dom[k];
-        sl.qm[d] = 1;
+        const int d = k + lb_u32(u1, u, B.wq_h[k]);
         atomicOr(&sl.pb[d >> 5], 1u << (d & 31));
       }
       if (lane == 0) {
@@ -2499,6 +2401,7 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   unsigned long long* counters = (unsigned long long*)ctx_alloc(ctx, 256);
   sedef_run_t* raw = (sedef_run_t*)ctx_alloc(ctx, (size_t)(cap > 0 ? cap : 1) * sizeof(sedef_run_t));
   if (!wi || !wqa || !wqb || !wseq || !ovl || !ovl1 || !counters || !raw) return SEDEF_ERR_OOM;
+
   SEDEF_CUDA(cudaMemsetAsync(counters, 0, 256, st));
 
   FArgs a;
