@@ -2,9 +2,10 @@
 // merge of chains into SD candidates.
 //
 // Chain: one warp per kept run.  Anchors are enumerated straight from the
-// index: each query minimizer of the window binary-searches its posting list
-// for the run's target span, so anchors come out sorted by (p, t') without a
-// sort (t' = t for o = 0; for o = 1 the posting list is walked backwards).
+// index: each query minimizer of the window searches its posting list for
+// the run's target span (an interpolated search, then a short gallop), so
+// anchors come out sorted by (p, t') without a sort (t' = t for o = 0; for
+// o = 1 the posting list is walked backwards).
 // The DP visits anchors in order; for anchor a the 32 lanes scan the
 // predecessors b (only those with p_b >= p_a - gap_max) and a warp max-reduce
 // over (f_b + 1, b) picks the predecessor with the larger count, then the
@@ -56,26 +57,30 @@ __device__ __forceinline__ void resolve(ChainArgs& a) {
   a.nt = live_n(a.nt, a.dnt);
 }
 
-__device__ __forceinline__ int64_t posting_lb(const uint64_t* idx, int64_t lo, int64_t hi,
-                                              uint32_t pos) {
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (rec_pos(idx[mid]) < pos) lo = mid + 1; else hi = mid;
+// Postings of query record q's hash inside run `run`'s target span
+// [j_a, j_b + n - k]: [*b0, *b1) of the index (empty when the list passes
+// max_occ).  The start comes from an interpolated search of the posting
+// list, the end from a gallop forward from it (the span is short).
+__device__ __forceinline__ void record_postings(const ChainArgs& a, const sedef_run_t& run,
+                                                uint64_t q, uint32_t* b0, uint32_t* b1) {
+  const uint32_t h = rec_hash(q);
+  const uint32_t st = a.toff[h], en = a.toff[h + 1];
+  if (a.max_occ > 0 && (int)(en - st) > a.max_occ) {
+    *b0 = *b1 = st;
+    return;
   }
-  return lo;
+  const uint32_t tlo = run.j_a, thi = run.j_b + (uint32_t)a.span;
+  *b0 = pos_lower_bound(a.tidx, st, en, (int64_t)tlo);
+  *b1 = pos_gallop_forward(a.tidx, *b0, en, (int64_t)thi + 1);
 }
 
-// Visits the anchors of run `r` contributed by query record x (lane-owned):
-// calls f(rank, p, t) for each, rank counting this record's anchors in
-// (p, t') order.  Returns the number of anchors.
+// Visits the anchors of run `run` contributed by query record q among the
+// postings [b0, b1): calls f(rank, p, t) for each, rank counting this
+// record's anchors in (p, t') order.  Returns the number of anchors.
 template <typename F>
-__device__ int record_anchors(const ChainArgs& a, const sedef_run_t& run, uint64_t q, F f) {
-  const uint32_t h = rec_hash(q), p = rec_pos(q), sq = rec_strand(q);
-  const uint32_t st = a.toff[h], en = a.toff[h + 1];
-  if (a.max_occ > 0 && (int)(en - st) > a.max_occ) return 0;
-  const uint32_t tlo = run.j_a, thi = run.j_b + (uint32_t)a.span;
-  const int64_t b0 = posting_lb(a.tidx, st, en, tlo);
-  const int64_t b1 = posting_lb(a.tidx, b0, en, thi + 1);
+__device__ int record_anchors(const ChainArgs& a, const sedef_run_t& run, uint64_t q, uint32_t b0,
+                              uint32_t b1, F f) {
+  const uint32_t p = rec_pos(q), sq = rec_strand(q);
   int cnt = 0;
   const int64_t i = run.i;
   auto visit = [&](int64_t y) {
@@ -89,7 +94,7 @@ __device__ int record_anchors(const ChainArgs& a, const sedef_run_t& run, uint64
   if (run.o == 0)
     for (int64_t y = b0; y < b1; ++y) visit(y);
   else
-    for (int64_t y = b1 - 1; y >= b0; --y) visit(y);
+    for (int64_t y = (int64_t)b1 - 1; y >= (int64_t)b0; --y) visit(y);
   return cnt;
 }
 
@@ -112,8 +117,12 @@ __global__ void k_anchor_count(ChainArgs a, uint32_t* count) {
     if (lane == 0) window_range(a, run.i, &qa, &qb);
     qa = __shfl_sync(0xffffffffu, qa, 0);
     qb = __shfl_sync(0xffffffffu, qb, 0);
-    for (int64_t x = qa + lane; x < qb; x += 32)
-      total += record_anchors(a, run, a.qrec[x], [](int, uint32_t, uint32_t) {});
+    for (int64_t x = qa + lane; x < qb; x += 32) {
+      const uint64_t q = a.qrec[x];
+      uint32_t b0, b1;
+      record_postings(a, run, q, &b0, &b1);
+      total += record_anchors(a, run, q, b0, b1, [](int, uint32_t, uint32_t) {});
+    }
     total = warp_sum(total);
   }
   if (lane == 0) {
@@ -143,11 +152,17 @@ __global__ void k_anchor_fill(ChainArgs a, const uint32_t* aoff, uint64_t* ancho
   for (int64_t x0 = qa; x0 < qb; x0 += 32) {
     const int64_t x = x0 + lane;
     int c = 0;
-    if (x < qb) c = record_anchors(a, run, a.qrec[x], [](int, uint32_t, uint32_t) {});
+    uint64_t q = 0;
+    uint32_t b0 = 0, b1 = 0;
+    if (x < qb) {
+      q = a.qrec[x];
+      record_postings(a, run, q, &b0, &b1);
+      c = record_anchors(a, run, q, b0, b1, [](int, uint32_t, uint32_t) {});
+    }
     const int inc = warp_inclusive_sum(c);
     const uint32_t my = base + (uint32_t)(inc - c);
     if (x < qb && c > 0)
-      record_anchors(a, run, a.qrec[x], [&](int rank, uint32_t p, uint32_t t) {
+      record_anchors(a, run, q, b0, b1, [&](int rank, uint32_t p, uint32_t t) {
         const uint32_t tp = run.o ? tref - t : t;
         anchors[my + rank] = ((uint64_t)p << 32) | tp;
       });
