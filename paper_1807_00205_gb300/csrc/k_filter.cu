@@ -905,6 +905,21 @@ __global__ void __launch_bounds__(32 * kWWarps) k_filter_warp(FArgs a, TierIO io
       atomicAdd(&S.slots[sl >> 1], 1u << ((sl & 1) * 16));
     });
     __syncwarp();
+    // A hit is collected only when its bin's counter and a neighbouring
+    // bin's (same strand) sum to m or more.  Word x of the table holds bin x
+    // (both strands), so when no two cyclically adjacent words reach m on
+    // either strand, nothing would be collected: the window ends here.
+    {
+      bool pass = false;
+      for (int x = lane; x < kWSlots / 2; x += 32) {
+        const uint32_t c = S.slots[x], d = S.slots[(x + 1) & (kWSlots / 2 - 1)];
+        pass |= (c & 0xFFFFu) + (d & 0xFFFFu) >= (uint32_t)m || (c >> 16) + (d >> 16) >= (uint32_t)m;
+      }
+      if (!__any_sync(0xffffffffu, pass)) {
+        if (io.stats && lane == 0) atomicAdd(a.stats + 0, (unsigned long long)H);
+        continue;
+      }
+    }
     each_hit([&](uint32_t t, uint32_t hid, uint32_t o) {
       const uint32_t b = t >> kBinShift;
       const uint32_t c0 = slot_count(S.slots, wslot_of(t, o));
