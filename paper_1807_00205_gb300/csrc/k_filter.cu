@@ -423,6 +423,99 @@ __device__ int build_wq(const FArgs& a, QBuild q, int c, int64_t seq_lo = 0, int
   return s_count;
 }
 
+// Posting ranges in index order (eager batch self-search).  The query
+// records of a self-search are the index's own records, and the entries of
+// the index with one hash in one genome form a run that is the narrowed
+// posting range of each of its records.  So the ranges come from one walk
+// over the index: a warp reads 32 consecutive entries, splits them into runs
+// by (hash, genome), and searches only for the ends of the runs that leave
+// its 32 entries.  Each range goes to its record, found by the rank of the
+// record's position among all record positions: a bitmap of the positions
+// with the count of set bits before each 32-bit word.
+struct RankWord {
+  uint32_t before;  // record positions below this word's first position
+  uint32_t bits;    // record positions inside it
+};
+
+// bits[p >> 5] |= 1 << (p & 31) for every record position p (rec sorted by
+// position, so the lanes with one word are consecutive: each run of them is
+// OR-ed into its first lane, which alone writes).
+__global__ void k_pos_bits(const uint64_t* __restrict__ rec, int64_t n, uint32_t* __restrict__ bits) {
+  const int lane = lane_id();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31; base < n;
+       base += stride) {
+    const int64_t x = base + lane;
+    const bool ok = x < n;
+    const uint32_t p = ok ? rec_pos(rec[x]) : 0u;
+    const uint32_t w = ok ? (p >> 5) : 0xFFFFFFFFu;
+    uint32_t v = ok ? (1u << (p & 31)) : 0u;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t ov = __shfl_down_sync(0xffffffffu, v, d);
+      const uint32_t ow = __shfl_down_sync(0xffffffffu, w, d);
+      if (lane + d < 32 && ow == w) v |= ov;
+    }
+    const uint32_t pw = __shfl_up_sync(0xffffffffu, w, 1);
+    if (ok && (lane == 0 || pw != w)) atomicOr(bits + w, v);
+  }
+}
+
+__global__ void k_pos_popc(const uint32_t* __restrict__ bits, int64_t nw, uint32_t* __restrict__ cnt) {
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw;
+       w += (int64_t)gridDim.x * blockDim.x)
+    cnt[w] = __popc(bits[w]);
+}
+
+__global__ void k_rank_words(const uint32_t* __restrict__ bits, const uint32_t* __restrict__ before,
+                             int64_t nw, RankWord* __restrict__ rw) {
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw;
+       w += (int64_t)gridDim.x * blockDim.x)
+    rw[w] = RankWord{before[w], bits[w]};
+}
+
+__global__ void k_qpost_index(FArgs a, int64_t n, const RankWord* __restrict__ rw,
+                              uint2* __restrict__ out) {
+  const int lane = lane_id();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31; e0 < n;
+       e0 += stride) {
+    const int64_t e = e0 + lane;
+    const int L = (int)(n - 1 - e0 < 31 ? n - 1 - e0 : 31);  // last lane with an entry
+    const bool ok = lane <= L;
+    uint32_t h = 0xFFFFFFFFu, p = 0;
+    int g = -1;
+    if (ok) {
+      const uint64_t r = a.tsorted[e];
+      h = rec_hash(r);
+      p = rec_pos(r);
+      g = seq_of(a.tseq, a.ntseq, (int64_t)p);
+    }
+    const uint32_t ph = __shfl_up_sync(0xffffffffu, h, 1), nh = __shfl_down_sync(0xffffffffu, h, 1);
+    const int pg = __shfl_up_sync(0xffffffffu, g, 1), ng = __shfl_down_sync(0xffffffffu, g, 1);
+    const bool st = ok && (lane == 0 || ph != h || pg != g);
+    const bool en = ok && (lane == L || nh != h || ng != g);
+    const unsigned sb = __ballot_sync(0xffffffffu, st), eb = __ballot_sync(0xffffffffu, en);
+    const int fl = 31 - __clz(sb & ((2u << lane) - 1u));  // first lane of my run
+    const int ll = __ffs(eb & ~((1u << lane) - 1u)) - 1;  // last lane of my run
+    // the run holding the first entry may start before it, the run holding
+    // the last one may end after it
+    uint32_t s0 = 0, eL = 0;
+    if (lane == 0) s0 = pos_lower_bound(a.tsorted, a.toff[h], (uint32_t)e0, a.tseq[g]);
+    if (lane == L) eL = pos_gallop_forward(a.tsorted, (uint32_t)e + 1, a.toff[h + 1], a.tseq[g + 1]);
+    s0 = __shfl_sync(0xffffffffu, s0, 0);
+    eL = __shfl_sync(0xffffffffu, eL, L);
+    if (ok) {
+      const uint32_t rs = fl == 0 ? s0 : (uint32_t)(e0 + fl);
+      const uint32_t re = ll == L ? eL : (uint32_t)(e0 + ll + 1);
+      uint2 v = make_uint2(rs, re - rs);
+      if (a.max_occ > 0 && (int)(a.toff[h + 1] - a.toff[h]) > a.max_occ) v = make_uint2(kNone, 0u);
+      const RankWord q = rw[p >> 5];
+      out[q.before + __popc(q.bits & ((1u << (p & 31)) - 1u))] = v;
+    }
+  }
+}
+
 // ------------------------------------------------------------- fast path --
 
 template <int TPB, int LCAP, int GCAP, int SLOTS>
@@ -2463,13 +2556,36 @@ int run_filter(sedef_ctx* ctx, const uint64_t* qrec, int64_t nq, const int64_t* 
   }
   if (D.self_mode == 2 && 2 * D.k <= 24) {
     // batch self-search: every query record's posting range in its own
-    // genome, once (the warp tier reads them; its sort keys carry a
-    // record's offset beside a hash of at most 24 bits)
+    // genome, once (the warp tier reads them by record offset).  An eager
+    // pass walks the index (the query records are its records, with the
+    // same sequence offsets); a planned pass, whose counts live on the
+    // device, searches per record.
     uint2* qp = (uint2*)ctx_alloc(ctx, (size_t)nq * sizeof(uint2));
     if (!qp) return SEDEF_ERR_OOM;
+    const int64_t nw = (a.ttotal + 31) >> 5;
+    const bool walk = !pl && nqseq == ntseq &&
+                      std::memcmp(h_qoff, h_toff, (size_t)(ntseq + 1) * sizeof(int64_t)) == 0;
+    uint32_t* pbits = walk ? (uint32_t*)ctx_alloc(ctx, (size_t)(nw + 1) * 4) : nullptr;
+    uint32_t* pcnt = walk ? (uint32_t*)ctx_alloc(ctx, (size_t)(nw + 1) * 4) : nullptr;
+    uint32_t* pbef = walk ? (uint32_t*)ctx_alloc(ctx, (size_t)(nw + 1) * 4) : nullptr;
+    RankWord* rw = walk ? (RankWord*)ctx_alloc(ctx, (size_t)(nw + 1) * sizeof(RankWord)) : nullptr;
+    if (walk && (!pbits || !pcnt || !pbef || !rw)) return SEDEF_ERR_OOM;
     int64_t g = (nq + 255) / 256;
     if (g > (int64_t)ctx_sm_count(ctx) * 16) g = (int64_t)ctx_sm_count(ctx) * 16;
-    SEDEF_KERNEL(ctx, "k_qpost", k_qpost<<<(int)g, 256, 0, st>>>(a, nq, dnq, qp));
+    if (g < 1) g = 1;
+    if (!walk) {
+      SEDEF_KERNEL(ctx, "k_qpost", k_qpost<<<(int)g, 256, 0, st>>>(a, nq, dnq, qp));
+    } else {
+      int64_t gw = (nw + 255) / 256;
+      if (gw > (int64_t)ctx_sm_count(ctx) * 16) gw = (int64_t)ctx_sm_count(ctx) * 16;
+      if (gw < 1) gw = 1;
+      SEDEF_CUDA(cudaMemsetAsync(pbits, 0, (size_t)(nw + 1) * 4, st));
+      SEDEF_KERNEL(ctx, "k_pos_bits", k_pos_bits<<<(int)g, 256, 0, st>>>(qrec, nq, pbits));
+      SEDEF_KERNEL(ctx, "k_pos_popc", k_pos_popc<<<(int)gw, 256, 0, st>>>(pbits, nw, pcnt));
+      SEDEF_TRY(scan_exclusive_u32(ctx, pcnt, pbef, nw, pbef + nw));
+      SEDEF_KERNEL(ctx, "k_rank_words", k_rank_words<<<(int)gw, 256, 0, st>>>(pbits, pbef, nw, rw));
+      SEDEF_KERNEL(ctx, "k_qpost", k_qpost_index<<<(int)g, 256, 0, st>>>(a, nt, rw, qp));
+    }
     a.qpost = qp;
   }
   SEDEF_KERNEL(ctx, "k_windows",
