@@ -785,13 +785,15 @@ __global__ void __launch_bounds__(TPB) k_filter_fast(FArgs a, TierIO io) {
 //
 // Small windows (at most 128 query records, 4,096 hits, 256 collected hits
 // and 64 dense groups) take the same steps as k_filter_fast with one warp
-// per window and no block barriers: W_Q by a warp bitonic sort, hits by
-// binary search over the posting prefix sums, (bin, o) counters as the
-// prefilter, collected hits sorted per strand, dense groups found by the warp
-// and swept exactly by lane 0.  Windows past any limit go to the next tier.
+// per window and no block barriers: W_Q by insertion into a hash table (no
+// sort), hits found 32 at a time by a shuffle search over the posting prefix
+// sums, (bin, o) counters as the prefilter (a window with no adjacent bin
+// pair reaching m stops there), collected hits sorted per strand, dense
+// groups found by the warp and swept exactly by lane 0.  Windows past any
+// limit go to the next tier.
 
 constexpr int kWQ = 128;        // query records
-static_assert(kWQ <= 128, "the warp tier's sort keys carry a record offset in 7 bits");
+static_assert(kWQ <= 128, "a lane holds at most four of a window's query records");
 constexpr int kWSlots = 1024;   // (bin, o) 16-bit counters (512 bins)
 constexpr int kWL = 256;        // collected hits
 constexpr int kWG = 64;         // dense groups
