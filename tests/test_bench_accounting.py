@@ -40,3 +40,28 @@ def test_filter_bytes_match_direct_count(self_mode):
     assert got["windows"] == nwin and got["query_records"] == nq
     assert got["distinct_query_hashes"] == npairs and got["postings"] == post
     assert got["bytes"] == 4 * post + 8 * npairs + 8 * nq + 32 * 7
+
+
+def test_counters_used_only_for_their_workload_shape_and_source(tmp_path, monkeypatch):
+    """The per-unit ncu counters behind roofline.issue / roofline.traffic are
+    used only for the workload and filter shape they were captured on, and
+    only while the captured source file is unchanged."""
+    import hashlib
+    import json
+    import bench
+    src = tmp_path / "kernel.cu"
+    src.write_text("// captured revision\n")
+    entry = {"kernel": "filter family", "workload": "batch", "filter_shape": 11,
+             "source": str(src), "sha256": hashlib.sha256(src.read_bytes()).hexdigest(),
+             "unit": "hits", "warp_instructions_per_unit": 32.0, "dram_bytes_per_unit": 20.0}
+    path = tmp_path / "counters.json"
+    path.write_text(json.dumps({"entries": [entry]}))
+    monkeypatch.setattr(bench, "COUNTERS", str(path))
+    assert bench.counters_entry("filter family", "batch", 11)["warp_instructions_per_unit"] == 32.0
+    assert bench.counters_entry("filter family", "batch", 3) is None
+    assert bench.counters_entry("filter family", "human", 11) is None
+    assert bench.counters_entry("refine family", "batch", 11) is None
+    src.write_text("// changed revision\n")
+    assert bench.counters_entry("filter family", "batch", 11) is None
+    monkeypatch.setattr(bench, "COUNTERS", str(tmp_path / "missing.json"))
+    assert bench.counters_entry("filter family", "batch", 11) is None
