@@ -11,8 +11,12 @@
 // then the rightmost minimum of its 9 windows with a van Herk / Gil-Werman
 // split (suffix minima, a shared middle, prefix minima), and keeps a window's
 // argmin when it differs from the previous window's (winnowing argmins are
-// non-decreasing, so this emits each selected position once, in order).  A
-// count pass and a write pass bracket a device scan of the per-tile counts.
+// non-decreasing, so this emits each selected position once, in order).  The
+// window keys are (hash, reversed slot): 32 bits when the hash has at most 24
+// bits and a thread's windows span at most 128 slots, else 64.  The eager
+// pass writes its records in the same pass, finding each tile's offset by a
+// decoupled look-back over the tiles taken before it; the planned (graph)
+// pass and the allocation-free call count, scan and write instead.
 #include <cstring>
 
 #include "common.cuh"
