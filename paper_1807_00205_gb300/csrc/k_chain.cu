@@ -604,7 +604,7 @@ int run_chain(sedef_ctx* ctx, const sedef_run_t* runs, int64_t nruns, const uint
   SEDEF_CUDA(cudaMemcpyAsync(h_tot, pos + nruns, 4, cudaMemcpyDeviceToHost, st));
   SEDEF_CUDA(cudaStreamSynchronize(st));
   *nchains = *h_tot;
-  if (*nchains > cap) return fail(SEDEF_ERR_CAPACITY, "sedef_chain_t: chain buffer too small");
+  if (*nchains > cap) return fail(SEDEF_ERR_CAPACITY, "sedef_chain: chain buffer too small");
   SEDEF_KERNEL(ctx, "k_chain_compact",
                k_chain_compact<<<grid_of(nruns, 256), 256, 0, st>>>(tmp, nruns, pos, chains, cap,
                                                                     nullptr));
